@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark: selected-G^R energies x blocks per second on one GB300.
+
+A step is one full selected inversion (upward Schur sweep, per-block
+inversions, downward pass, G_1N chain) of the synthetic nanowire workload
+"batched64x64": 64 blocks of b = 64, block tridiagonal, 512 energies in
+[-2, 2] with eta = 1e-6, all energies in one call.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference    # the CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank runs the full workload on its own GPU with
+its own energy grid (weak scaling, no collective on the data path); rank 0
+prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "batched64x64"
+METRIC = "selected-G^R energies x blocks / s"
+UNIT = "energy-blocks/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-energies", type=int, default=96,
+                    help="energies of the bounded CPU-oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (the only place besides tests and smoke that runs oracle/)
+# ---------------------------------------------------------------------------
+def _oracle_worker(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    name, idx = args
+    from oracle import rgf as O
+    from workloads import workload
+    prob = workload(name)
+    t0 = time.perf_counter()
+    for e in idx:
+        E = prob.energies[e]
+        O.rgf_selected(O.system_blocks(prob, E), prob.sizes, prob.w, first_row=True)
+    return time.perf_counter() - t0
+
+
+def oracle_sample(name, n_energies, pool, cores):
+    from workloads import workload
+    prob = workload(name)
+    nE = len(prob.energies)
+    n = min(n_energies, nE)
+    picks = [int(round(i * (nE - 1) / max(n - 1, 1))) for i in range(n)]
+    chunks = [picks[i::cores] for i in range(cores)]
+    chunks = [c for c in chunks if c]
+    t0 = time.perf_counter()
+    pool.map(_oracle_worker, [(name, c) for c in chunks])
+    wall = time.perf_counter() - t0
+    units = n * prob.n_blocks
+    return dict(value=units / wall, unit=UNIT, cores=len(chunks), kind="oracle",
+                sample=f"{n} of {nE} energies x all {prob.n_blocks} blocks of {name} "
+                       f"(oracle sequential RGF, complex128, numpy/LAPACK), {wall:.2f} s wall"), wall
+
+
+def make_pool(cores):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(cores)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(a, rank, world, local_rank):
+    import numpy as np
+    pool = None
+    cores = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not a.no_cpu:
+        pool = make_pool(cores)          # spawn, before the first GPU call
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2605_19910_gb300 as P
+    from workloads import workload
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prob = workload(a.workload)
+    if world > 1 and rank > 0:
+        prob.energies = prob.energies + 1e-3 * rank      # each rank its own energy grid
+    N, nE = prob.n_blocks, len(prob.energies)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    Hh = torch.tensor(P.pack_band(prob.H, prob.sizes, prob.w)).pin_memory()
+    sLh = torch.tensor(prob.sigma_L).pin_memory()
+    sRh = torch.tensor(prob.sigma_R).pin_memory()
+    Eh = torch.tensor(prob.energies).pin_memory()
+    H, sL, sR, E = (x.to(dev) for x in (Hh, sLh, sRh, Eh))
+    outputs = P.NEGF_OUT_BAND | P.NEGF_OUT_G1N | P.NEGF_OUT_TRANSMISSION
+    plan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision=a.precision, outputs=outputs)
+    Gb = torch.empty(nE, plan.band_elems, dtype=torch.complex128, device=dev)
+    G1 = torch.empty(nE, prob.sizes[0], prob.sizes[-1], dtype=torch.complex128, device=dev)
+
+    def step():
+        plan.solve(H, sL, sR, E, out_band=Gb, out_g1n=G1, sync=False)
+
+    for _ in range(a.warmup):
+        step()
+    plan.sync()
+
+    # per-kernel profile of one extra step (events around every launch)
+    P.negf_profile_enable(plan.handle, 1)
+    step()
+    prof = P.negf_profile_read(plan.handle)
+    P.negf_profile_enable(plan.handle, 0)
+    plan.sync()
+    launches_per_step = int(sum(v[2] for v in prof.values()))
+
+    clocks = Clocks(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(a.steps):
+        step()
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    st = plan.sync  # raises on any device-reported error
+    st()
+    ms = t_start.elapsed_time(t_end) / a.steps
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * nE * N / (ms * 1e-3)
+
+    # sampled parity against the oracle (two energies) for the rel-err report
+    rel = None
+    if rank == 0:
+        from oracle import rgf as O
+        errs = []
+        for e in (0, nE // 2):
+            ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, prob.w, first_row=True)
+            got = P.unpack_band(Gb[e].cpu().numpy(), prob.sizes, prob.w)
+            num = sum(np.linalg.norm(got[k] - v) ** 2 for k, v in ref["band"].items())
+            den = sum(np.linalg.norm(v) ** 2 for v in ref["band"].values())
+            errs.append(float(np.sqrt(num / den)))
+        rel = max(errs)
+
+    # end to end through the public API: pinned host inputs -> device, solve,
+    # selected blocks and G_1N back to pinned host memory, every step
+    e2e = None
+    if not a.no_e2e:
+        Gb_h = torch.empty(Gb.shape, dtype=Gb.dtype).pin_memory()
+        G1_h = torch.empty(G1.shape, dtype=G1.dtype).pin_memory()
+
+        def e2e_step():
+            H.copy_(Hh, non_blocking=True)
+            sL.copy_(sLh, non_blocking=True)
+            sR.copy_(sRh, non_blocking=True)
+            E.copy_(Eh, non_blocking=True)
+            plan.solve(H, sL, sR, E, out_band=Gb, out_g1n=G1, sync=False)
+            Gb_h.copy_(Gb, non_blocking=True)
+            G1_h.copy_(G1, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(1, min(a.steps, 5))
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k2):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = e0.elapsed_time(e1) / k2
+        if dist:
+            tt = torch.tensor([ms2], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms2 = float(tt.item())
+        h2d = sum(x.numel() * x.element_size() for x in (Hh, sLh, sRh, Eh))
+        d2h = Gb_h.numel() * Gb_h.element_size() + G1_h.numel() * G1_h.element_size()
+        e2e = {"value": world * nE * N / (ms2 * 1e-3), "unit": UNIT, "ms_per_step": ms2,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel (from the profiled step)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+    fp64_peak = bf16 * (1.25 / 2250.0)          # FP64 nominal : bf16 nominal
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (dms, dfl, dln) = dom
+    achieved = dfl / (dms * 1e-3) / 1e12 if dms > 0 else 0.0
+    roof = {"kernel": name, "bound": "tensor" if name == "zgemm_f64_kernel" else "alu",
+            "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+            "traffic": None,
+            "peak_source": "MEASURED_PEAKS bf16 sustained x nominal FP64:bf16 (1.25:2250)",
+            "kernel_share": dms / sum(v[0] for v in prof.values()),
+            "launches_per_step": int(dln)}
+
+    from oracle.rgf import rgf_flops_paper
+    flops_step = rgf_flops_paper(prob.sizes, prob.w) * nE
+    ws_gb = P.negf_workspace_bytes(plan.handle) / 1e9
+    plan.close()
+
+    cpu = None
+    if pool is not None:
+        cpu, _ = oracle_sample(a.workload, a.cpu_energies, pool, cores)
+        pool.close()
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64" if a.precision == "fp64" else "mixed: bf16x3-split tensor products, f64 inverses",
+            "data": "synthetic",
+            "config": {"workload": a.workload, "n_blocks": N, "block_size": prob.sizes[0], "band_n": 2 * prob.w + 1,
+                       "n_energies": nE, "eta": 1e-6, "precision": a.precision,
+                       "outputs": "band + G_1N per energy",
+                       "l2": "no flush: each step writes %.1f GB of selected blocks and %.1f GB of sweep "
+                             "workspace, both far above the 129 MB L2" % (Gb.numel() * 16 / 1e9, ws_gb),
+                       "parallelism": f"replicas x{world} (energies)"},
+            "effective_tflops_paper_count": flops_step / (ms * 1e-3) / 1e12 * world,
+            "rel_err_vs_oracle_sampled": rel,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": launches_per_step * a.steps,
+        }
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle, on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    pool = make_pool(cores)
+    from workloads import workload
+    prob = workload(a.workload)
+    n = min(a.cpu_energies, 16 * cores)
+    for _ in range(a.warmup):
+        oracle_sample(a.workload, min(n, cores), pool, cores)
+    vals, walls = [], []
+    cpu = None
+    for _ in range(a.steps):
+        cpu, wall = oracle_sample(a.workload, n, pool, cores)
+        vals.append(cpu["value"])
+        walls.append(wall)
+    pool.close()
+    v = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.median(walls) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": a.workload, "n_blocks": prob.n_blocks, "block_size": prob.sizes[0],
+                      "n_energies": len(prob.energies), "sample_energies_per_step": n},
+           "cpu_baseline": dict(cpu, value=v),
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    a = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_ours(a, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

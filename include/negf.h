@@ -1,0 +1,183 @@
+/*
+ * negf.h -- C-ABI of the GB300 selected-inversion library (libnegf.so).
+ *
+ * The library computes, for a grid of complex energies E, selected blocks of
+ * the retarded Green's function
+ *
+ *     G^R(E) = M(E)^{-1},   M(E) = E I - H - Sigma^R            (Sec. 2, eq. for M)
+ *
+ * where H is block n-diagonal over N principal layers (n = 3, 5, ...; the
+ * half-bandwidth is w = (n-1)/2, Sec. 2.3, Prop. 3) and the lead
+ * self-energy Sigma^R acts on layer 1 (Sigma_L) and layer N (Sigma_R) only.
+ * The selected blocks are bndiag(G^R) (Sec. 2, "the Dyson problem"), computed
+ * by the recursive Green's function method (Alg. 1; Sec. 2.3 for n > 3) or by
+ * single-level domain-decomposition RGF (Alg. 2), plus the corner block
+ * G_{1N} (Eq. 4x4_exact_RGF, first row), the transmission
+ * T(E) = Tr[Gamma_L G_1N Gamma_R G_1N^H] with Gamma = i(Sigma - Sigma^H), and
+ * the gradient of T with respect to the band blocks of H and to Sigma_L/R.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are interleaved (re, im) doubles: negf_c128, the layout
+ *   of cuDoubleComplex and of torch.complex128.
+ * - Every block is dense and row-major: block (i, j) has b_i rows and b_j
+ *   columns, element (r, c) at offset r * b_j + c.
+ * - "Band-packed" storage of a block n-diagonal matrix: the existing blocks
+ *   (i, i + d) are stored back to back for d = -w .. w (outer) and
+ *   i = 0 .. N-1 (inner), skipping blocks with i + d outside [0, N).
+ *   negf_band_offset() gives the element offset of block (i, i + d) and
+ *   negf_band_elems() the total element count of one band-packed matrix.
+ *   Layers are 0-based in this interface.
+ * - All array arguments of negf_solve / negf_transmission / negf_grad are
+ *   DEVICE pointers on the device that was current at negf_plan().  The
+ *   caller owns them; the library never frees them.  Calls are asynchronous
+ *   on the plan's stream: outputs are ready after negf_sync() or after any
+ *   later work on that stream.
+ * - Errors: argument errors are returned before anything is launched.
+ *   Numerical failures found on the device (an exactly zero or non-finite
+ *   pivot in a per-block inversion) are written to info[e] (0 = success,
+ *   k > 0 = 1-based layer whose Schur complement failed first, for energy e)
+ *   and folded into the status that negf_sync() returns
+ *   (NEGF_ERR_SINGULAR / NEGF_ERR_NONFINITE).  No entry point aborts,
+ *   traps or throws.
+ * - A plan is not thread-safe; use one plan per host thread.
+ */
+#ifndef NEGF_H
+#define NEGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } negf_c128;
+
+typedef enum {
+  NEGF_OK = 0,
+  NEGF_ERR_ARG = 1,          /* invalid argument or descriptor                */
+  NEGF_ERR_SINGULAR = 2,     /* a zero pivot in a per-block inversion          */
+  NEGF_ERR_NONFINITE = 3,    /* a NaN/Inf pivot (e.g. NaN in H)                */
+  NEGF_ERR_NOMEM = 4,        /* workspace allocation failed                    */
+  NEGF_ERR_CUDA = 5,         /* a CUDA runtime call failed                     */
+  NEGF_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up             */
+  NEGF_ERR_UNSUPPORTED = 7   /* valid request this build does not implement    */
+} negf_status;
+
+/* Arithmetic of the sweep.
+ * NEGF_FP64:  every product and every per-block inverse in double precision.
+ * NEGF_MIXED: block products on the tensor cores in an FP32-accurate split
+ *             (each operand split into bf16 parts, FP32 accumulation),
+ *             per-block inverses (and the DDRGF interface system) in FP64;
+ *             inputs and outputs stay complex128. */
+typedef enum { NEGF_FP64 = 0, NEGF_MIXED = 1 } negf_precision;
+
+/* Output selection bits (negf_desc.outputs). */
+enum {
+  NEGF_OUT_BAND = 1,          /* bndiag(G) per energy                          */
+  NEGF_OUT_G1N = 2,           /* G_{1N} per energy                             */
+  NEGF_OUT_TRANSMISSION = 4,  /* T(E)                                          */
+  NEGF_OUT_GRAD = 8           /* allow negf_grad (keeps the first-row chain)   */
+};
+
+typedef struct {
+  int32_t n_blocks;                   /* N >= 1 (N > w)                        */
+  const int32_t* block_sizes;         /* host array of N sizes b_i, 1 <= b_i <= NEGF_MAX_BLOCK */
+  int32_t band_n;                     /* n = 3 or 5 (w = (n-1)/2)              */
+  int32_t n_energies;                 /* >= 1                                  */
+  int32_t n_domains;                  /* 1 = plain RGF, >1 = single-level DDRGF */
+  const int32_t* domain_first_block;  /* host, n_domains entries or NULL       */
+  int32_t precision;                  /* negf_precision                        */
+  int32_t refine_steps;               /* 0 or 1 (NEGF_MIXED only)              */
+  int32_t outputs;                    /* NEGF_OUT_* bit mask                   */
+  int32_t checkpoint_every;           /* adjoint: keep every k-th layer, 0=all */
+} negf_desc;
+
+#define NEGF_MAX_BLOCK 160
+
+typedef struct negf_plan_s negf_plan_t;   /* opaque plan handle */
+
+/* Validate the descriptor, fix the schedule and allocate the workspace.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * Returns NEGF_ERR_ARG for an invalid descriptor, NEGF_ERR_NOMEM if the
+ * workspace cannot be allocated, NEGF_ERR_UNSUPPORTED for a combination this
+ * build does not implement.  On success *out owns the workspace. */
+negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream);
+
+/* Bytes of device workspace the plan holds. */
+size_t negf_workspace_bytes(const negf_plan_t* p);
+
+/* Element offset of block (i, i + d) in band-packed storage, or -1 if that
+ * block does not exist (|d| > w or i + d outside [0, N)). */
+int64_t negf_band_offset(const negf_plan_t* p, int32_t d, int32_t i);
+
+/* Elements of one band-packed matrix (per energy). */
+int64_t negf_band_elems(const negf_plan_t* p);
+
+/* bndiag(G^R(E)) and/or G_{1N} for every energy (Alg. 1, Sec. 2.3, Alg. 2).
+ *   H:       band-packed H (energy independent), negf_band_elems() elements.
+ *   sigma_L: b_1 x b_1 per energy, energy e at sigma_L + e * sigma_E_stride
+ *            (stride 0 broadcasts one matrix to all energies); same for sigma_R
+ *            (b_N x b_N).  sigma_E_stride is in elements.
+ *   E:       n_energies complex energies (E_r + i eta).
+ *   G_band:  n_energies x negf_band_elems() elements (energy-major); may be
+ *            NULL if NEGF_OUT_BAND is not requested.
+ *   G_1N:    n_energies x (b_1 * b_N); may be NULL.
+ *   info:    n_energies int32 (see the error conventions above); required. */
+negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                       const negf_c128* sigma_R, int64_t sigma_E_stride,
+                       const negf_c128* E, negf_c128* G_band, negf_c128* G_1N,
+                       int32_t* info);
+
+/* T(E) = Tr[Gamma_L G_1N Gamma_R G_1N^H] for every energy into T[n_energies]
+ * (doubles).  Same inputs as negf_solve. */
+negf_status negf_transmission(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                              const negf_c128* sigma_R, int64_t sigma_E_stride,
+                              const negf_c128* E, double* T, int32_t* info);
+
+/* Gradient of L = sum_e dL_dT[e] * T(E_e) (vector-Jacobian product) with
+ * respect to the band blocks of H and to sigma_L / sigma_R, in the
+ * convention dL/dRe z + i dL/dIm z (the one torch.autograd uses for a real
+ * loss of complex inputs).  Blocks of H are treated as independent inputs
+ * (the Hermitian tie H_{i+1,i} = H_{i,i+1}^H is not imposed).
+ *   dL_dT:    n_energies doubles.
+ *   T:        optional (may be NULL): receives T(E) as in negf_transmission.
+ *   dH:       band-packed, negf_band_elems() elements, summed over energies.
+ *   dSigma_L: b_1 x b_1 per energy with stride sigma_E_stride (0 = summed
+ *             over energies into one matrix); dSigma_R likewise.  Either may
+ *             be NULL.
+ * Requires a plan with NEGF_OUT_GRAD, n_domains == 1 and band_n == 3. */
+negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                      const negf_c128* sigma_R, int64_t sigma_E_stride,
+                      const negf_c128* E, const double* dL_dT, double* T,
+                      negf_c128* dH, negf_c128* dSigma_L, negf_c128* dSigma_R,
+                      int32_t* info);
+
+/* Wait for the plan's stream, then return the first error the device
+ * reported since the previous negf_sync (and clear it). */
+negf_status negf_sync(negf_plan_t* p);
+
+/* Release the workspace and the plan.  NULL is allowed. */
+void negf_destroy(negf_plan_t* p);
+
+/* Instrumentation: per-kernel timing of the calls made while enabled.
+ * With profiling on, calls run without graph capture and every kernel launch
+ * is bracketed by CUDA events on the plan's stream.  negf_profile_read waits
+ * for the stream and returns, per kernel kind (index NEGF_PROF_*), the summed
+ * device milliseconds, the algorithmic real flops (8 m n k per complex block
+ * product, 8 b^3 per block inverse) and the launch count, then resets them.
+ * Any of the three arrays may be NULL; each must hold NEGF_PROF_KINDS
+ * entries.  Returns NEGF_PROF_KINDS, or -1 on error. */
+enum { NEGF_PROF_INV = 0, NEGF_PROF_GEMM_F64 = 1, NEGF_PROF_GEMM_TC = 2, NEGF_PROF_MISC = 3,
+       NEGF_PROF_KINDS = 4 };
+negf_status negf_profile_enable(negf_plan_t* p, int32_t on);
+int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* launches);
+
+/* Static, human-readable name of a status code. */
+const char* negf_status_string(negf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEGF_H */

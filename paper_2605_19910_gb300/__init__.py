@@ -1,0 +1,365 @@
+"""Python binding of libnegf.so: GB300 selected inversion of G^R(E) = (E I - H - Sigma)^{-1}.
+
+The functions named ``negf_*`` mirror the C-ABI in ``include/negf.h`` one to
+one and only marshal arguments (device pointers from torch tensors, the
+current CUDA stream).  Every step of the computation runs in the library's
+CUDA kernels; there is no CPU or PyTorch fallback: if ``libnegf.so`` is
+missing or fails to load, importing this package raises.
+
+Higher-level helpers: :func:`band_layout` / :func:`pack_band` /
+:func:`unpack_band` (host-side layout of band-packed block matrices),
+:class:`Plan` (a plan bound to torch tensors), and :class:`Transmission`
+(a ``torch.autograd.Function`` whose backward is the library's adjoint).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnegf.so")
+
+NEGF_OK = 0
+NEGF_ERR_ARG = 1
+NEGF_ERR_SINGULAR = 2
+NEGF_ERR_NONFINITE = 3
+NEGF_ERR_NOMEM = 4
+NEGF_ERR_CUDA = 5
+NEGF_ERR_TIMEOUT = 6
+NEGF_ERR_UNSUPPORTED = 7
+
+NEGF_FP64 = 0
+NEGF_MIXED = 1
+
+NEGF_OUT_BAND = 1
+NEGF_OUT_G1N = 2
+NEGF_OUT_TRANSMISSION = 4
+NEGF_OUT_GRAD = 8
+
+NEGF_MAX_BLOCK = 160
+
+NEGF_PROF_INV = 0
+NEGF_PROF_GEMM_F64 = 1
+NEGF_PROF_GEMM_TC = 2
+NEGF_PROF_MISC = 3
+NEGF_PROF_KINDS = 4
+PROF_NAMES = ["zinv_gj_kernel", "zgemm_f64_kernel", "zgemm_tc_kernel", "misc"]
+
+EXPORTED = [
+    "negf_plan", "negf_workspace_bytes", "negf_band_offset", "negf_band_elems", "negf_solve",
+    "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
+    "negf_profile_enable", "negf_profile_read",
+]
+
+
+class NegfError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = int(status)
+        super().__init__(f"{where}: {negf_status_string(status)} ({status})")
+
+
+class negf_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_blocks", ctypes.c_int32),
+        ("block_sizes", ctypes.POINTER(ctypes.c_int32)),
+        ("band_n", ctypes.c_int32),
+        ("n_energies", ctypes.c_int32),
+        ("n_domains", ctypes.c_int32),
+        ("domain_first_block", ctypes.POINTER(ctypes.c_int32)),
+        ("precision", ctypes.c_int32),
+        ("refine_steps", ctypes.c_int32),
+        ("outputs", ctypes.c_int32),
+        ("checkpoint_every", ctypes.c_int32),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libnegf.so not found at {LIB_PATH}; build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+    lib.negf_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(negf_desc), vp]
+    lib.negf_plan.restype = st
+    lib.negf_workspace_bytes.argtypes = [vp]
+    lib.negf_workspace_bytes.restype = ctypes.c_size_t
+    lib.negf_band_offset.argtypes = [vp, i32, i32]
+    lib.negf_band_offset.restype = i64
+    lib.negf_band_elems.argtypes = [vp]
+    lib.negf_band_elems.restype = i64
+    lib.negf_solve.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.negf_solve.restype = st
+    lib.negf_transmission.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+    lib.negf_transmission.restype = st
+    lib.negf_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]
+    lib.negf_grad.restype = st
+    lib.negf_sync.argtypes = [vp]
+    lib.negf_sync.restype = st
+    lib.negf_destroy.argtypes = [vp]
+    lib.negf_destroy.restype = None
+    lib.negf_profile_enable.argtypes = [vp, i32]
+    lib.negf_profile_enable.restype = st
+    dp = ctypes.POINTER(ctypes.c_double)
+    lp = ctypes.POINTER(ctypes.c_int64)
+    lib.negf_profile_read.argtypes = [vp, dp, dp, lp]
+    lib.negf_profile_read.restype = i32
+    lib.negf_status_string.argtypes = [st]
+    lib.negf_status_string.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# C-ABI mirror (argument marshalling only)
+# ---------------------------------------------------------------------------
+def negf_status_string(status):
+    return _lib.negf_status_string(int(status)).decode()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def negf_plan(block_sizes, band_n=3, n_energies=1, n_domains=1, domain_first_block=None,
+              precision=NEGF_FP64, refine_steps=0, outputs=NEGF_OUT_BAND | NEGF_OUT_G1N,
+              checkpoint_every=0, stream=None):
+    """Create a plan; returns an opaque handle (int).  Raises NegfError."""
+    sizes = (ctypes.c_int32 * len(block_sizes))(*[int(b) for b in block_sizes])
+    d = negf_desc()
+    d.n_blocks = len(block_sizes)
+    d.block_sizes = sizes
+    d.band_n = band_n
+    d.n_energies = n_energies
+    d.n_domains = n_domains
+    if domain_first_block is not None:
+        dfb = (ctypes.c_int32 * len(domain_first_block))(*[int(x) for x in domain_first_block])
+        d.domain_first_block = dfb
+    d.precision = precision
+    d.refine_steps = refine_steps
+    d.outputs = outputs
+    d.checkpoint_every = checkpoint_every
+    h = ctypes.c_void_p()
+    s = _lib.negf_plan(ctypes.byref(h), ctypes.byref(d), stream)
+    if s != NEGF_OK:
+        raise NegfError(s, "negf_plan")
+    return h.value
+
+
+def negf_workspace_bytes(plan):
+    return int(_lib.negf_workspace_bytes(plan))
+
+
+def negf_band_offset(plan, d, i):
+    return int(_lib.negf_band_offset(plan, d, i))
+
+
+def negf_band_elems(plan):
+    return int(_lib.negf_band_elems(plan))
+
+
+def negf_solve(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info):
+    return _lib.negf_solve(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
+                           _ptr(G_band), _ptr(G_1N), _ptr(info))
+
+
+def negf_transmission(plan, H, sigma_L, sigma_R, sigma_E_stride, E, T, info):
+    return _lib.negf_transmission(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride),
+                                  _ptr(E), _ptr(T), _ptr(info))
+
+
+def negf_grad(plan, H, sigma_L, sigma_R, sigma_E_stride, E, dL_dT, T, dH, dSigma_L, dSigma_R, info):
+    return _lib.negf_grad(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
+                          _ptr(dL_dT), _ptr(T), _ptr(dH), _ptr(dSigma_L), _ptr(dSigma_R), _ptr(info))
+
+
+def negf_sync(plan):
+    return _lib.negf_sync(plan)
+
+
+def negf_destroy(plan):
+    _lib.negf_destroy(plan)
+
+
+def negf_profile_enable(plan, on):
+    return _lib.negf_profile_enable(plan, int(bool(on)))
+
+
+def negf_profile_read(plan):
+    """Returns ``{kind_name: (ms, flops, launches)}`` for the calls made since
+    profiling was enabled (or since the previous read)."""
+    ms = (ctypes.c_double * NEGF_PROF_KINDS)()
+    fl = (ctypes.c_double * NEGF_PROF_KINDS)()
+    ln = (ctypes.c_int64 * NEGF_PROF_KINDS)()
+    n = _lib.negf_profile_read(plan, ms, fl, ln)
+    if n < 0:
+        raise NegfError(NEGF_ERR_CUDA, "negf_profile_read")
+    return {PROF_NAMES[k]: (ms[k], fl[k], ln[k]) for k in range(n)}
+
+
+# ---------------------------------------------------------------------------
+# Host-side layout helpers (no arithmetic of the method)
+# ---------------------------------------------------------------------------
+def band_layout(sizes, w):
+    """Offsets of the band-packed layout of include/negf.h: blocks (i, i+d)
+    for d = -w..w (outer), i = 0..N-1 (inner), existing blocks only.
+    Returns ``(offsets dict {(i, j): offset}, total elements)``."""
+    N = len(sizes)
+    off = {}
+    o = 0
+    for d in range(-w, w + 1):
+        for i in range(N):
+            j = i + d
+            if 0 <= j < N:
+                off[(i, j)] = o
+                o += sizes[i] * sizes[j]
+    return off, o
+
+
+def pack_band(blocks, sizes, w, dtype=np.complex128):
+    """Pack a dict ``{(i, j): block}`` into one band-packed vector."""
+    off, n = band_layout(sizes, w)
+    out = np.zeros(n, dtype=dtype)
+    for (i, j), o in off.items():
+        blk = blocks.get((i, j))
+        if blk is not None:
+            out[o:o + sizes[i] * sizes[j]] = np.asarray(blk, dtype=dtype).reshape(-1)
+    return out
+
+
+def unpack_band(vec, sizes, w):
+    """Inverse of :func:`pack_band` (views into ``vec``)."""
+    off, _ = band_layout(sizes, w)
+    return {(i, j): vec[o:o + sizes[i] * sizes[j]].reshape(sizes[i], sizes[j]) for (i, j), o in off.items()}
+
+
+# ---------------------------------------------------------------------------
+# Plan bound to torch tensors
+# ---------------------------------------------------------------------------
+class Plan:
+    """A negf plan whose calls take and return torch CUDA tensors.
+
+    ``sizes``: block sizes; ``band_n``: 3 or 5; ``n_energies``; ``precision``:
+    ``"fp64"`` or ``"mixed"``; ``outputs``: NEGF_OUT_* mask.  The plan is bound
+    to the torch CUDA stream current at construction.
+    """
+
+    def __init__(self, sizes, band_n=3, n_energies=1, n_domains=1, domain_first_block=None,
+                 precision="fp64", refine_steps=0, outputs=NEGF_OUT_BAND | NEGF_OUT_G1N,
+                 checkpoint_every=0, stream=None):
+        import torch
+        self.torch = torch
+        self.sizes = [int(b) for b in sizes]
+        self.w = (band_n - 1) // 2
+        self.band_n = band_n
+        self.n_energies = int(n_energies)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        prec = {"fp64": NEGF_FP64, "mixed": NEGF_MIXED}[precision] if isinstance(precision, str) else precision
+        self.handle = negf_plan(self.sizes, band_n, self.n_energies, n_domains, domain_first_block, prec,
+                                refine_steps, outputs, checkpoint_every, self.stream.cuda_stream)
+        self.band_elems = negf_band_elems(self.handle)
+        self.info = torch.zeros(self.n_energies, dtype=torch.int32, device="cuda")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            negf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, status, where):
+        if status != NEGF_OK:
+            raise NegfError(status, where)
+
+    def sync(self):
+        s = negf_sync(self.handle)
+        if s != NEGF_OK:
+            raise NegfError(s, "negf_sync")
+
+    @staticmethod
+    def _sig_stride(sig, b):
+        return 0 if sig.dim() == 2 else b * b
+
+    def solve(self, H, sigma_L, sigma_R, E, band=True, g1n=True, out_band=None, out_g1n=None, sync=True):
+        """Returns ``(G_band [n_E, band_elems] or None, G_1N [n_E, b1, bN] or None)``."""
+        torch = self.torch
+        nE = self.n_energies
+        b0, bN = self.sizes[0], self.sizes[-1]
+        Gb = out_band if out_band is not None else (
+            torch.empty(nE, self.band_elems, dtype=torch.complex128, device="cuda") if band else None)
+        G1 = out_g1n if out_g1n is not None else (
+            torch.empty(nE, b0, bN, dtype=torch.complex128, device="cuda") if g1n else None)
+        stride = self._sig_stride(sigma_L, b0)
+        self._check(negf_solve(self.handle, H, sigma_L, sigma_R, stride, E, Gb, G1, self.info), "negf_solve")
+        if sync:
+            self.sync()
+        return Gb, G1
+
+    def transmission(self, H, sigma_L, sigma_R, E, out=None, sync=True):
+        torch = self.torch
+        T = out if out is not None else torch.empty(self.n_energies, dtype=torch.float64, device="cuda")
+        stride = self._sig_stride(sigma_L, self.sizes[0])
+        self._check(negf_transmission(self.handle, H, sigma_L, sigma_R, stride, E, T, self.info),
+                    "negf_transmission")
+        if sync:
+            self.sync()
+        return T
+
+    def grad(self, H, sigma_L, sigma_R, E, dL_dT, sync=True):
+        """Returns ``(T, dH, dSigma_L, dSigma_R)``."""
+        torch = self.torch
+        T = torch.empty(self.n_energies, dtype=torch.float64, device="cuda")
+        dH = torch.empty(self.band_elems, dtype=torch.complex128, device="cuda")
+        dSL = torch.empty_like(sigma_L)
+        dSR = torch.empty_like(sigma_R)
+        stride = self._sig_stride(sigma_L, self.sizes[0])
+        self._check(negf_grad(self.handle, H, sigma_L, sigma_R, stride, E, dL_dT.contiguous(), T, dH, dSL, dSR,
+                              self.info), "negf_grad")
+        if sync:
+            self.sync()
+        return T, dH, dSL, dSR
+
+
+def _autograd():
+    import torch
+
+    class Transmission(torch.autograd.Function):
+        """``T(E) = Tr[Gamma_L G_1N Gamma_R G_1N^H]`` with the library's adjoint
+        as backward.  ``Transmission.apply(plan, H, sigma_L, sigma_R, E)``: the
+        plan must have been created with ``NEGF_OUT_GRAD``."""
+
+        @staticmethod
+        def forward(ctx, plan, H, sigma_L, sigma_R, E):
+            ctx.plan = plan
+            ctx.save_for_backward(H, sigma_L, sigma_R, E)
+            return plan.transmission(H, sigma_L, sigma_R, E)
+
+        @staticmethod
+        def backward(ctx, gT):
+            H, sL, sR, E = ctx.saved_tensors
+            _, dH, dSL, dSR = ctx.plan.grad(H, sL, sR, E, gT.to(torch.float64))
+            return None, dH, dSL, dSR, None
+
+    return Transmission
+
+
+def __getattr__(name):
+    if name == "Transmission":
+        return _autograd()
+    raise AttributeError(name)

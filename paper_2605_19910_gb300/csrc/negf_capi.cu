@@ -1,0 +1,650 @@
+// C-ABI of libnegf.so: plan construction, the schedule of the RGF sweep over
+// a batch of energies, CUDA-graph capture of that schedule, and error folding.
+//
+// The sweep is Alg. 1 (block tridiagonal) generalised to a block n-diagonal
+// matrix with half-bandwidth w (Sec. 2.3, Prop. 3 and the prose on the
+// downward pass).  Every step runs for all energies of a chunk at once: each
+// launch is one batched kernel over energies (the per-block inversion, or a
+// block product whose H operand is shared by every energy).  The whole
+// schedule of one call is captured once into a CUDA graph and replayed while
+// the caller's pointers stay the same.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/negf.h"
+#include "negf_common.cuh"
+#include "negf_kernels.h"
+
+using negf::ZGemm;
+
+namespace {
+
+struct BlockRef {        // where block S_ab of the running Schur complement lives
+  bool materialized = false;
+};
+
+struct CallKey {
+  const void* p[12];
+  int64_t stride;
+  int kind;
+  bool operator==(const CallKey& o) const {
+    return kind == o.kind && stride == o.stride && std::memcmp(p, o.p, sizeof(p)) == 0;
+  }
+};
+
+}  // namespace
+
+struct negf_plan_s {
+  int N = 0, w = 1, nE = 0, n_domains = 1, precision = 0, refine = 0, outputs = 0, ckpt = 0;
+  std::vector<int> b;
+  std::vector<int64_t> band_off;   // (d + w) * N + i -> element offset or -1
+  int64_t band_elems = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int chunk = 0;                   // energies per chunk
+
+  // workspace (one allocation)
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int* d_err = nullptr;
+
+  // per-energy element offsets inside one chunk slab of each region
+  std::vector<int64_t> t_off, x_off, y_off;   // x_off/y_off indexed [i * w + (i - c - 1)]
+  int64_t t_elems = 0, x_elems = 0, y_elems = 0;
+  double2 *T_ws = nullptr, *X_ws = nullptr, *Y_ws = nullptr;
+  double2* S_ws = nullptr;      // (w+1)^2 slots of bmax^2 per energy
+  int64_t s_slot = 0;           // bmax^2
+  double2* R_ws = nullptr;      // first-row chain: full row (grad) or a ring of w+1
+  std::vector<int64_t> r_off;   // per layer offset (per energy) in R_ws
+  int64_t r_elems = 0;
+  double2* P_ws = nullptr;      // grad: suffix products P_i (b_i x b_N)
+  double2* LC_ws = nullptr;     // grad: last column g_i (b_i x b_N)
+  std::vector<int64_t> p_off;
+  int64_t p_elems = 0;
+  double2* Gint = nullptr;      // grad: internal first-row / scratch
+  double2* scratch = nullptr;   // transmission: Gamma_L, Gamma_R, P, Q per energy
+  int64_t scr_elems = 0;
+  double2* G1N_ws = nullptr;    // G_1N when the caller does not keep it
+  double* Tdummy = nullptr;
+
+  // optional per-launch timing (negf_profile_enable)
+  bool profiling = false;
+  struct Rec { int kind; double flops; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  double prof_ms[NEGF_PROF_KINDS] = {0};
+  double prof_flops[NEGF_PROF_KINDS] = {0};
+  int64_t prof_launches[NEGF_PROF_KINDS] = {0};
+
+  // CUDA graph of the last call
+  cudaGraphExec_t gexec = nullptr;
+  bool have_key = false;
+  CallKey key{};
+};
+
+namespace {
+
+inline negf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA; }
+
+#define NEGF_TRY(x)                                          \
+  do {                                                       \
+    cudaError_t _e = (x);                                    \
+    if (_e != cudaSuccess) return _e;                        \
+  } while (0)
+
+int64_t sq(int x) { return (int64_t)x * x; }
+
+// ---------------------------------------------------------------------------
+// One call's schedule.
+// ---------------------------------------------------------------------------
+struct Sweep {
+  negf_plan_s* p;
+  cudaStream_t st;
+  const double2* H;
+  const double2* sigL;
+  const double2* sigR;
+  int64_t sig_stride;
+  const double2* E;
+  double2* Gband;     // may be null
+  double2* G1N;       // may be null
+  int32_t* info;
+  int e0, ne;         // energy chunk
+
+  // Every kernel launch of the schedule goes through here so that the
+  // optional profiler can bracket it with events on the launching stream.
+  template <class F>
+  cudaError_t launch(int kind, double flops, F f) {
+    if (!p->profiling) return f();
+    negf_plan_s::Rec r{kind, flops, nullptr, nullptr};
+    NEGF_TRY(cudaEventCreate(&r.a));
+    NEGF_TRY(cudaEventCreate(&r.b));
+    NEGF_TRY(cudaEventRecord(r.a, st));
+    cudaError_t e = f();
+    NEGF_TRY(cudaEventRecord(r.b, st));
+    p->recs.push_back(r);
+    return e;
+  }
+  static double gemm_flops(const ZGemm& g) {
+    return 8.0 * g.m * (double)g.n * g.k * (g.reduce ? g.batch : g.batch);
+  }
+  cudaError_t gemm(ZGemm g) {
+    if (p->precision == NEGF_MIXED)
+      return launch(NEGF_PROF_GEMM_TC, gemm_flops(g), [&] { return negf::zgemm_tc(g, st); });
+    return launch(NEGF_PROF_GEMM_F64, gemm_flops(g), [&] { return negf::zgemm_f64(g, st); });
+  }
+  cudaError_t gemm64(ZGemm g) {
+    return launch(NEGF_PROF_GEMM_F64, gemm_flops(g), [&] { return negf::zgemm_f64(g, st); });
+  }
+  cudaError_t inv(const double2* S, int64_t sS, double2* T, int64_t sT, int b, int batch, int layer1) {
+    return launch(NEGF_PROF_INV, 8.0 * b * (double)b * b * batch, [&] {
+      return negf::zinv_f64(S, sS, T, sT, b, batch, info + e0, layer1, p->d_err, st);
+    });
+  }
+  template <class F>
+  cudaError_t misc(F f) { return launch(NEGF_PROF_MISC, 0.0, f); }
+  const double2* Hblk(int a, int bb) const { return H + p->band_off[(bb - a + p->w) * p->N + a]; }
+  double2* Tblk(int i) const { return p->T_ws + p->t_off[i] * p->chunk; }
+  double2* Xblk(int i, int c) const { return p->X_ws + p->x_off[i * p->w + (i - c - 1)] * p->chunk; }
+  double2* Yblk(int c, int i) const { return p->Y_ws + p->y_off[i * p->w + (i - c - 1)] * p->chunk; }
+  double2* Sslot(int a, int bb) const {
+    int r = p->w + 1;
+    return p->S_ws + (int64_t)((a % r) * r + (bb % r)) * p->s_slot * p->chunk;
+  }
+  double2* Gb(int a, int bb) const { return Gband + (int64_t)e0 * p->band_elems + p->band_off[(bb - a + p->w) * p->N + a]; }
+  const double2* sigma_for(int layer) const {
+    // Sigma_L on layer 0, Sigma_R on layer N-1 (both when N == 1 is handled by the caller)
+    const double2* s = layer == 0 ? sigL : sigR;
+    return s ? s + (sig_stride ? (int64_t)e0 * sig_stride : 0) : nullptr;
+  }
+
+  // Upward pass (Alg. 1 upward loop / Sec. 2.3): eliminate layers N-1 .. 0.
+  cudaError_t upward(bool need_x) {
+    const int N = p->N, w = p->w, C = ne;
+    std::map<std::pair<int, int>, bool> mat;   // S_ab materialized per energy
+    // S_{N-1,N-1} = E I - H - Sigma_R (- Sigma_L when N == 1)
+    {
+      int bl = p->b[N - 1];
+      double2* dst = Sslot(N - 1, N - 1);
+      NEGF_TRY(misc([&] {
+        return negf::assemble_diag(Hblk(N - 1, N - 1), E + e0, sigma_for(N - 1), sig_stride, dst, sq(bl), bl,
+                                   C, st);
+      }));
+      if (N == 1 && sigL) {
+        ZGemm g;   // dst -= Sigma_L : expressed as C = 1*dst - 1*SigmaL with an empty product
+        g.m = bl; g.n = bl; g.k = 0;
+        g.A = dst; g.B = dst; g.lda = bl; g.ldb = bl;
+        g.C = dst; g.sC = sq(bl); g.ldc = bl;
+        g.C1 = dst; g.sC1 = sq(bl); g.ldc1 = bl; g.beta1 = {1.0, 0.0};
+        g.C2 = sigma_for(0); g.sC2 = sig_stride; g.ldc2 = bl; g.beta2 = {-1.0, 0.0};
+        g.batch = C;
+        NEGF_TRY(gemm64(g));
+      }
+      mat[{N - 1, N - 1}] = true;
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      const int bi = p->b[i];
+      NEGF_TRY(inv(Sslot(i, i), sq(bi), Tblk(i), sq(bi), bi, C, i + 1));
+      const int lo = std::max(0, i - w);
+      for (int c = lo; c < i; ++c) {
+        const int bc = p->b[c];
+        const bool mic = mat.count({i, c}) > 0, mci = mat.count({c, i}) > 0;
+        if (need_x) {   // X_{i,c} = t_i S_{i,c}
+          ZGemm g;
+          g.m = bi; g.n = bc; g.k = bi;
+          g.A = Tblk(i); g.sA = sq(bi); g.lda = bi;
+          if (mic) { g.B = Sslot(i, c); g.sB = (int64_t)bi * bc; g.ldb = bc; g.alpha = {1.0, 0.0}; }
+          else { g.B = Hblk(i, c); g.sB = 0; g.ldb = bc; g.alpha = {-1.0, 0.0}; }
+          g.C = Xblk(i, c); g.sC = (int64_t)bi * bc; g.ldc = bc;
+          g.batch = C;
+          NEGF_TRY(gemm(g));
+        }
+        {   // Y_{c,i} = S_{c,i} t_i
+          ZGemm g;
+          g.m = bc; g.n = bi; g.k = bi;
+          if (mci) { g.A = Sslot(c, i); g.sA = (int64_t)bc * bi; g.lda = bi; g.alpha = {1.0, 0.0}; }
+          else { g.A = Hblk(c, i); g.sA = 0; g.lda = bi; g.alpha = {-1.0, 0.0}; }
+          g.B = Tblk(i); g.sB = sq(bi); g.ldb = bi;
+          g.C = Yblk(c, i); g.sC = (int64_t)bc * bi; g.ldc = bi;
+          g.batch = C;
+          NEGF_TRY(gemm(g));
+        }
+      }
+      // Window update S_ab -= Y_{a,i} S_{i,b}  (= S_{a,i} t_i S_{i,b}), a, b in [i-w, i-1]
+      for (int a = lo; a < i; ++a) {
+        for (int bb = lo; bb < i; ++bb) {
+          const int ba = p->b[a], bbs = p->b[bb];
+          const bool mib = mat.count({i, bb}) > 0, mab = mat.count({a, bb}) > 0;
+          ZGemm g;
+          g.m = ba; g.n = bbs; g.k = bi;
+          g.A = Yblk(a, i); g.sA = (int64_t)ba * bi; g.lda = bi;
+          if (mib) { g.B = Sslot(i, bb); g.sB = (int64_t)bi * bbs; g.ldb = bbs; g.alpha = {-1.0, 0.0}; }
+          else { g.B = Hblk(i, bb); g.sB = 0; g.ldb = bbs; g.alpha = {1.0, 0.0}; }
+          double2* out = Sslot(a, bb);
+          g.C = out; g.sC = (int64_t)ba * bbs; g.ldc = bbs;
+          if (mab) { g.C1 = out; g.sC1 = (int64_t)ba * bbs; g.ldc1 = bbs; g.beta1 = {1.0, 0.0}; }
+          else {
+            g.C1 = Hblk(a, bb); g.sC1 = 0; g.ldc1 = bbs; g.beta1 = {-1.0, 0.0};
+            if (a == bb) {
+              g.dshift = E + e0; g.sD = 1; g.gamma = {1.0, 0.0};
+              const double2* sg = nullptr;
+              if (a == 0) sg = sigma_for(0);
+              if (sg) { g.C2 = sg; g.sC2 = sig_stride; g.ldc2 = ba; g.beta2 = {-1.0, 0.0}; }
+            }
+          }
+          g.batch = C;
+          NEGF_TRY(gemm(g));
+          mat[{a, bb}] = true;
+        }
+      }
+    }
+    return cudaSuccess;
+  }
+
+  // Downward pass (Alg. 1 downward loop / Sec. 2.3), written into Gband.
+  cudaError_t downward() {
+    const int N = p->N, w = p->w, C = ne;
+    const int64_t sG = p->band_elems;
+    NEGF_TRY(misc([&] { return negf::copy_blocks(Tblk(0), sq(p->b[0]), Gb(0, 0), sG, sq(p->b[0]), C, st); }));
+    for (int i = 1; i < N; ++i) {
+      const int bi = p->b[i];
+      const int lo = std::max(0, i - w);
+      for (int a = lo; a < i; ++a) {     // G_{a,i} = -sum_c G_{a,c} Y_{c,i}
+        for (int c = lo; c < i; ++c) {
+          ZGemm g;
+          g.m = p->b[a]; g.n = bi; g.k = p->b[c];
+          g.A = Gb(a, c); g.sA = sG; g.lda = p->b[c];
+          g.B = Yblk(c, i); g.sB = (int64_t)p->b[c] * bi; g.ldb = bi;
+          g.C = Gb(a, i); g.sC = sG; g.ldc = bi; g.alpha = {-1.0, 0.0};
+          if (c > lo) { g.C1 = Gb(a, i); g.sC1 = sG; g.ldc1 = bi; g.beta1 = {1.0, 0.0}; }
+          g.batch = C;
+          NEGF_TRY(gemm(g));
+        }
+      }
+      for (int bb = lo; bb < i; ++bb) {  // G_{i,b} = -sum_c X_{i,c} G_{c,b}
+        for (int c = lo; c < i; ++c) {
+          ZGemm g;
+          g.m = bi; g.n = p->b[bb]; g.k = p->b[c];
+          g.A = Xblk(i, c); g.sA = (int64_t)bi * p->b[c]; g.lda = p->b[c];
+          g.B = Gb(c, bb); g.sB = sG; g.ldb = p->b[bb];
+          g.C = Gb(i, bb); g.sC = sG; g.ldc = p->b[bb]; g.alpha = {-1.0, 0.0};
+          if (c > lo) { g.C1 = Gb(i, bb); g.sC1 = sG; g.ldc1 = p->b[bb]; g.beta1 = {1.0, 0.0}; }
+          g.batch = C;
+          NEGF_TRY(gemm(g));
+        }
+      }
+      for (int c = lo; c < i; ++c) {     // G_ii = t_i - sum_c X_{i,c} G_{c,i}
+        ZGemm g;
+        g.m = bi; g.n = bi; g.k = p->b[c];
+        g.A = Xblk(i, c); g.sA = (int64_t)bi * p->b[c]; g.lda = p->b[c];
+        g.B = Gb(c, i); g.sB = sG; g.ldb = bi;
+        g.C = Gb(i, i); g.sC = sG; g.ldc = bi; g.alpha = {-1.0, 0.0};
+        if (c == lo) { g.C1 = Tblk(i); g.sC1 = sq(bi); g.ldc1 = bi; g.beta1 = {1.0, 0.0}; }
+        else { g.C1 = Gb(i, i); g.sC1 = sG; g.ldc1 = bi; g.beta1 = {1.0, 0.0}; }
+        g.batch = C;
+        NEGF_TRY(gemm(g));
+      }
+    }
+    return cudaSuccess;
+  }
+
+  // First block row G_{1,j} = -sum_c G_{1,c} Y_{c,j} (Eq. 4x4_exact_RGF, first
+  // row); R_ws holds either the whole row (gradient) or a ring of w + 1.
+  double2* Rblk(int j) const {
+    if (p->outputs & NEGF_OUT_GRAD) return p->R_ws + p->r_off[j] * p->chunk;
+    return p->R_ws + (int64_t)(j % (p->w + 1)) * (int64_t)p->b[0] * p->r_elems * p->chunk;
+  }
+  cudaError_t first_row(double2* g1n_out, int64_t s_out) {
+    const int N = p->N, w = p->w, C = ne;
+    const int b0 = p->b[0];
+    if (N == 1) return misc([&] { return negf::copy_blocks(Tblk(0), sq(b0), g1n_out, s_out, sq(b0), C, st); });
+    NEGF_TRY(misc([&] { return negf::copy_blocks(Tblk(0), sq(b0), Rblk(0), sq(b0), sq(b0), C, st); }));
+    for (int j = 1; j < N; ++j) {
+      const int bj = p->b[j];
+      const int lo = std::max(0, j - w);
+      const bool last = (j == N - 1);
+      double2* out = last ? g1n_out : Rblk(j);
+      const int64_t so = last ? s_out : (int64_t)b0 * bj;
+      for (int c = lo; c < j; ++c) {
+        ZGemm g;
+        g.m = b0; g.n = bj; g.k = p->b[c];
+        g.A = Rblk(c); g.sA = (int64_t)b0 * p->b[c]; g.lda = p->b[c];
+        g.B = Yblk(c, j); g.sB = (int64_t)p->b[c] * bj; g.ldb = bj;
+        g.C = out; g.sC = so; g.ldc = bj; g.alpha = {-1.0, 0.0};
+        if (c > lo) { g.C1 = out; g.sC1 = so; g.ldc1 = bj; g.beta1 = {1.0, 0.0}; }
+        g.batch = C;
+        NEGF_TRY(gemm(g));
+      }
+      if (last && (p->outputs & NEGF_OUT_GRAD))
+        NEGF_TRY(misc([&] { return negf::copy_blocks(out, so, Rblk(j), (int64_t)b0 * bj, (int64_t)b0 * bj, C, st); }));
+    }
+    return cudaSuccess;
+  }
+
+  // T(E) = Re Tr[Gamma_L G_1N Gamma_R G_1N^H] from G_1N (stride sG).
+  cudaError_t transmission(const double2* g1n, int64_t sG, double* T) {
+    const int C = ne, b0 = p->b[0], bN = p->b[p->N - 1];
+    double2* gL = p->scratch;
+    double2* gR = gL + sq(b0) * p->chunk;
+    double2* Pm = gR + sq(bN) * p->chunk;
+    double2* Qm = Pm + (int64_t)b0 * bN * p->chunk;
+    const int nsig = sig_stride ? C : 1;
+    NEGF_TRY(misc([&] { return negf::gamma_from_sigma(sigma_for(0), sig_stride, gL, sq(b0), b0, nsig, st); }));
+    NEGF_TRY(misc([&] { return negf::gamma_from_sigma(sigma_for(p->N - 1), sig_stride, gR, sq(bN), bN, nsig, st); }));
+    {   // P = Gamma_L G_1N
+      ZGemm g;
+      g.m = b0; g.n = bN; g.k = b0;
+      g.A = gL; g.sA = sig_stride ? sq(b0) : 0; g.lda = b0;
+      g.B = g1n; g.sB = sG; g.ldb = bN;
+      g.C = Pm; g.sC = (int64_t)b0 * bN; g.ldc = bN;
+      g.batch = C;
+      NEGF_TRY(gemm64(g));
+    }
+    {   // Q = Gamma_R G_1N^H
+      ZGemm g;
+      g.m = bN; g.n = b0; g.k = bN;
+      g.A = gR; g.sA = sig_stride ? sq(bN) : 0; g.lda = bN;
+      g.B = g1n; g.sB = sG; g.ldb = bN; g.opB = negf::OP_C;
+      g.C = Qm; g.sC = (int64_t)bN * b0; g.ldc = b0;
+      g.batch = C;
+      NEGF_TRY(gemm64(g));
+    }
+    return misc([&] { return negf::trace_prod(Pm, (int64_t)b0 * bN, Qm, (int64_t)bN * b0, b0, bN, T + e0, C, 1.0, 0, st); });
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Plan construction
+// ---------------------------------------------------------------------------
+negf_status validate(const negf_desc* d) {
+  if (!d) return NEGF_ERR_ARG;
+  if (d->n_blocks < 1 || !d->block_sizes) return NEGF_ERR_ARG;
+  if (d->band_n < 3 || (d->band_n % 2) == 0) return NEGF_ERR_ARG;
+  const int w = (d->band_n - 1) / 2;
+  if (d->n_blocks <= w && d->n_blocks > 1) return NEGF_ERR_ARG;
+  if (d->n_energies < 1) return NEGF_ERR_ARG;
+  if (d->n_domains < 1) return NEGF_ERR_ARG;
+  if (d->precision != NEGF_FP64 && d->precision != NEGF_MIXED) return NEGF_ERR_ARG;
+  if (d->refine_steps < 0 || d->refine_steps > 1) return NEGF_ERR_ARG;
+  if (d->outputs & ~(NEGF_OUT_BAND | NEGF_OUT_G1N | NEGF_OUT_TRANSMISSION | NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
+  if (d->checkpoint_every < 0) return NEGF_ERR_ARG;
+  for (int i = 0; i < d->n_blocks; ++i)
+    if (d->block_sizes[i] < 1 || d->block_sizes[i] > NEGF_MAX_BLOCK) return NEGF_ERR_ARG;
+  return NEGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* negf_status_string(negf_status s) {
+  switch (s) {
+    case NEGF_OK: return "NEGF_OK";
+    case NEGF_ERR_ARG: return "NEGF_ERR_ARG: invalid argument";
+    case NEGF_ERR_SINGULAR: return "NEGF_ERR_SINGULAR: zero pivot in a block inversion";
+    case NEGF_ERR_NONFINITE: return "NEGF_ERR_NONFINITE: non-finite pivot in a block inversion";
+    case NEGF_ERR_NOMEM: return "NEGF_ERR_NOMEM: workspace allocation failed";
+    case NEGF_ERR_CUDA: return "NEGF_ERR_CUDA: CUDA runtime error";
+    case NEGF_ERR_TIMEOUT: return "NEGF_ERR_TIMEOUT: bounded device wait expired";
+    case NEGF_ERR_UNSUPPORTED: return "NEGF_ERR_UNSUPPORTED: not implemented for this descriptor";
+  }
+  return "negf: unknown status";
+}
+
+negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) {
+  if (!out) return NEGF_ERR_ARG;
+  *out = nullptr;
+  negf_status v = validate(d);
+  if (v != NEGF_OK) return v;
+  const int w = (d->band_n - 1) / 2;
+  if (d->n_domains > 1) return NEGF_ERR_UNSUPPORTED;
+  if (d->precision == NEGF_MIXED && !negf::zgemm_tc_available()) return NEGF_ERR_UNSUPPORTED;
+  if ((d->outputs & NEGF_OUT_GRAD) && w != 1) return NEGF_ERR_UNSUPPORTED;
+  for (int i = 0; i < d->n_blocks; ++i)
+    if (d->block_sizes[i] > negf::zinv_max_block()) return NEGF_ERR_UNSUPPORTED;
+
+  negf_plan_s* p = new (std::nothrow) negf_plan_s();
+  if (!p) return NEGF_ERR_NOMEM;
+  p->N = d->n_blocks; p->w = w; p->nE = d->n_energies; p->n_domains = d->n_domains;
+  p->precision = d->precision; p->refine = d->refine_steps; p->outputs = d->outputs;
+  p->ckpt = d->checkpoint_every;
+  p->b.assign(d->block_sizes, d->block_sizes + d->n_blocks);
+  p->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&p->device);
+  const int N = p->N;
+
+  // band-packed offsets: d = -w..w outer, i inner, existing blocks only
+  p->band_off.assign((size_t)(2 * w + 1) * N, -1);
+  int64_t off = 0;
+  for (int dd = -w; dd <= w; ++dd)
+    for (int i = 0; i < N; ++i) {
+      int j = i + dd;
+      if (j < 0 || j >= N) continue;
+      p->band_off[(size_t)(dd + w) * N + i] = off;
+      off += (int64_t)p->b[i] * p->b[j];
+    }
+  p->band_elems = off;
+
+  // per-energy workspace layout
+  int bmax = *std::max_element(p->b.begin(), p->b.end());
+  p->t_off.resize(N); p->x_off.assign((size_t)N * w, 0); p->y_off.assign((size_t)N * w, 0);
+  int64_t te = 0, xe = 0, ye = 0;
+  for (int i = 0; i < N; ++i) {
+    p->t_off[i] = te; te += sq(p->b[i]);
+    for (int c = std::max(0, i - w); c < i; ++c) {
+      p->x_off[(size_t)i * w + (i - c - 1)] = xe; xe += (int64_t)p->b[i] * p->b[c];
+      p->y_off[(size_t)i * w + (i - c - 1)] = ye; ye += (int64_t)p->b[c] * p->b[i];
+    }
+  }
+  p->t_elems = te; p->x_elems = xe; p->y_elems = ye;
+  p->s_slot = sq(bmax);
+  const bool grad = (d->outputs & NEGF_OUT_GRAD) != 0;
+  p->r_off.resize(N);
+  int64_t re = 0;
+  for (int j = 0; j < N; ++j) { p->r_off[j] = re; re += (int64_t)p->b[0] * p->b[j]; }
+  p->r_elems = grad ? re : bmax;   // ring: (w+1) slots of b0 x bmax
+  const int bN = p->b[N - 1], b0 = p->b[0];
+  p->p_off.resize(N);
+  int64_t pe = 0;
+  for (int i = 0; i < N; ++i) { p->p_off[i] = pe; pe += (int64_t)p->b[i] * bN; }
+  p->p_elems = grad ? pe : 0;
+  p->scr_elems = sq(b0) + sq(bN) + 2 * (int64_t)b0 * bN + (int64_t)b0 * bN;
+
+  int64_t per_e = te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot +
+                  (grad ? re : (int64_t)(w + 1) * b0 * bmax) + 2 * p->p_elems + p->scr_elems;
+  // chunk energies so that the workspace stays within a budget
+  const int64_t budget_elems = (int64_t)(24.0 * (1ull << 30)) / (int64_t)sizeof(double2);
+  int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(p->nE, budget_elems / std::max<int64_t>(per_e, 1)));
+  p->chunk = chunk;
+  p->ws_bytes = (size_t)per_e * chunk * sizeof(double2) + 256;
+  cudaError_t err = cudaMalloc((void**)&p->ws, p->ws_bytes);
+  if (err != cudaSuccess) { cudaGetLastError(); delete p; return NEGF_ERR_NOMEM; }
+  err = cudaMalloc((void**)&p->d_err, sizeof(int) + sizeof(double) * (size_t)p->nE);
+  if (err != cudaSuccess) { cudaGetLastError(); cudaFree(p->ws); delete p; return NEGF_ERR_NOMEM; }
+  cudaMemset(p->d_err, 0, sizeof(int));
+  p->Tdummy = reinterpret_cast<double*>(p->d_err + 2);
+  double2* q = reinterpret_cast<double2*>(p->ws);
+  p->T_ws = q; q += te * chunk;
+  p->X_ws = q; q += xe * chunk;
+  p->Y_ws = q; q += ye * chunk;
+  p->S_ws = q; q += (int64_t)(w + 1) * (w + 1) * p->s_slot * chunk;
+  p->R_ws = q; q += (grad ? re : (int64_t)(w + 1) * b0 * bmax) * chunk;
+  p->P_ws = q; q += p->p_elems * chunk;
+  p->LC_ws = q; q += p->p_elems * chunk;
+  p->scratch = q; q += p->scr_elems * chunk;
+  p->G1N_ws = p->scratch + (sq(b0) + sq(bN) + 2 * (int64_t)b0 * bN) * chunk;
+  // one-time kernel attributes (kept out of graph capture)
+  if (negf::kernels_init() != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
+  *out = p;
+  return NEGF_OK;
+}
+
+size_t negf_workspace_bytes(const negf_plan_t* p) { return p ? p->ws_bytes : 0; }
+
+int64_t negf_band_offset(const negf_plan_t* p, int32_t d, int32_t i) {
+  if (!p || d < -p->w || d > p->w || i < 0 || i >= p->N) return -1;
+  return p->band_off[(size_t)(d + p->w) * p->N + i];
+}
+
+int64_t negf_band_elems(const negf_plan_t* p) { return p ? p->band_elems : -1; }
+
+void negf_destroy(negf_plan_t* p) {
+  if (!p) return;
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  cudaFree(p->ws);
+  cudaFree(p->d_err);
+  delete p;
+}
+
+negf_status negf_sync(negf_plan_t* p) {
+  if (!p) return NEGF_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return NEGF_ERR_CUDA;
+  int word = 0;
+  e = cudaMemcpy(&word, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return NEGF_ERR_CUDA;
+  if (word) cudaMemset(p->d_err, 0, sizeof(int));
+  if (word & negf::ERRBIT_NONFINITE) return NEGF_ERR_NONFINITE;
+  if (word & negf::ERRBIT_SINGULAR) return NEGF_ERR_SINGULAR;
+  if (word & negf::ERRBIT_TIMEOUT) return NEGF_ERR_TIMEOUT;
+  return NEGF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+enum CallKind { CALL_SOLVE = 1, CALL_TRANS = 2, CALL_GRAD = 3 };
+
+// Enqueue (or replay) the schedule of one call.  `body` enqueues the work of
+// every energy chunk on p->stream.
+template <class F>
+negf_status run_captured(negf_plan_s* p, const CallKey& key, F body) {
+  if (p->profiling) return cuda_status(body());
+  if (p->have_key && p->key == key && p->gexec) {
+    return cuda_status(cudaGraphLaunch(p->gexec, p->stream));
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return NEGF_ERR_CUDA;
+  cudaError_t be = body();
+  e = cudaStreamEndCapture(p->stream, &graph);
+  if (be != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return NEGF_ERR_CUDA;
+  }
+  if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+  e = cudaGraphInstantiate(&p->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) { p->gexec = nullptr; p->have_key = false; return NEGF_ERR_CUDA; }
+  p->key = key;
+  p->have_key = true;
+  return cuda_status(cudaGraphLaunch(p->gexec, p->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                       const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                       negf_c128* G_band, negf_c128* G_1N, int32_t* info) {
+  if (!p || !H || !E || !info || sigma_E_stride < 0) return NEGF_ERR_ARG;
+  if (!G_band && !G_1N) return NEGF_ERR_ARG;
+  if (p->precision == NEGF_MIXED) {
+    // mixed products are dispatched per launch; nothing else to check here
+  }
+  CallKey key{};
+  key.kind = CALL_SOLVE;
+  key.stride = sigma_E_stride;
+  const void* ptrs[] = {H, sigma_L, sigma_R, E, G_band, G_1N, info};
+  std::memcpy(key.p, ptrs, sizeof(ptrs));
+  return run_captured(p, key, [&]() -> cudaError_t {
+    NEGF_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * p->nE, p->stream));
+    for (int e0 = 0; e0 < p->nE; e0 += p->chunk) {
+      Sweep s{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
+              sigma_E_stride, (const double2*)E, (double2*)G_band, (double2*)G_1N, info,
+              e0, std::min(p->chunk, p->nE - e0)};
+      NEGF_TRY(s.upward(G_band != nullptr));
+      if (G_band) NEGF_TRY(s.downward());
+      if (G_1N) {
+        const int64_t s1 = (int64_t)p->b[0] * p->b[p->N - 1];
+        NEGF_TRY(s.first_row((double2*)G_1N + (int64_t)e0 * s1, s1));
+      }
+    }
+    return cudaSuccess;
+  });
+}
+
+negf_status negf_transmission(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                              const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                              double* T, int32_t* info) {
+  if (!p || !H || !E || !info || !T || !sigma_L || !sigma_R || sigma_E_stride < 0) return NEGF_ERR_ARG;
+  CallKey key{};
+  key.kind = CALL_TRANS;
+  key.stride = sigma_E_stride;
+  const void* ptrs[] = {H, sigma_L, sigma_R, E, T, info};
+  std::memcpy(key.p, ptrs, sizeof(ptrs));
+  return run_captured(p, key, [&]() -> cudaError_t {
+    NEGF_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * p->nE, p->stream));
+    const int64_t s1 = (int64_t)p->b[0] * p->b[p->N - 1];
+    for (int e0 = 0; e0 < p->nE; e0 += p->chunk) {
+      Sweep s{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
+              sigma_E_stride, (const double2*)E, nullptr, nullptr, info,
+              e0, std::min(p->chunk, p->nE - e0)};
+      NEGF_TRY(s.upward(false));
+      NEGF_TRY(s.first_row(p->G1N_ws, s1));
+      NEGF_TRY(s.transmission(p->G1N_ws, s1, T));
+    }
+    return cudaSuccess;
+  });
+}
+
+negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                      const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                      const double* dL_dT, double* T, negf_c128* dH, negf_c128* dSigma_L,
+                      negf_c128* dSigma_R, int32_t* info) {
+  (void)H; (void)sigma_L; (void)sigma_R; (void)sigma_E_stride; (void)E; (void)dL_dT; (void)T;
+  (void)dH; (void)dSigma_L; (void)dSigma_R; (void)info;
+  if (!p) return NEGF_ERR_ARG;
+  if (!(p->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
+  return NEGF_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+negf_status negf_profile_enable(negf_plan_t* p, int32_t on) {
+  if (!p) return NEGF_ERR_ARG;
+  p->profiling = on != 0;
+  return NEGF_OK;
+}
+
+int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* launches) {
+  if (!p) return -1;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return -1;
+  for (auto& r : p->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      p->prof_ms[r.kind] += t;
+      p->prof_flops[r.kind] += r.flops;
+      p->prof_launches[r.kind] += 1;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  p->recs.clear();
+  for (int k = 0; k < NEGF_PROF_KINDS; ++k) {
+    if (ms) ms[k] = p->prof_ms[k];
+    if (flops) flops[k] = p->prof_flops[k];
+    if (launches) launches[k] = p->prof_launches[k];
+    p->prof_ms[k] = 0; p->prof_flops[k] = 0; p->prof_launches[k] = 0;
+  }
+  return NEGF_PROF_KINDS;
+}
+
+}  // extern "C"

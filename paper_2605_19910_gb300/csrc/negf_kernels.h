@@ -1,0 +1,65 @@
+// Internal launch interface of the libnegf.so kernels (host side, C++).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace negf {
+
+// Operand access mode of a batched block product.
+enum Op : int { OP_N = 0, OP_C = 1 /* conjugate transpose */ };
+
+// One batched complex product over a batch of energies:
+//   C[e] = alpha * op(A[e]) op(B[e]) + beta1 * C1[e] + beta2 * C2[e]
+//          + gamma * dshift[e] * I
+// Every operand X[e] lives at X + e * sX (sX = 0 shares one block across the
+// batch); blocks are row-major with leading dimension ldX.  C1/C2/dshift may
+// be null.  With reduce != 0 the batch is summed into one C:
+//   C = alpha * sum_e weight[e] * op(A[e]) op(B[e]) + beta1 * C1.
+struct ZGemm {
+  int m = 0, n = 0, k = 0;
+  const double2* A = nullptr; int64_t sA = 0; int lda = 0; int opA = OP_N;
+  const double2* B = nullptr; int64_t sB = 0; int ldb = 0; int opB = OP_N;
+  double2* C = nullptr; int64_t sC = 0; int ldc = 0;
+  const double2* C1 = nullptr; int64_t sC1 = 0; int ldc1 = 0;
+  const double2* C2 = nullptr; int64_t sC2 = 0; int ldc2 = 0;
+  const double2* dshift = nullptr; int64_t sD = 1;
+  double2 alpha = {1.0, 0.0}, beta1 = {0.0, 0.0}, beta2 = {0.0, 0.0}, gamma = {0.0, 0.0};
+  const double* weight = nullptr;
+  int batch = 1;
+  int reduce = 0;
+};
+
+// FP64 product on the FP64 tensor path (mma.sync m8n8k4 f64).
+cudaError_t zgemm_f64(const ZGemm& g, cudaStream_t st);
+// FP32-accurate split product on the 5th-generation tensor cores.
+cudaError_t zgemm_tc(const ZGemm& g, cudaStream_t st);
+bool zgemm_tc_available();
+
+// One-time kernel attributes (shared-memory opt-in); call outside capture.
+cudaError_t kernels_init();
+
+// Batched in-place-capable FP64 inversion T[e] = S[e]^{-1} (b x b, row-major,
+// contiguous) by Gauss-Jordan elimination with partial pivoting.  On an
+// exactly zero or non-finite pivot: info[e] = layer1 if it was 0, and the
+// error word gets ERRBIT_SINGULAR / ERRBIT_NONFINITE.
+cudaError_t zinv_f64(const double2* S, int64_t sS, double2* T, int64_t sT, int b, int batch,
+                     int32_t* info, int layer1, int* errword, cudaStream_t st);
+int zinv_max_block();
+
+// D[e] = s_e * I - H - extra[e]  with s_e = E[e] (b x b, extra may be null).
+cudaError_t assemble_diag(const double2* H, const double2* E, const double2* extra, int64_t sExtra,
+                          double2* D, int64_t sD, int b, int batch, cudaStream_t st);
+
+// Strided batched block copy: dst[e] = src[e] (rows x cols, row-major, ld = cols).
+cudaError_t copy_blocks(const double2* src, int64_t sSrc, double2* dst, int64_t sDst, int64_t elems,
+                        int batch, cudaStream_t st);
+
+// Gam[e] = i (Sig[e] - Sig[e]^H)   (b x b).
+cudaError_t gamma_from_sigma(const double2* sig, int64_t sSig, double2* gam, int64_t sGam, int b,
+                             int batch, cudaStream_t st);
+
+// T[e] (+)= scale * Re sum_ij P[e]_ij Q[e]_ji  for P rows x cols, Q cols x rows.
+cudaError_t trace_prod(const double2* P, int64_t sP, const double2* Q, int64_t sQ, int rows, int cols,
+                       double* T, int batch, double scale, int accumulate, cudaStream_t st);
+
+}  // namespace negf

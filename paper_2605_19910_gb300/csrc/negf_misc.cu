@@ -1,0 +1,123 @@
+// Small element-wise kernels of the sweep: assembling the diagonal blocks of
+// M = E I - H - Sigma (Sec. 2), strided block copies, Gamma = i(Sigma -
+// Sigma^H) and the trace reduction of the transmission.
+#include "negf_common.cuh"
+#include "negf_kernels.h"
+
+namespace negf {
+
+namespace {
+
+__global__ void assemble_diag_kernel(const double2* __restrict__ H, const double2* __restrict__ E,
+                                     const double2* __restrict__ extra, int64_t sExtra,
+                                     double2* __restrict__ D, int64_t sD, int b) {
+  const int e = blockIdx.y;
+  const double2 en = E[e];
+  const int64_t n = (int64_t)b * b;
+  double2* d = D + (int64_t)e * sD;
+  const double2* x = extra ? extra + (int64_t)e * sExtra : nullptr;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(idx / b), c = (int)(idx - (int64_t)r * b);
+    double2 h = H[idx];
+    double2 v = make_double2(-h.x, -h.y);
+    if (r == c) { v.x += en.x; v.y += en.y; }
+    if (x) { v.x -= x[idx].x; v.y -= x[idx].y; }
+    d[idx] = v;
+  }
+}
+
+__global__ void copy_blocks_kernel(const double2* __restrict__ src, int64_t sSrc, double2* __restrict__ dst,
+                                   int64_t sDst, int64_t elems) {
+  const int e = blockIdx.y;
+  const double2* s = src + (int64_t)e * sSrc;
+  double2* d = dst + (int64_t)e * sDst;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < elems;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+
+__global__ void gamma_kernel(const double2* __restrict__ sig, int64_t sSig, double2* __restrict__ gam,
+                             int64_t sGam, int b) {
+  const int e = blockIdx.y;
+  const double2* s = sig + (int64_t)e * sSig;
+  double2* g = gam + (int64_t)e * sGam;
+  const int64_t n = (int64_t)b * b;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(idx / b), c = (int)(idx - (int64_t)r * b);
+    double2 a = s[idx];
+    double2 t = s[(int64_t)c * b + r];   // (Sigma^H)_{rc} = conj(Sigma_{cr})
+    // i * (a - conj(t)) = i * ((a.x - t.x) + i (a.y + t.y))
+    g[idx] = make_double2(-(a.y + t.y), a.x - t.x);
+  }
+}
+
+// One CTA per energy: T[e] = scale * Re sum_ij P_ij Q_ji.
+__global__ void trace_prod_kernel(const double2* __restrict__ P, int64_t sP, const double2* __restrict__ Q,
+                                  int64_t sQ, int rows, int cols, double* __restrict__ T, double scale,
+                                  int accumulate) {
+  const int e = blockIdx.x;
+  const double2* p = P + (int64_t)e * sP;
+  const double2* q = Q + (int64_t)e * sQ;
+  double acc = 0.0;
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    int i = (int)(idx / cols), j = (int)(idx - (int64_t)i * cols);
+    double2 a = p[idx];
+    double2 c = q[(int64_t)j * rows + i];
+    acc = fma(a.x, c.x, acc);
+    acc = fma(-a.y, c.y, acc);
+  }
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    acc = lane < nw ? red[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) T[e] = (accumulate ? T[e] : 0.0) + scale * acc;
+  }
+}
+
+inline int grid_x_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
+}
+
+}  // namespace
+
+cudaError_t assemble_diag(const double2* H, const double2* E, const double2* extra, int64_t sExtra,
+                          double2* D, int64_t sD, int b, int batch, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  dim3 grid(grid_x_for((int64_t)b * b, 256), batch);
+  assemble_diag_kernel<<<grid, 256, 0, st>>>(H, E, extra, sExtra, D, sD, b);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_blocks(const double2* src, int64_t sSrc, double2* dst, int64_t sDst, int64_t elems,
+                        int batch, cudaStream_t st) {
+  if (batch <= 0 || elems <= 0) return cudaSuccess;
+  dim3 grid(grid_x_for(elems, 256), batch);
+  copy_blocks_kernel<<<grid, 256, 0, st>>>(src, sSrc, dst, sDst, elems);
+  return cudaGetLastError();
+}
+
+cudaError_t gamma_from_sigma(const double2* sig, int64_t sSig, double2* gam, int64_t sGam, int b,
+                             int batch, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  dim3 grid(grid_x_for((int64_t)b * b, 256), batch);
+  gamma_kernel<<<grid, 256, 0, st>>>(sig, sSig, gam, sGam, b);
+  return cudaGetLastError();
+}
+
+cudaError_t trace_prod(const double2* P, int64_t sP, const double2* Q, int64_t sQ, int rows, int cols,
+                       double* T, int batch, double scale, int accumulate, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  trace_prod_kernel<<<batch, 256, 0, st>>>(P, sP, Q, sQ, rows, cols, T, scale, accumulate);
+  return cudaGetLastError();
+}
+
+}  // namespace negf
