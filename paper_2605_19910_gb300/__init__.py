@@ -265,7 +265,10 @@ class Plan:
         self.w = (band_n - 1) // 2
         self.band_n = band_n
         self.n_energies = int(n_energies)
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        # The plan runs on a stream of its own (graph capture needs a created
+        # stream); every call orders itself after the caller's current stream
+        # and makes the caller's stream wait for it.
+        self.stream = stream if stream is not None else torch.cuda.Stream()
         prec = {"fp64": NEGF_FP64, "mixed": NEGF_MIXED}[precision] if isinstance(precision, str) else precision
         self.handle = negf_plan(self.sizes, band_n, self.n_energies, n_domains, domain_first_block, prec,
                                 refine_steps, outputs, checkpoint_every, self.stream.cuda_stream)
@@ -287,6 +290,12 @@ class Plan:
         if status != NEGF_OK:
             raise NegfError(status, where)
 
+    def _enter(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+
+    def _leave(self):
+        self.torch.cuda.current_stream().wait_stream(self.stream)
+
     def sync(self):
         s = negf_sync(self.handle)
         if s != NEGF_OK:
@@ -306,7 +315,10 @@ class Plan:
         G1 = out_g1n if out_g1n is not None else (
             torch.empty(nE, b0, bN, dtype=torch.complex128, device="cuda") if g1n else None)
         stride = self._sig_stride(sigma_L, b0)
-        self._check(negf_solve(self.handle, H, sigma_L, sigma_R, stride, E, Gb, G1, self.info), "negf_solve")
+        self._enter()
+        st = negf_solve(self.handle, H, sigma_L, sigma_R, stride, E, Gb, G1, self.info)
+        self._leave()
+        self._check(st, "negf_solve")
         if sync:
             self.sync()
         return Gb, G1
@@ -315,8 +327,10 @@ class Plan:
         torch = self.torch
         T = out if out is not None else torch.empty(self.n_energies, dtype=torch.float64, device="cuda")
         stride = self._sig_stride(sigma_L, self.sizes[0])
-        self._check(negf_transmission(self.handle, H, sigma_L, sigma_R, stride, E, T, self.info),
-                    "negf_transmission")
+        self._enter()
+        st = negf_transmission(self.handle, H, sigma_L, sigma_R, stride, E, T, self.info)
+        self._leave()
+        self._check(st, "negf_transmission")
         if sync:
             self.sync()
         return T
@@ -329,8 +343,11 @@ class Plan:
         dSL = torch.empty_like(sigma_L)
         dSR = torch.empty_like(sigma_R)
         stride = self._sig_stride(sigma_L, self.sizes[0])
-        self._check(negf_grad(self.handle, H, sigma_L, sigma_R, stride, E, dL_dT.contiguous(), T, dH, dSL, dSR,
-                              self.info), "negf_grad")
+        dL = dL_dT.contiguous()
+        self._enter()
+        st = negf_grad(self.handle, H, sigma_L, sigma_R, stride, E, dL, T, dH, dSL, dSR, self.info)
+        self._leave()
+        self._check(st, "negf_grad")
         if sync:
             self.sync()
         return T, dH, dSL, dSR

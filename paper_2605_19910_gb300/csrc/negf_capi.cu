@@ -522,7 +522,10 @@ enum CallKind { CALL_SOLVE = 1, CALL_TRANS = 2, CALL_GRAD = 3 };
 // every energy chunk on p->stream.
 template <class F>
 negf_status run_captured(negf_plan_s* p, const CallKey& key, F body) {
-  if (p->profiling) return cuda_status(body());
+  // Graph capture needs a created stream; on the legacy default stream, or
+  // while profiling, the schedule is launched directly.
+  if (p->profiling || p->stream == nullptr || p->stream == cudaStreamLegacy || p->stream == cudaStreamPerThread)
+    return cuda_status(body());
   if (p->have_key && p->key == key && p->gexec) {
     return cuda_status(cudaGraphLaunch(p->gexec, p->stream));
   }
