@@ -174,6 +174,10 @@ enum { NEGF_PROF_INV = 0, NEGF_PROF_GEMM_F64 = 1, NEGF_PROF_GEMM_TC = 2, NEGF_PR
 negf_status negf_profile_enable(negf_plan_t* p, int32_t on);
 int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* launches);
 
+/* Text of the last CUDA runtime error this thread's calls met (for
+ * NEGF_ERR_CUDA diagnostics); "no error" if none. */
+const char* negf_last_cuda_error(void);
+
 /* Static, human-readable name of a status code. */
 const char* negf_status_string(negf_status s);
 

@@ -50,14 +50,17 @@ PROF_NAMES = ["zinv_gj_kernel", "zgemm_f64_kernel", "zgemm_tc_kernel", "misc"]
 EXPORTED = [
     "negf_plan", "negf_workspace_bytes", "negf_band_offset", "negf_band_elems", "negf_solve",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
-    "negf_profile_enable", "negf_profile_read",
+    "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error",
 ]
 
 
 class NegfError(RuntimeError):
     def __init__(self, status, where=""):
         self.status = int(status)
-        super().__init__(f"{where}: {negf_status_string(status)} ({status})")
+        extra = ""
+        if self.status == NEGF_ERR_CUDA:
+            extra = f" [{_lib.negf_last_cuda_error().decode()}]"
+        super().__init__(f"{where}: {negf_status_string(status)} ({status}){extra}")
 
 
 class negf_desc(ctypes.Structure):
@@ -106,6 +109,8 @@ def _load():
     lp = ctypes.POINTER(ctypes.c_int64)
     lib.negf_profile_read.argtypes = [vp, dp, dp, lp]
     lib.negf_profile_read.restype = i32
+    lib.negf_last_cuda_error.argtypes = []
+    lib.negf_last_cuda_error.restype = ctypes.c_char_p
     lib.negf_status_string.argtypes = [st]
     lib.negf_status_string.restype = ctypes.c_char_p
     return lib

@@ -87,7 +87,12 @@ struct negf_plan_s {
 
 namespace {
 
-inline negf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA; }
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+inline negf_status cuda_status(cudaError_t e) {
+  if (e != cudaSuccess) g_last_cuda = e;
+  return e == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
+}
 
 #define NEGF_TRY(x)                                          \
   do {                                                       \
@@ -402,6 +407,10 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   if (d->n_domains > 1) return NEGF_ERR_UNSUPPORTED;
   if (d->precision == NEGF_MIXED && !negf::zgemm_tc_available()) return NEGF_ERR_UNSUPPORTED;
   if ((d->outputs & NEGF_OUT_GRAD) && w != 1) return NEGF_ERR_UNSUPPORTED;
+  {
+    cudaError_t ie = negf::kernels_init();
+    if (ie != cudaSuccess) { g_last_cuda = ie; return NEGF_ERR_CUDA; }
+  }
   for (int i = 0; i < d->n_blocks; ++i)
     if (d->block_sizes[i] > negf::zinv_max_block()) return NEGF_ERR_UNSUPPORTED;
 
@@ -460,7 +469,7 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   p->chunk = chunk;
   p->ws_bytes = (size_t)per_e * chunk * sizeof(double2) + 256;
   cudaError_t err = cudaMalloc((void**)&p->ws, p->ws_bytes);
-  if (err != cudaSuccess) { cudaGetLastError(); delete p; return NEGF_ERR_NOMEM; }
+  if (err != cudaSuccess) { g_last_cuda = err; cudaGetLastError(); delete p; return NEGF_ERR_NOMEM; }
   err = cudaMalloc((void**)&p->d_err, sizeof(int) + sizeof(double) * (size_t)p->nE);
   if (err != cudaSuccess) { cudaGetLastError(); cudaFree(p->ws); delete p; return NEGF_ERR_NOMEM; }
   cudaMemset(p->d_err, 0, sizeof(int));
@@ -476,12 +485,17 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   p->scratch = q; q += p->scr_elems * chunk;
   p->G1N_ws = p->scratch + (sq(b0) + sq(bN) + 2 * (int64_t)b0 * bN) * chunk;
   // one-time kernel attributes (kept out of graph capture)
-  if (negf::kernels_init() != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
+  {
+    cudaError_t ie = negf::kernels_init();
+    if (ie != cudaSuccess) { g_last_cuda = ie; negf_destroy(p); return NEGF_ERR_CUDA; }
+  }
   *out = p;
   return NEGF_OK;
 }
 
 size_t negf_workspace_bytes(const negf_plan_t* p) { return p ? p->ws_bytes : 0; }
+
+const char* negf_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
 
 int64_t negf_band_offset(const negf_plan_t* p, int32_t d, int32_t i) {
   if (!p || d < -p->w || d > p->w || i < 0 || i >= p->N) return -1;
@@ -535,6 +549,7 @@ negf_status run_captured(negf_plan_s* p, const CallKey& key, F body) {
   cudaError_t be = body();
   e = cudaStreamEndCapture(p->stream, &graph);
   if (be != cudaSuccess || e != cudaSuccess) {
+    g_last_cuda = be != cudaSuccess ? be : e;
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
     return NEGF_ERR_CUDA;

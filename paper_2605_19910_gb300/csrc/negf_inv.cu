@@ -120,13 +120,28 @@ size_t inv_smem_bytes(int b) {
 
 }  // namespace
 
+static size_t g_inv_dyn_max = 0;   // dynamic shared memory opt-in of the kernel
+
 cudaError_t zinv_init() {
-  return cudaFuncSetAttribute(zinv_gj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, zinv_gj_kernel);
+  if (e != cudaSuccess) return e;
+  size_t dyn = (size_t)optin - fa.sharedSizeBytes;
+  e = cudaFuncSetAttribute(zinv_gj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e != cudaSuccess) return e;
+  g_inv_dyn_max = dyn;
+  return cudaSuccess;
 }
 
 int zinv_max_block() {
+  size_t lim = g_inv_dyn_max ? g_inv_dyn_max : (size_t)227 * 1024 - 1024;
   int b = 1;
-  while (inv_smem_bytes(b + 1) <= 227 * 1024) ++b;
+  while (inv_smem_bytes(b + 1) <= lim) ++b;
   return b;
 }
 
@@ -134,7 +149,7 @@ cudaError_t zinv_f64(const double2* S, int64_t sS, double2* T, int64_t sT, int b
                      int32_t* info, int layer1, int* errword, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   size_t sm = inv_smem_bytes(b);
-  if (sm > 227 * 1024) return cudaErrorInvalidValue;
+  if (sm > g_inv_dyn_max) return cudaErrorInvalidValue;
   zinv_gj_kernel<<<batch, dim3(INV_TX, INV_TY), sm, st>>>(S, sS, T, sT, b, info, layer1, errword);
   return cudaGetLastError();
 }
