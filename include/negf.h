@@ -174,6 +174,40 @@ enum { NEGF_PROF_INV = 0, NEGF_PROF_GEMM_F64 = 1, NEGF_PROF_GEMM_TC = 2, NEGF_PR
 negf_status negf_profile_enable(negf_plan_t* p, int32_t on);
 int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* launches);
 
+/* negf_solve for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this entry point exists for embedding.  Some
+ * callers cannot call cudaMalloc: code that runs while another component owns
+ * all device memory through its own pool, code whose memory budget is fixed
+ * before it runs, and loops that must not pay the device-wide
+ * synchronisation an allocation can cause.  This call creates no plan and
+ * allocates nothing on the device: its scratch (the per-block inverses, the
+ * multipliers of the sweep and the running Schur complement) lives in one
+ * file-scope device array of NEGF_NOALLOC_SCRATCH_BYTES bytes, which every
+ * GPU that loads the library holds until the process exits.
+ *
+ * Arguments are those of negf_plan plus negf_solve, with the descriptor in
+ * place of a plan: FP64 only, n_domains == 1, no NEGF_OUT_GRAD (otherwise
+ * NEGF_ERR_UNSUPPORTED).  The caller passes device inputs and outputs as for
+ * negf_solve.  If the scratch this descriptor needs,
+ *   256 + 16 * n_energies * (sum_i b_i^2 + 2 * sum_{|i-j|=1..w, i>j} b_i b_j
+ *                            + (w+1)^2 * bmax^2 + (w+1) * b_1 * bmax)  bytes,
+ * exceeds NEGF_NOALLOC_SCRATCH_BYTES, the call returns NEGF_ERR_ARG before
+ * launching anything.  Work is enqueued on cuda_stream without a CUDA graph.
+ * Numerical failures are reported only through info[] (there is no plan to
+ * negf_sync).
+ *
+ * The first call on each device sets that device up (it looks up the device
+ * address of the scratch array and sets kernel attributes); make that first
+ * call before any stream capture.  Every call shares the one array and
+ * leaves its contents behind: calls that overlap on the GPU (on different
+ * streams, or from different host threads) race on it and must be
+ * serialised by the caller. */
+#define NEGF_NOALLOC_SCRATCH_BYTES (32u << 20)
+negf_status negf_solve_noalloc(const negf_desc* d, const negf_c128* H, const negf_c128* sigma_L,
+                               const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                               negf_c128* G_band, negf_c128* G_1N, int32_t* info, void* cuda_stream);
+
 /* Text of the last CUDA runtime error this thread's calls met (for
  * NEGF_ERR_CUDA diagnostics); "no error" if none. */
 const char* negf_last_cuda_error(void);

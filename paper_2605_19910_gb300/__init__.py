@@ -50,8 +50,10 @@ PROF_NAMES = ["zinv_gj_kernel", "zgemm_f64_kernel", "zgemm_tc_kernel", "misc"]
 EXPORTED = [
     "negf_plan", "negf_workspace_bytes", "negf_band_offset", "negf_band_elems", "negf_solve",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
-    "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error",
+    "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
 ]
+
+NEGF_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class NegfError(RuntimeError):
@@ -109,6 +111,8 @@ def _load():
     lp = ctypes.POINTER(ctypes.c_int64)
     lib.negf_profile_read.argtypes = [vp, dp, dp, lp]
     lib.negf_profile_read.restype = i32
+    lib.negf_solve_noalloc.argtypes = [ctypes.POINTER(negf_desc), vp, vp, vp, i64, vp, vp, vp, vp, vp]
+    lib.negf_solve_noalloc.restype = st
     lib.negf_last_cuda_error.argtypes = []
     lib.negf_last_cuda_error.restype = ctypes.c_char_p
     lib.negf_status_string.argtypes = [st]
@@ -161,6 +165,25 @@ def negf_plan(block_sizes, band_n=3, n_energies=1, n_domains=1, domain_first_blo
     if s != NEGF_OK:
         raise NegfError(s, "negf_plan")
     return h.value
+
+
+def negf_solve_noalloc(block_sizes, band_n, n_energies, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N,
+                       info, stream=None, outputs=NEGF_OUT_BAND | NEGF_OUT_G1N):
+    """negf_solve without a plan and without any device allocation (scratch in
+    a fixed device array of NEGF_NOALLOC_SCRATCH_BYTES).  Returns the status."""
+    sizes = (ctypes.c_int32 * len(block_sizes))(*[int(b) for b in block_sizes])
+    d = negf_desc()
+    d.n_blocks = len(block_sizes)
+    d.block_sizes = sizes
+    d.band_n = band_n
+    d.n_energies = n_energies
+    d.n_domains = 1
+    d.precision = NEGF_FP64
+    d.refine_steps = 0
+    d.outputs = outputs
+    d.checkpoint_every = 0
+    return _lib.negf_solve_noalloc(ctypes.byref(d), _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride),
+                                   _ptr(E), _ptr(G_band), _ptr(G_1N), _ptr(info), stream)
 
 
 def negf_workspace_bytes(plan):

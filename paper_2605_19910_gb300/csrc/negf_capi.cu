@@ -666,3 +666,110 @@ int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* la
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// negf_solve_noalloc: negf_solve for callers that cannot allocate device
+// memory.  The sweep's scratch lives in one file-scope device array that
+// every GPU loading this library holds until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NEGF_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+// Device address of g_noalloc_scratch per device ordinal.  The host-side
+// symbol g_noalloc_scratch is only a stand-in: kernels must receive this.
+void* g_noalloc_base[kNoallocMaxDevices] = {};
+}  // namespace
+
+extern "C" negf_status negf_solve_noalloc(const negf_desc* d, const negf_c128* H, const negf_c128* sigma_L,
+                                          const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                                          negf_c128* G_band, negf_c128* G_1N, int32_t* info, void* cuda_stream) {
+  negf_status v = validate(d);
+  if (v != NEGF_OK) return v;
+  if (!H || !E || !info || sigma_E_stride < 0 || (!G_band && !G_1N)) return NEGF_ERR_ARG;
+  if (d->n_domains != 1 || d->precision != NEGF_FP64 || (d->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_UNSUPPORTED;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { g_last_cuda = e; return NEGF_ERR_CUDA; }
+  if (dev < 0 || dev >= kNoallocMaxDevices) return NEGF_ERR_UNSUPPORTED;
+  void* base = nullptr;
+  {
+    // One-time set-up per device, with that device current (first call).
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) { g_last_cuda = e; return NEGF_ERR_CUDA; }
+      e = negf::kernels_init();
+      if (e != cudaSuccess) { g_last_cuda = e; return NEGF_ERR_CUDA; }
+      g_noalloc_base[dev] = ptr;
+    }
+    base = g_noalloc_base[dev];
+  }
+  const int w = (d->band_n - 1) / 2;
+  for (int i = 0; i < d->n_blocks; ++i)
+    if (d->block_sizes[i] > negf::zinv_max_block()) return NEGF_ERR_UNSUPPORTED;
+
+  // Host-side layout of the same schedule as a plan, all energies in one
+  // chunk, with every workspace region placed inside the static scratch.
+  negf_plan_s p;
+  p.N = d->n_blocks; p.w = w; p.nE = d->n_energies; p.n_domains = 1;
+  p.precision = NEGF_FP64; p.refine = 0; p.outputs = d->outputs; p.ckpt = 0;
+  p.b.assign(d->block_sizes, d->block_sizes + d->n_blocks);
+  p.stream = (cudaStream_t)cuda_stream;
+  p.device = dev;
+  const int N = p.N;
+  p.band_off.assign((size_t)(2 * w + 1) * N, -1);
+  int64_t off = 0;
+  for (int dd = -w; dd <= w; ++dd)
+    for (int i = 0; i < N; ++i) {
+      int j = i + dd;
+      if (j < 0 || j >= N) continue;
+      p.band_off[(size_t)(dd + w) * N + i] = off;
+      off += (int64_t)p.b[i] * p.b[j];
+    }
+  p.band_elems = off;
+  const int bmax = *std::max_element(p.b.begin(), p.b.end());
+  p.t_off.resize(N); p.x_off.assign((size_t)N * w, 0); p.y_off.assign((size_t)N * w, 0);
+  int64_t te = 0, xe = 0, ye = 0;
+  for (int i = 0; i < N; ++i) {
+    p.t_off[i] = te; te += sq(p.b[i]);
+    for (int c = std::max(0, i - w); c < i; ++c) {
+      p.x_off[(size_t)i * w + (i - c - 1)] = xe; xe += (int64_t)p.b[i] * p.b[c];
+      p.y_off[(size_t)i * w + (i - c - 1)] = ye; ye += (int64_t)p.b[c] * p.b[i];
+    }
+  }
+  p.s_slot = sq(bmax);
+  p.r_elems = bmax;
+  const int64_t ring = (int64_t)(w + 1) * p.b[0] * bmax;
+  const int64_t per_e = te + xe + ye + (int64_t)(w + 1) * (w + 1) * p.s_slot + ring;
+  const int64_t C = p.nE;
+  const size_t need = 256 + (size_t)per_e * (size_t)C * sizeof(double2);
+  if (need > (size_t)NEGF_NOALLOC_SCRATCH_BYTES) return NEGF_ERR_ARG;
+  p.chunk = (int)C;
+  p.d_err = reinterpret_cast<int*>(base);                      // first 256 bytes: error word
+  double2* q = reinterpret_cast<double2*>(static_cast<char*>(base) + 256);
+  p.T_ws = q; q += te * C;
+  p.X_ws = q; q += xe * C;
+  p.Y_ws = q; q += ye * C;
+  p.S_ws = q; q += (int64_t)(w + 1) * (w + 1) * p.s_slot * C;
+  p.R_ws = q;
+
+  // The scratch keeps the previous call's contents: only the error word must
+  // start at zero (every workspace block is written before it is read).
+  cudaStream_t st = p.stream;
+  e = cudaMemsetAsync(p.d_err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(info, 0, sizeof(int32_t) * (size_t)p.nE, st);
+  if (e == cudaSuccess) {
+    Sweep s{&p, st, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R, sigma_E_stride,
+            (const double2*)E, (double2*)G_band, (double2*)G_1N, info, 0, p.nE};
+    e = s.upward(G_band != nullptr);
+    if (e == cudaSuccess && G_band) e = s.downward();
+    if (e == cudaSuccess && G_1N) e = s.first_row((double2*)G_1N, (int64_t)p.b[0] * p.b[N - 1]);
+  }
+  if (e != cudaSuccess) { g_last_cuda = e; return NEGF_ERR_CUDA; }
+  return NEGF_OK;
+}
