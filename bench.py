@@ -42,6 +42,9 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-energies", type=int, default=96,
                     help="energies of the bounded CPU-oracle sample")
+    ap.add_argument("--n-blocks", type=int, default=None, help="override the workload's block count")
+    ap.add_argument("--n-energies", type=int, default=None, help="override the workload's energy count")
+    ap.add_argument("--block-size", type=int, default=None, help="override the workload's block size")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -142,6 +145,17 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def _overrides(a):
+    over = {}
+    if a.n_blocks:
+        over["n_blocks"] = a.n_blocks
+    if a.n_energies:
+        over["n_energies"] = a.n_energies
+    if a.block_size:
+        over["b"] = a.block_size
+    return over
+
+
 def run_ours(a, rank, world, local_rank):
     import numpy as np
     pool = None
@@ -159,7 +173,7 @@ def run_ours(a, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    prob = workload(a.workload)
+    prob = workload(a.workload, **_overrides(a))
     if world > 1 and rank > 0:
         prob.energies = prob.energies + 1e-3 * rank      # each rank its own energy grid
     N, nE = prob.n_blocks, len(prob.energies)

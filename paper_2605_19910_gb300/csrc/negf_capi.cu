@@ -10,6 +10,7 @@
 // the caller's pointers stay the same.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -71,6 +72,11 @@ struct negf_plan_s {
   double2* G1N_ws = nullptr;    // G_1N when the caller does not keep it
   double* Tdummy = nullptr;
 
+  // independent energy groups run on forked streams (graph branches)
+  int groups = 2;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;   // [0] fork, [1..] joins
+
   // optional per-launch timing (negf_profile_enable)
   bool profiling = false;
   struct Rec { int kind; double flops; cudaEvent_t a, b; };
@@ -116,7 +122,8 @@ struct Sweep {
   double2* Gband;     // may be null
   double2* G1N;       // may be null
   int32_t* info;
-  int e0, ne;         // energy chunk
+  int e0, ne;         // energy range of this sweep
+  int wofs = 0;       // energy offset of this range inside the chunk workspace
 
   // Every kernel launch of the schedule goes through here so that the
   // optional profiler can bracket it with events on the launching stream.
@@ -136,6 +143,7 @@ struct Sweep {
     return 8.0 * g.m * (double)g.n * g.k * (g.reduce ? g.batch : g.batch);
   }
   cudaError_t gemm(ZGemm g) {
+    g.errword = p->d_err;
     if (p->precision == NEGF_MIXED)
       return launch(NEGF_PROF_GEMM_TC, gemm_flops(g), [&] { return negf::zgemm_tc(g, st); });
     return launch(NEGF_PROF_GEMM_F64, gemm_flops(g), [&] { return negf::zgemm_f64(g, st); });
@@ -151,12 +159,17 @@ struct Sweep {
   template <class F>
   cudaError_t misc(F f) { return launch(NEGF_PROF_MISC, 0.0, f); }
   const double2* Hblk(int a, int bb) const { return H + p->band_off[(bb - a + p->w) * p->N + a]; }
-  double2* Tblk(int i) const { return p->T_ws + p->t_off[i] * p->chunk; }
-  double2* Xblk(int i, int c) const { return p->X_ws + p->x_off[i * p->w + (i - c - 1)] * p->chunk; }
-  double2* Yblk(int c, int i) const { return p->Y_ws + p->y_off[i * p->w + (i - c - 1)] * p->chunk; }
+  double2* Tblk(int i) const { return p->T_ws + p->t_off[i] * p->chunk + (int64_t)wofs * sq(p->b[i]); }
+  double2* Xblk(int i, int c) const {
+    return p->X_ws + p->x_off[i * p->w + (i - c - 1)] * p->chunk + (int64_t)wofs * p->b[i] * p->b[c];
+  }
+  double2* Yblk(int c, int i) const {
+    return p->Y_ws + p->y_off[i * p->w + (i - c - 1)] * p->chunk + (int64_t)wofs * p->b[c] * p->b[i];
+  }
   double2* Sslot(int a, int bb) const {
     int r = p->w + 1;
-    return p->S_ws + (int64_t)((a % r) * r + (bb % r)) * p->s_slot * p->chunk;
+    return p->S_ws + (int64_t)((a % r) * r + (bb % r)) * p->s_slot * p->chunk +
+           (int64_t)wofs * p->b[a] * p->b[bb];
   }
   double2* Gb(int a, int bb) const { return Gband + (int64_t)e0 * p->band_elems + p->band_off[(bb - a + p->w) * p->N + a]; }
   const double2* sigma_for(int layer) const {
@@ -298,8 +311,9 @@ struct Sweep {
   // First block row G_{1,j} = -sum_c G_{1,c} Y_{c,j} (Eq. 4x4_exact_RGF, first
   // row); R_ws holds either the whole row (gradient) or a ring of w + 1.
   double2* Rblk(int j) const {
-    if (p->outputs & NEGF_OUT_GRAD) return p->R_ws + p->r_off[j] * p->chunk;
-    return p->R_ws + (int64_t)(j % (p->w + 1)) * (int64_t)p->b[0] * p->r_elems * p->chunk;
+    const int64_t o = (int64_t)wofs * p->b[0] * p->b[j];
+    if (p->outputs & NEGF_OUT_GRAD) return p->R_ws + p->r_off[j] * p->chunk + o;
+    return p->R_ws + (int64_t)(j % (p->w + 1)) * (int64_t)p->b[0] * p->r_elems * p->chunk + o;
   }
   cudaError_t first_row(double2* g1n_out, int64_t s_out) {
     const int N = p->N, w = p->w, C = ne;
@@ -331,10 +345,10 @@ struct Sweep {
   // T(E) = Re Tr[Gamma_L G_1N Gamma_R G_1N^H] from G_1N (stride sG).
   cudaError_t transmission(const double2* g1n, int64_t sG, double* T) {
     const int C = ne, b0 = p->b[0], bN = p->b[p->N - 1];
-    double2* gL = p->scratch;
-    double2* gR = gL + sq(b0) * p->chunk;
-    double2* Pm = gR + sq(bN) * p->chunk;
-    double2* Qm = Pm + (int64_t)b0 * bN * p->chunk;
+    double2* gL = p->scratch + (int64_t)wofs * sq(b0);
+    double2* gR = p->scratch + sq(b0) * p->chunk + (int64_t)wofs * sq(bN);
+    double2* Pm = p->scratch + (sq(b0) + sq(bN)) * p->chunk + (int64_t)wofs * b0 * bN;
+    double2* Qm = p->scratch + (sq(b0) + sq(bN) + (int64_t)b0 * bN) * p->chunk + (int64_t)wofs * b0 * bN;
     const int nsig = sig_stride ? C : 1;
     NEGF_TRY(misc([&] { return negf::gamma_from_sigma(sigma_for(0), sig_stride, gL, sq(b0), b0, nsig, st); }));
     NEGF_TRY(misc([&] { return negf::gamma_from_sigma(sigma_for(p->N - 1), sig_stride, gR, sq(bN), bN, nsig, st); }));
@@ -489,6 +503,21 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
     cudaError_t ie = negf::kernels_init();
     if (ie != cudaSuccess) { g_last_cuda = ie; negf_destroy(p); return NEGF_ERR_CUDA; }
   }
+  {
+    const char* env = getenv("NEGF_STREAMS");
+    if (env) p->groups = std::max(1, std::min(8, atoi(env)));
+    p->groups = std::min(p->groups, p->chunk);
+    for (int g = 1; g < p->groups; ++g) {
+      cudaStream_t s2 = nullptr;
+      if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
+      p->side.push_back(s2);
+    }
+    for (int g = 0; g < p->groups; ++g) {
+      cudaEvent_t e2 = nullptr;
+      if (cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
+      p->ev.push_back(e2);
+    }
+  }
   *out = p;
   return NEGF_OK;
 }
@@ -507,6 +536,8 @@ int64_t negf_band_elems(const negf_plan_t* p) { return p ? p->band_elems : -1; }
 void negf_destroy(negf_plan_t* p) {
   if (!p) return;
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  for (auto s2 : p->side) cudaStreamDestroy(s2);
+  for (auto e2 : p->ev) cudaEventDestroy(e2);
   cudaFree(p->ws);
   cudaFree(p->d_err);
   delete p;
@@ -531,6 +562,31 @@ negf_status negf_sync(negf_plan_t* p) {
 namespace {
 
 enum CallKind { CALL_SOLVE = 1, CALL_TRANS = 2, CALL_GRAD = 3 };
+
+// Splits the energies [e0, e0 + ne) of one chunk into p->groups independent
+// ranges, forks them onto the plan's side streams and joins them back, so
+// that one range's block products run while another range inverts.
+template <class F>
+cudaError_t for_groups(negf_plan_s* p, Sweep base, F f) {
+  const int G = std::min(p->groups, base.ne);
+  if (G <= 1) return f(base);
+  NEGF_TRY(cudaEventRecord(p->ev[0], p->stream));
+  for (int g = 1; g < G; ++g) NEGF_TRY(cudaStreamWaitEvent(p->side[g - 1], p->ev[0], 0));
+  for (int g = 0; g < G; ++g) {
+    const int lo = (int)((int64_t)base.ne * g / G), hi = (int)((int64_t)base.ne * (g + 1) / G);
+    Sweep s = base;
+    s.st = g == 0 ? p->stream : p->side[g - 1];
+    s.e0 = base.e0 + lo;
+    s.ne = hi - lo;
+    s.wofs = base.wofs + lo;
+    NEGF_TRY(f(s));
+  }
+  for (int g = 1; g < G; ++g) {
+    NEGF_TRY(cudaEventRecord(p->ev[g], p->side[g - 1]));
+    NEGF_TRY(cudaStreamWaitEvent(p->stream, p->ev[g], 0));
+  }
+  return cudaSuccess;
+}
 
 // Enqueue (or replay) the schedule of one call.  `body` enqueues the work of
 // every energy chunk on p->stream.
@@ -583,15 +639,18 @@ negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigm
   return run_captured(p, key, [&]() -> cudaError_t {
     NEGF_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * p->nE, p->stream));
     for (int e0 = 0; e0 < p->nE; e0 += p->chunk) {
-      Sweep s{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
-              sigma_E_stride, (const double2*)E, (double2*)G_band, (double2*)G_1N, info,
-              e0, std::min(p->chunk, p->nE - e0)};
-      NEGF_TRY(s.upward(G_band != nullptr));
-      if (G_band) NEGF_TRY(s.downward());
-      if (G_1N) {
-        const int64_t s1 = (int64_t)p->b[0] * p->b[p->N - 1];
-        NEGF_TRY(s.first_row((double2*)G_1N + (int64_t)e0 * s1, s1));
-      }
+      Sweep base{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
+                 sigma_E_stride, (const double2*)E, (double2*)G_band, (double2*)G_1N, info,
+                 e0, std::min(p->chunk, p->nE - e0)};
+      NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
+        NEGF_TRY(s.upward(G_band != nullptr));
+        if (G_band) NEGF_TRY(s.downward());
+        if (G_1N) {
+          const int64_t s1 = (int64_t)p->b[0] * p->b[p->N - 1];
+          NEGF_TRY(s.first_row((double2*)G_1N + (int64_t)s.e0 * s1, s1));
+        }
+        return cudaSuccess;
+      }));
     }
     return cudaSuccess;
   });
@@ -610,12 +669,15 @@ negf_status negf_transmission(negf_plan_t* p, const negf_c128* H, const negf_c12
     NEGF_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * p->nE, p->stream));
     const int64_t s1 = (int64_t)p->b[0] * p->b[p->N - 1];
     for (int e0 = 0; e0 < p->nE; e0 += p->chunk) {
-      Sweep s{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
-              sigma_E_stride, (const double2*)E, nullptr, nullptr, info,
-              e0, std::min(p->chunk, p->nE - e0)};
-      NEGF_TRY(s.upward(false));
-      NEGF_TRY(s.first_row(p->G1N_ws, s1));
-      NEGF_TRY(s.transmission(p->G1N_ws, s1, T));
+      Sweep base{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
+                 sigma_E_stride, (const double2*)E, nullptr, nullptr, info,
+                 e0, std::min(p->chunk, p->nE - e0)};
+      NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
+        double2* g1n = p->G1N_ws + (int64_t)s.wofs * s1;
+        NEGF_TRY(s.upward(false));
+        NEGF_TRY(s.first_row(g1n, s1));
+        return s.transmission(g1n, s1, T);
+      }));
     }
     return cudaSuccess;
   });

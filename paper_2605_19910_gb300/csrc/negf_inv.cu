@@ -27,6 +27,7 @@ zinv_gj_kernel(const double2* __restrict__ S, int64_t sS, double2* __restrict__ 
   __shared__ int s_piv;
   __shared__ double2 s_pv;
   __shared__ double2 s_akk;
+  __shared__ double2 s_d;
   __shared__ int s_bad;
 
   const int e = blockIdx.x;
@@ -64,6 +65,7 @@ zinv_gj_kernel(const double2* __restrict__ S, int64_t sS, double2* __restrict__ 
         double2 pv = s_pv;
         bool finite = isfinite(pv.x) && isfinite(pv.y);
         bool zero = (pv.x == 0.0 && pv.y == 0.0);
+        s_d = crecip(pv);   // once per column: FP64 division is a multi-instruction sequence
         if ((!finite || zero) && !s_bad) {
           s_bad = 1;
           atomicOr(errword, finite ? ERRBIT_SINGULAR : ERRBIT_NONFINITE);
@@ -73,7 +75,7 @@ zinv_gj_kernel(const double2* __restrict__ S, int64_t sS, double2* __restrict__ 
     }
     __syncthreads();
     const int p = s_piv;
-    const double2 d = crecip(s_pv);
+    const double2 d = s_d;
     // Phase 2: swap rows k and p, scale the new row k by 1/pivot, and keep the
     // multipliers f_i (column k after the swap) for i != k.
     for (int j = tid; j < b; j += nth) {

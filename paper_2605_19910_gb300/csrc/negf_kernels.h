@@ -25,6 +25,7 @@ struct ZGemm {
   const double2* dshift = nullptr; int64_t sD = 1;
   double2 alpha = {1.0, 0.0}, beta1 = {0.0, 0.0}, beta2 = {0.0, 0.0}, gamma = {0.0, 0.0};
   const double* weight = nullptr;
+  int* errword = nullptr;   // device error word for bounded-wait timeouts (tensor-core path)
   int batch = 1;
   int reduce = 0;
 };
