@@ -40,7 +40,7 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--cpu-energies", type=int, default=96,
+    ap.add_argument("--cpu-energies", type=int, default=512,
                     help="energies of the bounded CPU-oracle sample")
     ap.add_argument("--n-blocks", type=int, default=None, help="override the workload's block count")
     ap.add_argument("--n-energies", type=int, default=None, help="override the workload's energy count")
@@ -311,7 +311,7 @@ def run_ours(a, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64" if a.precision == "fp64" else "mixed: bf16x3-split tensor products, f64 inverses",
+            "dtype": "f64" if a.precision == "fp64" else "mixed: exact bf16-slice tensor products (4 x 8 bit), f64 inverses",
             "data": "synthetic",
             "config": {"workload": a.workload, "n_blocks": N, "block_size": prob.sizes[0], "band_n": 2 * prob.w + 1,
                        "n_energies": nE, "eta": 1e-6, "precision": a.precision,

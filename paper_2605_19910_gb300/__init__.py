@@ -329,9 +329,33 @@ class Plan:
         if s != NEGF_OK:
             raise NegfError(s, "negf_sync")
 
-    @staticmethod
-    def _sig_stride(sig, b):
-        return 0 if sig.dim() == 2 else b * b
+    def _sigmas(self, sigma_L, sigma_R):
+        """Marshal the lead self-energies into the C-ABI form: one matrix each
+        (stride 0) or per-energy stacks sharing one element stride.  When
+        b_1 != b_N, per-energy stacks are copied into buffers padded to the
+        larger block.  Returns (sigma_L, sigma_R, stride)."""
+        if sigma_L.dim() == 2 and sigma_R.dim() == 2:
+            return sigma_L.contiguous(), sigma_R.contiguous(), 0
+        torch = self.torch
+        nE = self.n_energies
+        b0, bN = self.sizes[0], self.sizes[-1]
+        if sigma_L.dim() == 2:
+            sigma_L = sigma_L.expand(nE, b0, b0)
+        if sigma_R.dim() == 2:
+            sigma_R = sigma_R.expand(nE, bN, bN)
+        stride = max(b0, bN) ** 2
+        if b0 == bN:
+            return sigma_L.contiguous(), sigma_R.contiguous(), stride
+        pl = torch.zeros(nE, stride, dtype=sigma_L.dtype, device=sigma_L.device)
+        pr = torch.zeros(nE, stride, dtype=sigma_R.dtype, device=sigma_R.device)
+        pl[:, :b0 * b0] = sigma_L.reshape(nE, -1)
+        pr[:, :bN * bN] = sigma_R.reshape(nE, -1)
+        return pl, pr, stride
+
+    def _unpad(self, buf, b, stride):
+        if stride == 0:
+            return buf.reshape(b, b)
+        return buf.reshape(self.n_energies, stride)[:, :b * b].reshape(self.n_energies, b, b)
 
     def solve(self, H, sigma_L, sigma_R, E, band=True, g1n=True, out_band=None, out_g1n=None, sync=True):
         """Returns ``(G_band [n_E, band_elems] or None, G_1N [n_E, b1, bN] or None)``."""
@@ -342,7 +366,7 @@ class Plan:
             torch.empty(nE, self.band_elems, dtype=torch.complex128, device="cuda") if band else None)
         G1 = out_g1n if out_g1n is not None else (
             torch.empty(nE, b0, bN, dtype=torch.complex128, device="cuda") if g1n else None)
-        stride = self._sig_stride(sigma_L, b0)
+        sigma_L, sigma_R, stride = self._sigmas(sigma_L, sigma_R)
         self._enter()
         st = negf_solve(self.handle, H, sigma_L, sigma_R, stride, E, Gb, G1, self.info)
         self._leave()
@@ -354,7 +378,7 @@ class Plan:
     def transmission(self, H, sigma_L, sigma_R, E, out=None, sync=True):
         torch = self.torch
         T = out if out is not None else torch.empty(self.n_energies, dtype=torch.float64, device="cuda")
-        stride = self._sig_stride(sigma_L, self.sizes[0])
+        sigma_L, sigma_R, stride = self._sigmas(sigma_L, sigma_R)
         self._enter()
         st = negf_transmission(self.handle, H, sigma_L, sigma_R, stride, E, T, self.info)
         self._leave()
@@ -368,9 +392,10 @@ class Plan:
         torch = self.torch
         T = torch.empty(self.n_energies, dtype=torch.float64, device="cuda")
         dH = torch.empty(self.band_elems, dtype=torch.complex128, device="cuda")
+        shapes = (sigma_L.shape, sigma_R.shape)
+        sigma_L, sigma_R, stride = self._sigmas(sigma_L, sigma_R)
         dSL = torch.empty_like(sigma_L)
         dSR = torch.empty_like(sigma_R)
-        stride = self._sig_stride(sigma_L, self.sizes[0])
         dL = dL_dT.contiguous()
         self._enter()
         st = negf_grad(self.handle, H, sigma_L, sigma_R, stride, E, dL, T, dH, dSL, dSR, self.info)
@@ -378,6 +403,12 @@ class Plan:
         self._check(st, "negf_grad")
         if sync:
             self.sync()
+        dSL = self._unpad(dSL, self.sizes[0], stride)
+        dSR = self._unpad(dSR, self.sizes[-1], stride)
+        if len(shapes[0]) == 2 and stride:      # one Sigma broadcast to every energy: sum
+            dSL = dSL.sum(0)
+        if len(shapes[1]) == 2 and stride:
+            dSR = dSR.sum(0)
         return T, dH, dSL, dSR
 
 

@@ -168,44 +168,50 @@ struct Sweep {
   }
   double2* Sslot(int a, int bb) const {
     int r = p->w + 1;
-    return p->S_ws + (int64_t)((a % r) * r + (bb % r)) * p->s_slot * p->chunk +
-           (int64_t)wofs * p->b[a] * p->b[bb];
+    return p->S_ws + (int64_t)((a % r) * r + (bb % r)) * p->s_slot * p->chunk + (int64_t)wofs * p->s_slot;
   }
+  // Per-energy stride inside a shared slot is fixed (bmax^2, b_1 * bmax):
+  // concurrent energy groups can be at different layers of different sizes.
+  int64_t sS() const { return p->s_slot; }
+  int64_t sR(int j) const { return (p->outputs & NEGF_OUT_GRAD) ? (int64_t)p->b[0] * p->b[j] : (int64_t)p->b[0] * p->r_elems; }
   double2* Gb(int a, int bb) const { return Gband + (int64_t)e0 * p->band_elems + p->band_off[(bb - a + p->w) * p->N + a]; }
-  const double2* sigma_for(int layer) const {
-    // Sigma_L on layer 0, Sigma_R on layer N-1 (both when N == 1 is handled by the caller)
-    const double2* s = layer == 0 ? sigL : sigR;
-    return s ? s + (sig_stride ? (int64_t)e0 * sig_stride : 0) : nullptr;
-  }
+  // Lead self-energies of this energy range: Sigma_L acts on layer 0 and
+  // Sigma_R on layer N-1 (the same layer when N == 1).
+  const double2* sigmaL() const { return sigL ? sigL + (sig_stride ? (int64_t)e0 * sig_stride : 0) : nullptr; }
+  const double2* sigmaR() const { return sigR ? sigR + (sig_stride ? (int64_t)e0 * sig_stride : 0) : nullptr; }
 
-  // Upward pass (Alg. 1 upward loop / Sec. 2.3): eliminate layers N-1 .. 0.
-  cudaError_t upward(bool need_x) {
+  // Upward pass (Alg. 1 upward loop / Sec. 2.3): eliminate layers l .. f of
+  // the chain restricted to [f, l] (the whole chain by default; one DDRGF
+  // sub-domain otherwise).  Sigma_L / Sigma_R enter only if layer 0 / N-1 is
+  // inside the range.
+  cudaError_t upward(bool need_x, int f = 0, int l = -1) {
     const int N = p->N, w = p->w, C = ne;
+    if (l < 0) l = N - 1;
     std::map<std::pair<int, int>, bool> mat;   // S_ab materialized per energy
-    // S_{N-1,N-1} = E I - H - Sigma_R (- Sigma_L when N == 1)
+    // S_{l,l} = E I - H_ll (- Sigma_R if l = N-1) (- Sigma_L if l = 0)
     {
-      int bl = p->b[N - 1];
-      double2* dst = Sslot(N - 1, N - 1);
+      int bl = p->b[l];
+      double2* dst = Sslot(l, l);
+      const double2* extra = (l == N - 1) ? sigmaR() : nullptr;
       NEGF_TRY(misc([&] {
-        return negf::assemble_diag(Hblk(N - 1, N - 1), E + e0, sigma_for(N - 1), sig_stride, dst, sq(bl), bl,
-                                   C, st);
+        return negf::assemble_diag(Hblk(l, l), E + e0, extra, sig_stride, dst, sS(), bl, C, st);
       }));
-      if (N == 1 && sigL) {
+      if (l == 0 && sigL) {
         ZGemm g;   // dst -= Sigma_L : expressed as C = 1*dst - 1*SigmaL with an empty product
         g.m = bl; g.n = bl; g.k = 0;
         g.A = dst; g.B = dst; g.lda = bl; g.ldb = bl;
-        g.C = dst; g.sC = sq(bl); g.ldc = bl;
-        g.C1 = dst; g.sC1 = sq(bl); g.ldc1 = bl; g.beta1 = {1.0, 0.0};
-        g.C2 = sigma_for(0); g.sC2 = sig_stride; g.ldc2 = bl; g.beta2 = {-1.0, 0.0};
+        g.C = dst; g.sC = sS(); g.ldc = bl;
+        g.C1 = dst; g.sC1 = sS(); g.ldc1 = bl; g.beta1 = {1.0, 0.0};
+        g.C2 = sigmaL(); g.sC2 = sig_stride; g.ldc2 = bl; g.beta2 = {-1.0, 0.0};
         g.batch = C;
         NEGF_TRY(gemm64(g));
       }
-      mat[{N - 1, N - 1}] = true;
+      mat[{l, l}] = true;
     }
-    for (int i = N - 1; i >= 0; --i) {
+    for (int i = l; i >= f; --i) {
       const int bi = p->b[i];
-      NEGF_TRY(inv(Sslot(i, i), sq(bi), Tblk(i), sq(bi), bi, C, i + 1));
-      const int lo = std::max(0, i - w);
+      NEGF_TRY(inv(Sslot(i, i), sS(), Tblk(i), sq(bi), bi, C, i + 1));
+      const int lo = std::max(f, i - w);
       for (int c = lo; c < i; ++c) {
         const int bc = p->b[c];
         const bool mic = mat.count({i, c}) > 0, mci = mat.count({c, i}) > 0;
@@ -213,7 +219,7 @@ struct Sweep {
           ZGemm g;
           g.m = bi; g.n = bc; g.k = bi;
           g.A = Tblk(i); g.sA = sq(bi); g.lda = bi;
-          if (mic) { g.B = Sslot(i, c); g.sB = (int64_t)bi * bc; g.ldb = bc; g.alpha = {1.0, 0.0}; }
+          if (mic) { g.B = Sslot(i, c); g.sB = sS(); g.ldb = bc; g.alpha = {1.0, 0.0}; }
           else { g.B = Hblk(i, c); g.sB = 0; g.ldb = bc; g.alpha = {-1.0, 0.0}; }
           g.C = Xblk(i, c); g.sC = (int64_t)bi * bc; g.ldc = bc;
           g.batch = C;
@@ -222,7 +228,7 @@ struct Sweep {
         {   // Y_{c,i} = S_{c,i} t_i
           ZGemm g;
           g.m = bc; g.n = bi; g.k = bi;
-          if (mci) { g.A = Sslot(c, i); g.sA = (int64_t)bc * bi; g.lda = bi; g.alpha = {1.0, 0.0}; }
+          if (mci) { g.A = Sslot(c, i); g.sA = sS(); g.lda = bi; g.alpha = {1.0, 0.0}; }
           else { g.A = Hblk(c, i); g.sA = 0; g.lda = bi; g.alpha = {-1.0, 0.0}; }
           g.B = Tblk(i); g.sB = sq(bi); g.ldb = bi;
           g.C = Yblk(c, i); g.sC = (int64_t)bc * bi; g.ldc = bi;
@@ -238,17 +244,17 @@ struct Sweep {
           ZGemm g;
           g.m = ba; g.n = bbs; g.k = bi;
           g.A = Yblk(a, i); g.sA = (int64_t)ba * bi; g.lda = bi;
-          if (mib) { g.B = Sslot(i, bb); g.sB = (int64_t)bi * bbs; g.ldb = bbs; g.alpha = {-1.0, 0.0}; }
+          if (mib) { g.B = Sslot(i, bb); g.sB = sS(); g.ldb = bbs; g.alpha = {-1.0, 0.0}; }
           else { g.B = Hblk(i, bb); g.sB = 0; g.ldb = bbs; g.alpha = {1.0, 0.0}; }
           double2* out = Sslot(a, bb);
-          g.C = out; g.sC = (int64_t)ba * bbs; g.ldc = bbs;
-          if (mab) { g.C1 = out; g.sC1 = (int64_t)ba * bbs; g.ldc1 = bbs; g.beta1 = {1.0, 0.0}; }
+          g.C = out; g.sC = sS(); g.ldc = bbs;
+          if (mab) { g.C1 = out; g.sC1 = sS(); g.ldc1 = bbs; g.beta1 = {1.0, 0.0}; }
           else {
             g.C1 = Hblk(a, bb); g.sC1 = 0; g.ldc1 = bbs; g.beta1 = {-1.0, 0.0};
             if (a == bb) {
               g.dshift = E + e0; g.sD = 1; g.gamma = {1.0, 0.0};
               const double2* sg = nullptr;
-              if (a == 0) sg = sigma_for(0);
+              if (a == 0) sg = sigmaL();
               if (sg) { g.C2 = sg; g.sC2 = sig_stride; g.ldc2 = ba; g.beta2 = {-1.0, 0.0}; }
             }
           }
@@ -261,14 +267,15 @@ struct Sweep {
     return cudaSuccess;
   }
 
-  // Downward pass (Alg. 1 downward loop / Sec. 2.3), written into Gband.
-  cudaError_t downward() {
+  // Downward pass (Alg. 1 downward loop / Sec. 2.3) over [f, l], written into Gband.
+  cudaError_t downward(int f = 0, int l = -1) {
     const int N = p->N, w = p->w, C = ne;
+    if (l < 0) l = N - 1;
     const int64_t sG = p->band_elems;
-    NEGF_TRY(misc([&] { return negf::copy_blocks(Tblk(0), sq(p->b[0]), Gb(0, 0), sG, sq(p->b[0]), C, st); }));
-    for (int i = 1; i < N; ++i) {
+    NEGF_TRY(misc([&] { return negf::copy_blocks(Tblk(f), sq(p->b[f]), Gb(f, f), sG, sq(p->b[f]), C, st); }));
+    for (int i = f + 1; i <= l; ++i) {
       const int bi = p->b[i];
-      const int lo = std::max(0, i - w);
+      const int lo = std::max(f, i - w);
       for (int a = lo; a < i; ++a) {     // G_{a,i} = -sum_c G_{a,c} Y_{c,i}
         for (int c = lo; c < i; ++c) {
           ZGemm g;
@@ -311,25 +318,29 @@ struct Sweep {
   // First block row G_{1,j} = -sum_c G_{1,c} Y_{c,j} (Eq. 4x4_exact_RGF, first
   // row); R_ws holds either the whole row (gradient) or a ring of w + 1.
   double2* Rblk(int j) const {
-    const int64_t o = (int64_t)wofs * p->b[0] * p->b[j];
+    const int64_t o = (int64_t)wofs * sR(j);
     if (p->outputs & NEGF_OUT_GRAD) return p->R_ws + p->r_off[j] * p->chunk + o;
     return p->R_ws + (int64_t)(j % (p->w + 1)) * (int64_t)p->b[0] * p->r_elems * p->chunk + o;
   }
   cudaError_t first_row(double2* g1n_out, int64_t s_out) {
     const int N = p->N, w = p->w, C = ne;
     const int b0 = p->b[0];
-    if (N == 1) return misc([&] { return negf::copy_blocks(Tblk(0), sq(b0), g1n_out, s_out, sq(b0), C, st); });
-    NEGF_TRY(misc([&] { return negf::copy_blocks(Tblk(0), sq(b0), Rblk(0), sq(b0), sq(b0), C, st); }));
+    if (N == 1) {
+      if (p->outputs & NEGF_OUT_GRAD)
+        NEGF_TRY(misc([&] { return negf::copy_blocks(Tblk(0), sq(b0), Rblk(0), sR(0), sq(b0), C, st); }));
+      return misc([&] { return negf::copy_blocks(Tblk(0), sq(b0), g1n_out, s_out, sq(b0), C, st); });
+    }
+    NEGF_TRY(misc([&] { return negf::copy_blocks(Tblk(0), sq(b0), Rblk(0), sR(0), sq(b0), C, st); }));
     for (int j = 1; j < N; ++j) {
       const int bj = p->b[j];
       const int lo = std::max(0, j - w);
       const bool last = (j == N - 1);
       double2* out = last ? g1n_out : Rblk(j);
-      const int64_t so = last ? s_out : (int64_t)b0 * bj;
+      const int64_t so = last ? s_out : sR(j);
       for (int c = lo; c < j; ++c) {
         ZGemm g;
         g.m = b0; g.n = bj; g.k = p->b[c];
-        g.A = Rblk(c); g.sA = (int64_t)b0 * p->b[c]; g.lda = p->b[c];
+        g.A = Rblk(c); g.sA = sR(c); g.lda = p->b[c];
         g.B = Yblk(c, j); g.sB = (int64_t)p->b[c] * bj; g.ldb = bj;
         g.C = out; g.sC = so; g.ldc = bj; g.alpha = {-1.0, 0.0};
         if (c > lo) { g.C1 = out; g.sC1 = so; g.ldc1 = bj; g.beta1 = {1.0, 0.0}; }
@@ -337,7 +348,113 @@ struct Sweep {
         NEGF_TRY(gemm(g));
       }
       if (last && (p->outputs & NEGF_OUT_GRAD))
-        NEGF_TRY(misc([&] { return negf::copy_blocks(out, so, Rblk(j), (int64_t)b0 * bj, (int64_t)b0 * bj, C, st); }));
+        NEGF_TRY(misc([&] { return negf::copy_blocks(out, so, Rblk(j), sR(j), (int64_t)b0 * bj, C, st); }));
+    }
+    return cudaSuccess;
+  }
+
+  // Scratch slot k (0: Gamma_L, 1: Gamma_R, 2: P, 3: Q, 4: G_1N, 5, 6: gradient
+  // temporaries) of this energy range; per-energy stride scr_stride(k).
+  int64_t scr_stride(int k) const {
+    const int b0 = p->b[0], bN = p->b[p->N - 1];
+    return k == 0 ? sq(b0) : (k == 1 ? sq(bN) : (int64_t)b0 * bN);
+  }
+  double2* scr(int k) const {
+    const int b0 = p->b[0], bN = p->b[p->N - 1];
+    int64_t off = 0;
+    for (int j = 0; j < k; ++j) off += (j == 0 ? sq(b0) : (j == 1 ? sq(bN) : (int64_t)b0 * bN)) * p->chunk;
+    (void)b0; (void)bN;
+    return p->scratch + off + (int64_t)wofs * scr_stride(k);
+  }
+  double2* Pblk(int i) const { return p->P_ws + p->p_off[i] * p->chunk + (int64_t)wofs * p->b[i] * p->b[p->N - 1]; }
+  double2* LCblk(int i) const { return p->LC_ws + p->p_off[i] * p->chunk + (int64_t)wofs * p->b[i] * p->b[p->N - 1]; }
+
+  // Last block column G_{i,N} (adjoint sweep).  With the factorisation
+  // M = U D L of the upward pass (U_{i,i+1} = Y_{i,i+1}, L_{i+1,i} = X_{i+1,i},
+  // D = diag(S_i); Eq. 2x2_UDL_factorization applied layer by layer), column N
+  // of M^{-1} = L^{-1} D^{-1} U^{-1} e_N is:
+  //   P_{N} = I,  P_i = -Y_{i,i+1} P_{i+1}            (U^{-1} e_N)
+  //   G_{1,N}' = t_1 P_1,  G_{i,N} = t_i P_i - X_{i,i-1} G_{i-1,N}.
+  cudaError_t last_column() {
+    const int N = p->N, C = ne, bN = p->b[N - 1];
+    const int64_t sI = sq(bN);
+    // P_{N-1} = I: assemble_diag with E = 1 and H = 0 is not available; use a
+    // k = 0 product: C = gamma * 1 * I with dshift = 1 from a constant.
+    for (int i = N - 1; i >= 0; --i) {
+      const int bi = p->b[i];
+      if (i == N - 1) {
+        NEGF_TRY(misc([&] { return negf::set_identity(Pblk(i), sI, bN, C, st); }));
+        continue;
+      }
+      ZGemm g;   // P_i = -Y_{i,i+1} P_{i+1}
+      g.m = bi; g.n = bN; g.k = p->b[i + 1];
+      g.A = Yblk(i, i + 1); g.sA = (int64_t)bi * p->b[i + 1]; g.lda = p->b[i + 1];
+      g.B = Pblk(i + 1); g.sB = (int64_t)p->b[i + 1] * bN; g.ldb = bN;
+      g.C = Pblk(i); g.sC = (int64_t)bi * bN; g.ldc = bN; g.alpha = {-1.0, 0.0};
+      g.batch = C;
+      NEGF_TRY(gemm(g));
+    }
+    for (int i = 0; i < N; ++i) {
+      const int bi = p->b[i];
+      ZGemm g;   // G_{i,N} = t_i P_i (- X_{i,i-1} G_{i-1,N} below)
+      g.m = bi; g.n = bN; g.k = bi;
+      g.A = Tblk(i); g.sA = sq(bi); g.lda = bi;
+      g.B = Pblk(i); g.sB = (int64_t)bi * bN; g.ldb = bN;
+      g.C = LCblk(i); g.sC = (int64_t)bi * bN; g.ldc = bN;
+      g.batch = C;
+      NEGF_TRY(gemm(g));
+      if (i > 0) {
+        ZGemm h;
+        h.m = bi; h.n = bN; h.k = p->b[i - 1];
+        h.A = Xblk(i, i - 1); h.sA = (int64_t)bi * p->b[i - 1]; h.lda = p->b[i - 1];
+        h.B = LCblk(i - 1); h.sB = (int64_t)p->b[i - 1] * bN; h.ldb = bN;
+        h.C = LCblk(i); h.sC = (int64_t)bi * bN; h.ldc = bN; h.alpha = {-1.0, 0.0};
+        h.C1 = LCblk(i); h.sC1 = (int64_t)bi * bN; h.ldc1 = bN; h.beta1 = {1.0, 0.0};
+        h.batch = C;
+        NEGF_TRY(gemm(h));
+      }
+    }
+    return cudaSuccess;
+  }
+
+  // K = Gamma_R G_1N^H Gamma_L (bN x b1) and U_a = K G_{1,a} (bN x b_a) for
+  // every layer a, written over P (no longer needed).
+  cudaError_t grad_prep(const double2* g1n, int64_t sG) {
+    const int N = p->N, C = ne, b0 = p->b[0], bN = p->b[N - 1];
+    const int nsig = sig_stride ? C : 1;
+    double2* gL = scr(0);
+    double2* gR = scr(1);
+    double2* W = scr(5);
+    double2* K = scr(6);
+    NEGF_TRY(misc([&] { return negf::gamma_from_sigma(sigmaL(), sig_stride, gL, sq(b0), b0, nsig, st); }));
+    NEGF_TRY(misc([&] { return negf::gamma_from_sigma(sigmaR(), sig_stride, gR, sq(bN), bN, nsig, st); }));
+    {   // W = G_1N^H Gamma_L  (bN x b0)
+      ZGemm g;
+      g.m = bN; g.n = b0; g.k = b0;
+      g.A = g1n; g.sA = sG; g.lda = bN; g.opA = negf::OP_C;
+      g.B = gL; g.sB = sig_stride ? sq(b0) : 0; g.ldb = b0;
+      g.C = W; g.sC = (int64_t)bN * b0; g.ldc = b0;
+      g.batch = C;
+      NEGF_TRY(gemm64(g));
+    }
+    {   // K = Gamma_R W
+      ZGemm g;
+      g.m = bN; g.n = b0; g.k = bN;
+      g.A = gR; g.sA = sig_stride ? sq(bN) : 0; g.lda = bN;
+      g.B = W; g.sB = (int64_t)bN * b0; g.ldb = b0;
+      g.C = K; g.sC = (int64_t)bN * b0; g.ldc = b0;
+      g.batch = C;
+      NEGF_TRY(gemm64(g));
+    }
+    for (int a = 0; a < N; ++a) {   // U_a = K G_{1,a}
+      const int ba = p->b[a];
+      ZGemm g;
+      g.m = bN; g.n = ba; g.k = b0;
+      g.A = K; g.sA = (int64_t)bN * b0; g.lda = b0;
+      g.B = Rblk(a); g.sB = sR(a); g.ldb = ba;
+      g.C = Pblk(a); g.sC = (int64_t)ba * bN; g.ldc = ba;
+      g.batch = C;
+      NEGF_TRY(gemm(g));
     }
     return cudaSuccess;
   }
@@ -350,8 +467,8 @@ struct Sweep {
     double2* Pm = p->scratch + (sq(b0) + sq(bN)) * p->chunk + (int64_t)wofs * b0 * bN;
     double2* Qm = p->scratch + (sq(b0) + sq(bN) + (int64_t)b0 * bN) * p->chunk + (int64_t)wofs * b0 * bN;
     const int nsig = sig_stride ? C : 1;
-    NEGF_TRY(misc([&] { return negf::gamma_from_sigma(sigma_for(0), sig_stride, gL, sq(b0), b0, nsig, st); }));
-    NEGF_TRY(misc([&] { return negf::gamma_from_sigma(sigma_for(p->N - 1), sig_stride, gR, sq(bN), bN, nsig, st); }));
+    NEGF_TRY(misc([&] { return negf::gamma_from_sigma(sigmaL(), sig_stride, gL, sq(b0), b0, nsig, st); }));
+    NEGF_TRY(misc([&] { return negf::gamma_from_sigma(sigmaR(), sig_stride, gR, sq(bN), bN, nsig, st); }));
     {   // P = Gamma_L G_1N
       ZGemm g;
       g.m = b0; g.n = bN; g.k = b0;
@@ -473,7 +590,8 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   int64_t pe = 0;
   for (int i = 0; i < N; ++i) { p->p_off[i] = pe; pe += (int64_t)p->b[i] * bN; }
   p->p_elems = grad ? pe : 0;
-  p->scr_elems = sq(b0) + sq(bN) + 2 * (int64_t)b0 * bN + (int64_t)b0 * bN;
+  // Gamma_L, Gamma_R, P, Q, G_1N, and two more b1 x bN temporaries (gradient)
+  p->scr_elems = sq(b0) + sq(bN) + 5 * (int64_t)b0 * bN;
 
   int64_t per_e = te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot +
                   (grad ? re : (int64_t)(w + 1) * b0 * bmax) + 2 * p->p_elems + p->scr_elems;
@@ -687,11 +805,123 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
                       const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                       const double* dL_dT, double* T, negf_c128* dH, negf_c128* dSigma_L,
                       negf_c128* dSigma_R, int32_t* info) {
-  (void)H; (void)sigma_L; (void)sigma_R; (void)sigma_E_stride; (void)E; (void)dL_dT; (void)T;
-  (void)dH; (void)dSigma_L; (void)dSigma_R; (void)info;
-  if (!p) return NEGF_ERR_ARG;
+  if (!p || !H || !E || !info || !dL_dT || !dH || !sigma_L || !sigma_R || sigma_E_stride < 0) return NEGF_ERR_ARG;
   if (!(p->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
-  return NEGF_ERR_UNSUPPORTED;
+  CallKey key{};
+  key.kind = CALL_GRAD;
+  key.stride = sigma_E_stride;
+  const void* ptrs[] = {H, sigma_L, sigma_R, E, dL_dT, T, dH, dSigma_L, dSigma_R, info};
+  std::memcpy(key.p, ptrs, sizeof(ptrs));
+  const int N = p->N, b0 = p->b[0], bN = p->b[N - 1];
+  const int64_t s1 = (int64_t)b0 * bN;
+  return run_captured(p, key, [&]() -> cudaError_t {
+    NEGF_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * p->nE, p->stream));
+    for (int e0 = 0; e0 < p->nE; e0 += p->chunk) {
+      const int ne = std::min(p->chunk, p->nE - e0);
+      const bool first = (e0 == 0);
+      Sweep base{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
+                 sigma_E_stride, (const double2*)E, nullptr, nullptr, info, e0, ne};
+      NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
+        double2* g1n = s.scr(4);
+        NEGF_TRY(s.upward(true));
+        NEGF_TRY(s.first_row(g1n, s1));
+        NEGF_TRY(s.last_column());
+        if (T) NEGF_TRY(s.transmission(g1n, s1, T));
+        return s.grad_prep(g1n, s1);
+      }));
+      // Energy-reduced adjoint products on the plan stream, over the chunk:
+      //   dH_ab (+)= 2 sum_e w_e (G_{b,N} U_a)^H = 2 sum_e w_e U_a^H G_{b,N}^H
+      Sweep s = base;   // wofs = 0: the whole chunk
+      for (int a = 0; a < N; ++a) {
+        for (int bb = std::max(0, a - 1); bb <= std::min(N - 1, a + 1); ++bb) {
+          const int ba = p->b[a], bbs = p->b[bb];
+          double2* out = (double2*)dH + p->band_off[(size_t)(bb - a + p->w) * N + a];
+          ZGemm g;
+          g.m = ba; g.n = bbs; g.k = bN;
+          g.A = s.Pblk(a); g.sA = (int64_t)ba * bN; g.lda = ba; g.opA = negf::OP_C;
+          g.B = s.LCblk(bb); g.sB = (int64_t)bbs * bN; g.ldb = bN; g.opB = negf::OP_C;
+          g.C = out; g.ldc = bbs; g.alpha = {2.0, 0.0};
+          if (!first) { g.C1 = out; g.ldc1 = bbs; g.beta1 = {1.0, 0.0}; }
+          g.weight = dL_dT + e0; g.reduce = 1; g.batch = ne;
+          NEGF_TRY(s.gemm64(g));
+        }
+      }
+      // Sigma terms.  Sigma enters M like H (the X_11 / X_NN parts are the
+      // dH_00 / dH_NN products) and also Gamma = i (Sigma - Sigma^H):
+      //   dSigma_L (+)= -2i sum_e w_e G_1N Gamma_R G_1N^H,
+      //   dSigma_R (+)= -2i sum_e w_e G_1N^H Gamma_L G_1N.
+      for (int side = 0; side < 2; ++side) {
+        negf_c128* dS = side == 0 ? dSigma_L : dSigma_R;
+        if (!dS) continue;
+        const int bs = side == 0 ? b0 : bN;
+        double2* V = s.scr(5);   // V = Gamma_R G_1N^H (bN x b0) or Gamma_L G_1N (b0 x bN)
+        {
+          ZGemm g;
+          if (side == 0) {
+            g.m = bN; g.n = b0; g.k = bN;
+            g.A = s.scr(1); g.sA = sigma_E_stride ? sq(bN) : 0; g.lda = bN;
+            g.B = s.scr(4); g.sB = s1; g.ldb = bN; g.opB = negf::OP_C;
+            g.C = V; g.sC = s1; g.ldc = b0;
+          } else {
+            g.m = b0; g.n = bN; g.k = b0;
+            g.A = s.scr(0); g.sA = sigma_E_stride ? sq(b0) : 0; g.lda = b0;
+            g.B = s.scr(4); g.sB = s1; g.ldb = bN;
+            g.C = V; g.sC = s1; g.ldc = bN;
+          }
+          g.batch = ne;
+          NEGF_TRY(s.gemm64(g));
+        }
+        ZGemm g;   // -2i sum_e w_e A_e or per energy
+        if (side == 0) {
+          g.m = b0; g.n = b0; g.k = bN;
+          g.A = s.scr(4); g.sA = s1; g.lda = bN;
+          g.B = V; g.sB = s1; g.ldb = b0;
+        } else {
+          g.m = bN; g.n = bN; g.k = b0;
+          g.A = s.scr(4); g.sA = s1; g.lda = bN; g.opA = negf::OP_C;
+          g.B = V; g.sB = s1; g.ldb = bN;
+        }
+        g.alpha = {0.0, -2.0};
+        g.weight = dL_dT + e0;
+        g.batch = ne;
+        if (sigma_E_stride == 0) {
+          g.C = (double2*)dS; g.ldc = bs; g.reduce = 1;
+          if (!first) { g.C1 = (double2*)dS; g.ldc1 = bs; g.beta1 = {1.0, 0.0}; }
+          NEGF_TRY(s.gemm64(g));
+        } else {
+          // per energy: M-path part 2 w_e (G_{i,N} U_i)^H first, then the Gamma part
+          const int layer = side == 0 ? 0 : N - 1;
+          ZGemm h;
+          h.m = bs; h.n = bs; h.k = bN;
+          h.A = s.Pblk(layer); h.sA = (int64_t)bs * bN; h.lda = bs; h.opA = negf::OP_C;
+          h.B = s.LCblk(layer); h.sB = (int64_t)bs * bN; h.ldb = bN; h.opB = negf::OP_C;
+          h.C = (double2*)dS + (int64_t)e0 * sigma_E_stride; h.sC = sigma_E_stride; h.ldc = bs;
+          h.alpha = {2.0, 0.0}; h.weight = dL_dT + e0; h.batch = ne;
+          NEGF_TRY(s.gemm64(h));
+          g.C = h.C; g.sC = sigma_E_stride; g.ldc = bs;
+          g.C1 = h.C; g.sC1 = sigma_E_stride; g.ldc1 = bs; g.beta1 = {1.0, 0.0};
+          NEGF_TRY(s.gemm64(g));
+        }
+      }
+    }
+    if (sigma_E_stride == 0) {   // add the M-path parts dH_00 / dH_NN once, after all chunks
+      Sweep s{p, p->stream, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, info, 0, 1};
+      for (int side = 0; side < 2; ++side) {
+        negf_c128* dS = side == 0 ? dSigma_L : dSigma_R;
+        if (!dS) continue;
+        const int layer = side == 0 ? 0 : N - 1, bs = p->b[layer];
+        ZGemm g;
+        g.m = bs; g.n = bs; g.k = 0;
+        g.A = (double2*)dS; g.B = (double2*)dS; g.lda = bs; g.ldb = bs;
+        g.C = (double2*)dS; g.ldc = bs;
+        g.C1 = (double2*)dS; g.ldc1 = bs; g.beta1 = {1.0, 0.0};
+        g.C2 = (const double2*)dH + p->band_off[(size_t)p->w * N + layer]; g.ldc2 = bs; g.beta2 = {1.0, 0.0};
+        g.batch = 1;
+        NEGF_TRY(s.gemm64(g));
+      }
+    }
+    return cudaSuccess;
+  });
 }
 
 }  // extern "C"

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(NTHREADS) zgemm_f64_kernel(ZGemm g, int tiles_
   for (int e = e_first; e < e_last; ++e) {
     const double2* A = g.A + (int64_t)e * g.sA;
     const double2* B = g.B + (int64_t)e * g.sB;
-    const double wgt = (g.reduce && g.weight) ? g.weight[e] : 1.0;
+    const double wgt = g.weight ? g.weight[e] : 1.0;   // per-batch real weight on A
     if (wgt == 0.0 && g.reduce) continue;
     for (int k0 = 0; k0 < g.k; k0 += BK) {
       load_a_tile(A, g.lda, g.opA, g.m, g.k, m0, k0, wgt, Ar, Ai, tid);

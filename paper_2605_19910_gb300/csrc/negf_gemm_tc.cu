@@ -4,24 +4,38 @@
 // Sec. 2.3 (the multipliers, the Schur update and the downward products);
 // the per-block inversions stay in FP64 (negf_inv.cu).
 //
-// A complex product C = A B is computed as one real product on the tensor
-// cores, with the real and imaginary parts stacked along M and K:
+// Complex -> real.  C = A B is one real product with the real and imaginary
+// parts stacked along M and K,
 //
 //     [Re C]   [Re A  -Im A] [Re B]
-//     [Im C] = [Im A   Re A] [Im B]
+//     [Im C] = [Im A   Re A] [Im B],
 //
-// so 64 complex rows of C form one M = 128 tcgen05 tile.  Each real operand
-// is split into two TF32 parts (x = hi + lo, hi = tf32(x), lo = tf32(x - hi))
-// and the product is accumulated in FP32 in tensor memory as
-// A_hi B_hi + A_hi B_lo + A_lo B_hi, which carries about 22 significant bits.
-// The epilogue reads the accumulator with tcgen05.ld, forms the complex
-// result and applies alpha / beta / the diagonal shift in FP64.
+// so 64 complex rows of C form one M = 128 tcgen05 tile.
 //
-// One CTA computes a 64 x N complex tile (N <= 256) of one batch entry; K is
-// streamed through shared memory in chunks of 32 complex columns.  Operands
-// use the K-major, non-swizzled canonical layout (8-row x 16-byte core
-// matrices).  One thread issues the MMAs; completion is tracked with an
-// mbarrier whose wait is bounded.
+// BF16 split with exact FP32 sums.  Each complex row r of A gets a power-of-two
+// scale 2^e_r above all its entries, each column c of B a scale 2^e_c.  An
+// entry x = 2^e_r * sum_l a_l 2^{-s(l+1)} is cut into L integer slices
+// |a_l| < 2^s (s = 8 bits, or 7 when K is long) that BF16 holds exactly.
+// A slice product is an integer below 2^{2s}; summed over K it stays below
+// 2^24, so the FP32 accumulation in tensor memory is exact.  The products
+// a_l b_m with l + m = d accumulate into TMEM accumulator d (levels
+// d = 0..L-1; deeper levels are dropped), and the epilogue combines the
+// levels exactly in 64-bit integers:
+//     C = 2^{e_r + e_c - s(L+1)} sum_d acc_d 2^{s(L-1-d)}.
+// The result carries about s*L = 32 significant bits relative to the row and
+// column scales.
+//
+// No FP64 instruction: GB300's FP64 pipe is the scarce resource of the whole
+// sweep (it runs the block inversions), so the slicing of FP64 inputs, the
+// level combination, the conversion to FP64 and the additions of the
+// epilogue (beta * C1, the diagonal shift E) are done with integer
+// operations on the IEEE bit patterns.
+//
+// One CTA computes a 64 x N complex tile of one batch entry (N <= 512 / L
+// TMEM columns per level); K streams through shared memory in chunks of 32
+// complex columns.  Operands use the K-major, non-swizzled canonical layout
+// (8-row x 16-byte core matrices).  One thread issues the MMAs; completion is
+// tracked with an mbarrier whose wait is bounded.
 #include "negf_common.cuh"
 #include "negf_kernels.h"
 
@@ -31,40 +45,130 @@ cudaError_t zinv_init();
 
 namespace {
 
-constexpr int TC_THREADS = 128;
-constexpr int MC = 64;                // complex rows per CTA (M = 128 real)
-constexpr int KC = 32;                // complex K per chunk (64 real)
-constexpr int KR = 2 * KC;            // real K per chunk
-constexpr int CORE_BYTES = 128;       // 8 rows x 16 bytes
-constexpr int SBO = (KR / 4) * CORE_BYTES;   // bytes between 8-row groups
-constexpr int LBO = CORE_BYTES;              // bytes between 16-byte K groups
-constexpr int A_BYTES = 128 * KR * 4;        // one split of the A chunk
+constexpr int TC_THREADS = 256;             // two warpgroups
+constexpr int MC = 64;                       // complex rows per CTA (M = 128 real)
+constexpr int KC = 32;                       // complex K per chunk
+constexpr int KR = 2 * KC;                   // real K per chunk (BF16 elements per row)
+constexpr int CORE = 128;                    // 8 rows x 16 bytes
+constexpr int LBO = CORE;                    // bytes between 16-byte K groups
+constexpr int SBO = (KR / 8) * CORE;         // bytes between 8-row groups
+constexpr int A_SLICE_BYTES = 128 * KR * 2;  // one slice of the A chunk
 constexpr long long WAIT_LIMIT = 1ll << 26;  // bounded mbarrier wait
+constexpr int ZERO_EXP = 0;                  // scale exponent of an all-zero row / column
+
+struct TcCfg {
+  int s;        // slice bits
+  int L;        // slices (= accumulator levels)
+  int n_mma;    // MMA N (complex columns per tile)
+  int tmem_cols;
+};
 
 __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// byte offset of real element (row, kcol) in a K-major non-swizzled tile
-__device__ __forceinline__ uint32_t kmaj_off(int row, int kcol) {
-  return (uint32_t)((row >> 3) * SBO + (kcol >> 2) * LBO + (row & 7) * 16 + (kcol & 3) * 4);
+__device__ __forceinline__ uint32_t kmaj_off(int row, int kcol) {   // BF16 element
+  return (uint32_t)((row >> 3) * SBO + (kcol >> 3) * LBO + (row & 7) * 16 + (kcol & 7) * 2);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// IEEE doubles are handled as 64-bit integer bit patterns throughout this
+// kernel, so that no instruction of GB300's scarce FP64 pipe is issued
+// (a sign flip on a double-typed value may compile to an FP64 negation).
+typedef unsigned long long u64;
+
+// e such that |x| < 2^e, from the biased exponent; zero/denormal -> very small
+__device__ __forceinline__ int exp_bound(u64 u) {
+  const int be = (int)((u >> 52) & 0x7FF);
+  return be == 0 ? -100000 : be - 1022;
 }
 
-__device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
-  hi = to_tf32((float)x);
-  lo = to_tf32((float)(x - (double)hi));
+// |x| * 2^(frac_bits - e_scale) as an unsigned integer (truncated), |x| < 2^e_scale.
+__device__ __forceinline__ u64 fixed_abs(u64 u, int e_scale, int frac_bits) {
+  const int be = (int)((u >> 52) & 0x7FF);
+  if (be == 0) return 0;
+  const u64 m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = be - 1075 + frac_bits - e_scale;     // value = m * 2^(be-1075); sh <= frac - 53 < 0
+  if (sh >= 0) return m << (sh > 10 ? 10 : sh);       // not reached for |x| < 2^e_scale
+  if (sh <= -64) return 0;
+  return m >> (-sh);
 }
 
-// tcgen05 shared-memory matrix descriptor: start address, leading (K) and
-// stride (M/N) byte offsets, descriptor version 1, no swizzle.
+// BF16 bits of the small integer v (< 256): exact through FP32 (2^23 + v), sign added after
+__device__ __forceinline__ uint32_t bf16_of_small(uint32_t v) {
+  return __float_as_uint(__uint_as_float(0x4B000000u | v) - 8388608.0f) >> 16;
+}
+
+// Signed 64-bit integer T times 2^e2 as IEEE double bits (round to nearest even)
+__device__ __forceinline__ u64 i64_scaled_bits(long long T, int e2) {
+  if (T == 0) return 0ull;
+  const u64 sgn = T < 0 ? 1ull : 0ull;
+  u64 u = T < 0 ? (u64)(-T) : (u64)T;
+  const int lz = __clzll((long long)u);
+  u <<= lz;                                   // leading one at bit 63
+  int e = 63 - lz + e2;
+  u64 m = u >> 11;                            // 53 bits with the leading one
+  const u64 rem = u & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) {
+    m += 1;
+    if (m >> 53) { m >>= 1; e += 1; }
+  }
+  const int be = e + 1023;
+  if (be <= 0) return sgn << 63;
+  if (be >= 2047) return (sgn << 63) | (0x7FFull << 52);
+  return (sgn << 63) | ((u64)be << 52) | (m & 0xFFFFFFFFFFFFFull);
+}
+
+// a + b on IEEE double bit patterns with integer operations (round to nearest).
+// Zeros and normals are handled, denormal results flush to zero; non-finite
+// operands (never produced by the sweep) propagate as NaN.
+__device__ __forceinline__ u64 add_bits(u64 ua, u64 ub) {
+  const u64 ABS = 0x7FFFFFFFFFFFFFFFull;
+  if ((ub & ABS) == 0) return ua;
+  if ((ua & ABS) == 0) return ub;
+  int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
+  if (ea == 0x7FF || eb == 0x7FF) return 0x7FF8000000000000ull;
+  if ((ua & ABS) < (ub & ABS)) {
+    u64 t = ua; ua = ub; ub = t;
+    int te = ea; ea = eb; eb = te;
+  }
+  if (ea == 0) return ua;                     // both denormal: negligible here
+  const u64 sa = ua >> 63, sb = ub >> 63;
+  const u64 ma = ((ua & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 9;   // leading one at bit 61
+  u64 mb = eb == 0 ? 0 : ((ub & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 9;
+  const int d = ea - eb;
+  if (d >= 62) mb = mb ? 1 : 0;
+  else if (d > 0) mb = (mb >> d) | ((mb & ((1ull << d) - 1)) ? 1ull : 0ull);
+  u64 m = (sa == sb) ? ma + mb : ma - mb;
+  if (m == 0) return 0ull;
+  int e = ea;
+  const int lz = __clzll((long long)m);
+  if (lz == 1) {                          // carry into bit 62
+    m = (m >> 1) | (m & 1ull);
+    e += 1;
+  } else if (lz > 2) {
+    m <<= (lz - 2);
+    e -= (lz - 2);
+  }
+  const u64 rem = m & 0x1FFull;
+  m >>= 9;
+  if (rem > 0x100ull || (rem == 0x100ull && (m & 1ull))) {
+    m += 1;
+    if (m >> 53) { m >>= 1; e += 1; }
+  }
+  if (e <= 0) return sa << 63;
+  if (e >= 2047) return (sa << 63) | (0x7FFull << 52);
+  return (sa << 63) | ((u64)e << 52) | (m & 0xFFFFFFFFFFFFFull);
+}
+
+__device__ __forceinline__ u64 flip(u64 x, bool neg) { return neg ? (x ^ 0x8000000000000000ull) : x; }
+
+__device__ __forceinline__ ulonglong2 ld_bits(const double2* p) {
+  return *reinterpret_cast<const ulonglong2*>(p);
+}
+
+// tcgen05 shared-memory matrix descriptor: start, LBO (K), SBO (M/N), version 1, no swizzle.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -74,16 +178,16 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor of kind::tf32, FP32 accumulate, K-major A and B
+// instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 accumulate
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
       :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
 }
 
@@ -104,110 +208,187 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared memory: [A hi | A lo | B hi | B lo] operand chunks, reused as the
-// FP32 staging of the accumulator in the epilogue.
-__global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles_n, int n_mma, int tmem_cols,
-                                                               int* errword) {
+// exact integer value of an FP32 accumulator that holds an integer below 2^31
+__device__ __forceinline__ long long acc_int(uint32_t bits) {
+  const int be = (int)((bits >> 23) & 0xFF);
+  if (be < 127) return 0;                          // |v| < 1: only 0 occurs
+  const long long m = (long long)((bits & 0x7FFFFFu) | 0x800000u);
+  const int sh = be - 150;                         // value = m * 2^(be - 150)
+  const long long v = sh >= 0 ? (m << sh) : (m >> (-sh));
+  return (bits >> 31) ? -v : v;
+}
+
+__global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base_s;
+  __shared__ int e_row[MC];
+  __shared__ int e_col[256];
 
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int L = cfg.L, s = cfg.s, n_mma = cfg.n_mma;
   const int tile = blockIdx.x;
   const int m0 = (tile / tiles_n) * MC;
   const int n0 = (tile % tiles_n) * n_mma;
   const int e = blockIdx.y;
-  const int nt = min(n_mma, g.n - n0);   // valid complex columns of this tile
-  const int b_bytes = n_mma * KR * 4;    // one split of the B chunk
-
-  unsigned char* sAh = smem;
-  unsigned char* sAl = smem + A_BYTES;
-  unsigned char* sBh = smem + 2 * A_BYTES;
-  unsigned char* sBl = smem + 2 * A_BYTES + b_bytes;
+  const int mt = min(MC, g.m - m0);
+  const int nt = min(n_mma, g.n - n0);
+  const int b_slice_bytes = n_mma * KR * 2;
+  unsigned char* sA = smem;                                   // L slices of A
+  unsigned char* sB = smem + (size_t)L * A_SLICE_BYTES;       // L slices of B^T
 
   const double2* A = g.A + (int64_t)e * g.sA;
   const double2* B = g.B + (int64_t)e * g.sB;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_base_s)), "r"(tmem_cols));
+                 :: "r"(smem_u32(&tmem_base_s)), "r"(cfg.tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+
+  // Pass 1: power-of-two scales of the rows of A and of the columns of B.
+  for (int r = warp; r < MC; r += TC_THREADS / 32) {
+    int mx = -100000;
+    if (m0 + r < g.m)
+      for (int k = lane; k < g.k; k += 32) {
+        const ulonglong2 v = ld_bits(A + (int64_t)(m0 + r) * g.lda + k);
+        mx = max(mx, max(exp_bound(v.x), exp_bound(v.y)));
+      }
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) e_row[r] = mx < -50000 ? ZERO_EXP : mx;
+  }
+  for (int c = tid; c < n_mma; c += TC_THREADS) e_col[c] = -100000;
+  __syncthreads();
+  for (int idx = tid; idx < g.k * nt; idx += TC_THREADS) {   // coalesced over columns
+    const int k = idx / nt, c = idx - k * nt;
+    const ulonglong2 v = ld_bits(B + (int64_t)k * g.ldb + n0 + c);
+    atomicMax(&e_col[c], max(exp_bound(v.x), exp_bound(v.y)));
+  }
+  __syncthreads();
+  for (int c = tid; c < n_mma; c += TC_THREADS)
+    if (e_col[c] < -50000) e_col[c] = ZERO_EXP;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem_d = tmem_base_s;
   const uint32_t mb = smem_u32(&mbar);
   const uint32_t idesc = make_idesc(128, n_mma);
+  const int frac = s * L;
+  const uint32_t smask = (1u << s) - 1u;
   bool ok = true;
   uint32_t last_parity = 0;
 
   const int nchunks = (g.k + KC - 1) / KC;
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int k0 = ch * KC;
-    // --- stage A: rows r (real part block) and 64 + r (imaginary part block)
-    for (int idx = tid; idx < MC * KC; idx += TC_THREADS) {
-      const int r = idx / KC, kk = idx % KC;
-      const int gr = m0 + r, gk = k0 + kk;
-      double2 v = make_double2(0.0, 0.0);
-      if (gr < g.m && gk < g.k) v = A[(int64_t)gr * g.lda + gk];
-      float rh, rl, ih, il, nih, nil;
-      split_tf32(v.x, rh, rl);
-      split_tf32(v.y, ih, il);
-      split_tf32(-v.y, nih, nil);
-      // row r: [Re A | -Im A]; row 64 + r: [Im A | Re A]
-      *reinterpret_cast<float*>(sAh + kmaj_off(r, kk)) = rh;
-      *reinterpret_cast<float*>(sAl + kmaj_off(r, kk)) = rl;
-      *reinterpret_cast<float*>(sAh + kmaj_off(r, KC + kk)) = nih;
-      *reinterpret_cast<float*>(sAl + kmaj_off(r, KC + kk)) = nil;
-      *reinterpret_cast<float*>(sAh + kmaj_off(MC + r, kk)) = ih;
-      *reinterpret_cast<float*>(sAl + kmaj_off(MC + r, kk)) = il;
-      *reinterpret_cast<float*>(sAh + kmaj_off(MC + r, KC + kk)) = rh;
-      *reinterpret_cast<float*>(sAl + kmaj_off(MC + r, KC + kk)) = rl;
+    // Pass 2a: slices of A, 8 consecutive K per thread item, one 16-byte
+    // core-matrix row per store.  Row r holds [Re A | -Im A], row 64 + r
+    // holds [Im A | Re A].
+    for (int item = tid; item < MC * (KC / 8); item += TC_THREADS) {
+      const int r = item >> 2, kg = item & 3;
+      const int gr = m0 + r;
+      const int er = e_row[r];
+      u64 fre[8], fim[8];
+      uint32_t sre = 0, sim = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int gk = k0 + kg * 8 + j;
+        ulonglong2 v = make_ulonglong2(0ull, 0ull);
+        if (gr < g.m && gk < g.k) v = ld_bits(A + (int64_t)gr * g.lda + gk);
+        fre[j] = fixed_abs(v.x, er, frac);
+        fim[j] = fixed_abs(v.y, er, frac);
+        sre |= (uint32_t)(v.x >> 63) << j;
+        sim |= (uint32_t)(v.y >> 63) << j;
+      }
+      for (int l = 0; l < L; ++l) {
+        const int sh = s * (L - 1 - l);
+        uint32_t pr[4], pi[4], pn[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const uint32_t r0 = bf16_of_small((uint32_t)(fre[2 * h] >> sh) & smask);
+          const uint32_t r1 = bf16_of_small((uint32_t)(fre[2 * h + 1] >> sh) & smask);
+          const uint32_t i0 = bf16_of_small((uint32_t)(fim[2 * h] >> sh) & smask);
+          const uint32_t i1 = bf16_of_small((uint32_t)(fim[2 * h + 1] >> sh) & smask);
+          const uint32_t sr0 = ((sre >> (2 * h)) & 1u) << 15, sr1 = ((sre >> (2 * h + 1)) & 1u) << 15;
+          const uint32_t si0 = ((sim >> (2 * h)) & 1u) << 15, si1 = ((sim >> (2 * h + 1)) & 1u) << 15;
+          pr[h] = (r0 | sr0) | ((r1 | sr1) << 16);
+          pi[h] = (i0 | si0) | ((i1 | si1) << 16);
+          pn[h] = (i0 | (si0 ^ 0x8000u)) | ((i1 | (si1 ^ 0x8000u)) << 16);
+        }
+        unsigned char* base = sA + (size_t)l * A_SLICE_BYTES;
+        const uint4 vr = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+        const uint4 vi = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+        const uint4 vn = make_uint4(pn[0], pn[1], pn[2], pn[3]);
+        *reinterpret_cast<uint4*>(base + kmaj_off(r, kg * 8)) = vr;
+        *reinterpret_cast<uint4*>(base + kmaj_off(r, KC + kg * 8)) = vn;
+        *reinterpret_cast<uint4*>(base + kmaj_off(MC + r, kg * 8)) = vi;
+        *reinterpret_cast<uint4*>(base + kmaj_off(MC + r, KC + kg * 8)) = vr;
+      }
     }
-    // --- stage B^T (K-major): row n holds [Re B(:, n) | Im B(:, n)]
-    for (int idx = tid; idx < KC * n_mma; idx += TC_THREADS) {
-      const int kk = idx / n_mma, c = idx % n_mma;
-      const int gk = k0 + kk, gc = n0 + c;
-      double2 v = make_double2(0.0, 0.0);
-      if (gk < g.k && c < nt) v = B[(int64_t)gk * g.ldb + gc];
-      float rh, rl, ih, il;
-      split_tf32(v.x, rh, rl);
-      split_tf32(v.y, ih, il);
-      *reinterpret_cast<float*>(sBh + kmaj_off(c, kk)) = rh;
-      *reinterpret_cast<float*>(sBl + kmaj_off(c, kk)) = rl;
-      *reinterpret_cast<float*>(sBh + kmaj_off(c, KC + kk)) = ih;
-      *reinterpret_cast<float*>(sBl + kmaj_off(c, KC + kk)) = il;
+    // Pass 2b: slices of B^T (K-major): row c holds [Re B(:, c) | Im B(:, c)].
+    for (int item = tid; item < n_mma * (KC / 8); item += TC_THREADS) {
+      const int c = item % n_mma, kg = item / n_mma;
+      const int ec = e_col[c];
+      u64 fre[8], fim[8];
+      uint32_t sre = 0, sim = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int gk = k0 + kg * 8 + j;
+        ulonglong2 v = make_ulonglong2(0ull, 0ull);
+        if (gk < g.k && c < nt) v = ld_bits(B + (int64_t)gk * g.ldb + n0 + c);
+        fre[j] = fixed_abs(v.x, ec, frac);
+        fim[j] = fixed_abs(v.y, ec, frac);
+        sre |= (uint32_t)(v.x >> 63) << j;
+        sim |= (uint32_t)(v.y >> 63) << j;
+      }
+      for (int l = 0; l < L; ++l) {
+        const int sh = s * (L - 1 - l);
+        uint32_t pr[4], pi[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const uint32_t r0 = bf16_of_small((uint32_t)(fre[2 * h] >> sh) & smask);
+          const uint32_t r1 = bf16_of_small((uint32_t)(fre[2 * h + 1] >> sh) & smask);
+          const uint32_t i0 = bf16_of_small((uint32_t)(fim[2 * h] >> sh) & smask);
+          const uint32_t i1 = bf16_of_small((uint32_t)(fim[2 * h + 1] >> sh) & smask);
+          pr[h] = (r0 | (((sre >> (2 * h)) & 1u) << 15)) | ((r1 | (((sre >> (2 * h + 1)) & 1u) << 15)) << 16);
+          pi[h] = (i0 | (((sim >> (2 * h)) & 1u) << 15)) | ((i1 | (((sim >> (2 * h + 1)) & 1u) << 15)) << 16);
+        }
+        unsigned char* base = sB + (size_t)l * b_slice_bytes;
+        *reinterpret_cast<uint4*>(base + kmaj_off(c, kg * 8)) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+        *reinterpret_cast<uint4*>(base + kmaj_off(c, KC + kg * 8)) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+      }
     }
-    // make the generic-proxy stores visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t aH = smem_u32(sAh), aL = smem_u32(sAl), bH = smem_u32(sBh), bL = smem_u32(sBl);
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
 #pragma unroll 1
-      for (int s = 0; s < KR / 8; ++s) {
-        const uint32_t koff = (uint32_t)s * 2 * LBO;    // 8 real K = two 16-byte core columns
-        const uint32_t acc0 = (ch > 0 || s > 0) ? 1u : 0u;
-        mma_tf32(tmem_d, make_desc(aH + koff), make_desc(bH + koff), idesc, acc0);
-        mma_tf32(tmem_d, make_desc(aH + koff), make_desc(bL + koff), idesc, 1u);
-        mma_tf32(tmem_d, make_desc(aL + koff), make_desc(bH + koff), idesc, 1u);
+      for (int st = 0; st < KR / 16; ++st) {
+        const uint32_t koff = (uint32_t)st * 2 * LBO;       // 16 BF16 of K = two core columns
+#pragma unroll 1
+        for (int d = 0; d < L; ++d) {
+          const uint32_t tm = tmem_d + (uint32_t)(d * n_mma);
+#pragma unroll 1
+          for (int l = 0; l <= d; ++l) {
+            const int m = d - l;
+            const uint32_t acc = (ch > 0 || st > 0 || l > 0) ? 1u : 0u;
+            mma_bf16(tm, make_desc(a0 + (uint32_t)l * A_SLICE_BYTES + koff),
+                     make_desc(b0 + (uint32_t)m * b_slice_bytes + koff), idesc, acc);
+          }
+        }
       }
       mma_commit(mb);
     }
@@ -217,84 +398,118 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
+  u64* stage = reinterpret_cast<u64*>(smem);   // 128 x n_mma doubles as bits (operands are dead)
   if (ok) {
-    // --- epilogue: TMEM lane = real row; stage FP32 rows in shared memory
-    float* stage = reinterpret_cast<float*>(smem);    // 128 x n_mma floats
-    const int row = warp * 32 + (tid & 31);
-    for (int c0 = 0; c0 < n_mma; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    // Epilogue 1: combine the levels of this thread's TMEM lane (real row R).
+    // Warp w reads lanes 32 (w % 4) .. + 31; the two warpgroups split the columns.
+    const int q = warp & 3, half = warp >> 2;
+    const int R = q * 32 + lane;
+    const int er = e_row[R & (MC - 1)];
+    const int cw = round_up((n_mma + 1) / 2, 16);
+    const int cbeg = half * cw, cend = min(n_mma, cbeg + cw);
+    for (int c0 = cbeg; c0 < cend; c0 += 16) {
+      long long T[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) stage[row * n_mma + c0 + i] = v[i];
+      for (int i = 0; i < 16; ++i) T[i] = 0;
+      for (int d = 0; d < L; ++d) {
+        uint32_t v[16];
+        tmem_ld16(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * n_mma + c0), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int sh = s * (L - 1 - d);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) T[i] += acc_int(v[i]) << sh;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int c = c0 + i;
+        stage[R * n_mma + c] = i64_scaled_bits(T[i], er + e_col[c] - s * (L + 1));
+      }
     }
   } else {
-    // give the MMAs still in flight a second bounded wait before TMEM is freed
-    mbar_wait(mb, last_parity);
-    if (tid == 0 && errword) atomicOr(errword, ERRBIT_TIMEOUT);
+    mbar_wait(mb, last_parity);       // second bounded wait for MMAs still in flight
+    if (tid == 0 && g.errword) atomicOr(g.errword, ERRBIT_TIMEOUT);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_d), "r"(tmem_cols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_d), "r"(cfg.tmem_cols));
   }
   if (!ok) return;
 
-  const float* stage = reinterpret_cast<const float*>(smem);
+  // Epilogue 2: alpha = +-1, + beta1 C1 + beta2 C2 + gamma dshift I (all +-1), FP64 store.
   double2* C = g.C + (int64_t)e * g.sC;
-  const double2* C1 = g.C1 ? g.C1 + (int64_t)e * g.sC1 : nullptr;
-  const double2* C2 = g.C2 ? g.C2 + (int64_t)e * g.sC2 : nullptr;
-  double2 dsh = make_double2(0.0, 0.0);
-  if (g.dshift) dsh = cmul(g.gamma, g.dshift[(int64_t)e * g.sD]);
-  const int mt = min(MC, g.m - m0);
+  const double2* C1 = (g.C1 && g.beta1.x != 0.0) ? g.C1 + (int64_t)e * g.sC1 : nullptr;
+  const double2* C2 = (g.C2 && g.beta2.x != 0.0) ? g.C2 + (int64_t)e * g.sC2 : nullptr;
+  const bool na = g.alpha.x < 0, n1 = g.beta1.x < 0, n2 = g.beta2.x < 0, ng = g.gamma.x < 0;
+  const bool has_d = g.dshift && g.gamma.x != 0.0;
+  ulonglong2 dsh = make_ulonglong2(0ull, 0ull);
+  if (has_d) dsh = ld_bits(g.dshift + (int64_t)e * g.sD);
   for (int idx = tid; idx < mt * nt; idx += TC_THREADS) {
     const int r = idx / nt, c = idx % nt;
     const int gr = m0 + r, gc = n0 + c;
-    double2 acc = make_double2((double)stage[r * n_mma + c], (double)stage[(MC + r) * n_mma + c]);
-    double2 v = cmul(acc, g.alpha);
+    u64 re = flip(stage[r * n_mma + c], na);
+    u64 im = flip(stage[(MC + r) * n_mma + c], na);
     if (C1) {
-      double2 x = cmul(g.beta1, C1[(int64_t)gr * g.ldc1 + gc]);
-      v.x += x.x; v.y += x.y;
+      const ulonglong2 x = ld_bits(C1 + (int64_t)gr * g.ldc1 + gc);
+      re = add_bits(re, flip(x.x, n1));
+      im = add_bits(im, flip(x.y, n1));
     }
     if (C2) {
-      double2 x = cmul(g.beta2, C2[(int64_t)gr * g.ldc2 + gc]);
-      v.x += x.x; v.y += x.y;
+      const ulonglong2 x = ld_bits(C2 + (int64_t)gr * g.ldc2 + gc);
+      re = add_bits(re, flip(x.x, n2));
+      im = add_bits(im, flip(x.y, n2));
     }
-    if (g.dshift && gr == gc) { v.x += dsh.x; v.y += dsh.y; }
-    C[(int64_t)gr * g.ldc + gc] = v;
+    if (has_d && gr == gc) {
+      re = add_bits(re, flip(dsh.x, ng));
+      im = add_bits(im, flip(dsh.y, ng));
+    }
+    *reinterpret_cast<ulonglong2*>(C + (int64_t)gr * g.ldc + gc) = make_ulonglong2(re, im);
   }
 }
 
 int g_tc_smem_optin = 0;
 
+bool is_pm1(double2 z) { return z.y == 0.0 && (z.x == 1.0 || z.x == -1.0); }
+bool is_pm1_or_0(double2 z) { return z.y == 0.0 && (z.x == 1.0 || z.x == -1.0 || z.x == 0.0); }
+
+TcCfg tc_config(int n, int k) {
+  TcCfg c;
+  // exact FP32 level-0 sums: K_real * (2^s - 1)^2 < 2^24
+  if (2 * k <= 256) { c.s = 8; c.L = 4; } else { c.s = 7; c.L = 5; }
+  const int cap = (512 / c.L) / 16 * 16;          // TMEM columns per level
+  int nm = round_up(n < 16 ? 16 : n, 16);
+  if (nm > cap) nm = cap;
+  c.n_mma = nm;
+  int tc = 32;
+  while (tc < c.L * nm) tc <<= 1;
+  c.tmem_cols = tc;
+  return c;
+}
+
+size_t tc_smem_bytes(const TcCfg& c) {
+  size_t op = (size_t)c.L * A_SLICE_BYTES + (size_t)c.L * c.n_mma * KR * 2;
+  size_t st = (size_t)128 * c.n_mma * 8;
+  return op > st ? op : st;
+}
+
 }  // namespace
 
 bool zgemm_tc_available() { return true; }
 
-// Largest n per tile: 256 columns of TMEM / MMA N.
-static int tc_n_tile(int n) {
-  int nm = round_up(n < 16 ? 16 : n, 16);
-  return nm > 256 ? 256 : nm;
-}
-
-static size_t tc_smem_bytes(int n_mma) {
-  size_t op = 2 * (size_t)A_BYTES + 2 * (size_t)n_mma * KR * 4;
-  size_t st = (size_t)128 * n_mma * 4;
-  return op > st ? op : st;
-}
-
 cudaError_t zgemm_tc(const ZGemm& g, cudaStream_t st) {
   if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return cudaSuccess;
-  if (g.opA != OP_N || g.opB != OP_N || g.reduce) return cudaErrorNotSupported;
-  if (g.k <= 0) return zgemm_f64(g, st);   // nothing to contract: the FP64 epilogue path
-  const int n_mma = tc_n_tile(g.n);
-  int tmem_cols = 32;
-  while (tmem_cols < n_mma) tmem_cols <<= 1;
-  const int tiles_m = (g.m + MC - 1) / MC, tiles_n = (g.n + n_mma - 1) / n_mma;
-  const size_t sm = tc_smem_bytes(n_mma);
+  if (g.k <= 0) return zgemm_f64(g, st);
+  if (g.opA != OP_N || g.opB != OP_N || g.reduce || g.k > 512 || !is_pm1(g.alpha) ||
+      (g.C1 && !is_pm1_or_0(g.beta1)) || (g.C2 && !is_pm1_or_0(g.beta2)) ||
+      (g.dshift && !is_pm1_or_0(g.gamma)))
+    return cudaErrorNotSupported;
+  const TcCfg cfg = tc_config(g.n, g.k);
+  const int tiles_m = (g.m + MC - 1) / MC, tiles_n = (g.n + cfg.n_mma - 1) / cfg.n_mma;
+  const size_t sm = tc_smem_bytes(cfg);
   if ((int)sm > g_tc_smem_optin) return cudaErrorInvalidValue;
   dim3 grid(tiles_m * tiles_n, g.batch);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  zgemm_tc_kernel<<<grid, TC_THREADS, sm, st>>>(g, tiles_n, n_mma, tmem_cols, g.errword);
+  zgemm_tc_kernel<<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
   return cudaGetLastError();
 }
 

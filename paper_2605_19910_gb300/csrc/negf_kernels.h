@@ -13,7 +13,8 @@ enum Op : int { OP_N = 0, OP_C = 1 /* conjugate transpose */ };
 //          + gamma * dshift[e] * I
 // Every operand X[e] lives at X + e * sX (sX = 0 shares one block across the
 // batch); blocks are row-major with leading dimension ldX.  C1/C2/dshift may
-// be null.  With reduce != 0 the batch is summed into one C:
+// be null.  With weight != null, op(A[e]) is scaled by the real weight[e].
+// With reduce != 0 the batch is summed into one C:
 //   C = alpha * sum_e weight[e] * op(A[e]) op(B[e]) + beta1 * C1.
 struct ZGemm {
   int m = 0, n = 0, k = 0;
@@ -54,6 +55,9 @@ cudaError_t assemble_diag(const double2* H, const double2* E, const double2* ext
 // Strided batched block copy: dst[e] = src[e] (rows x cols, row-major, ld = cols).
 cudaError_t copy_blocks(const double2* src, int64_t sSrc, double2* dst, int64_t sDst, int64_t elems,
                         int batch, cudaStream_t st);
+
+// D[e] = I (b x b).
+cudaError_t set_identity(double2* D, int64_t sD, int b, int batch, cudaStream_t st);
 
 // Gam[e] = i (Sig[e] - Sig[e]^H)   (b x b).
 cudaError_t gamma_from_sigma(const double2* sig, int64_t sSig, double2* gam, int64_t sGam, int b,

@@ -82,6 +82,17 @@ __global__ void trace_prod_kernel(const double2* __restrict__ P, int64_t sP, con
   }
 }
 
+__global__ void set_identity_kernel(double2* __restrict__ D, int64_t sD, int b) {
+  const int e = blockIdx.y;
+  double2* d = D + (int64_t)e * sD;
+  const int64_t n = (int64_t)b * b;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(idx / b), c = (int)(idx - (int64_t)r * b);
+    d[idx] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
+}
+
 inline int grid_x_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
@@ -102,6 +113,13 @@ cudaError_t copy_blocks(const double2* src, int64_t sSrc, double2* dst, int64_t 
   if (batch <= 0 || elems <= 0) return cudaSuccess;
   dim3 grid(grid_x_for(elems, 256), batch);
   copy_blocks_kernel<<<grid, 256, 0, st>>>(src, sSrc, dst, sDst, elems);
+  return cudaGetLastError();
+}
+
+cudaError_t set_identity(double2* D, int64_t sD, int b, int batch, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  dim3 grid(grid_x_for((int64_t)b * b, 256), batch);
+  set_identity_kernel<<<grid, 256, 0, st>>>(D, sD, b);
   return cudaGetLastError();
 }
 

@@ -56,3 +56,8 @@ def test_mixed_full_batched64x64_sampled(P, torch):
     prob = workload("batched64x64")
     run_and_compare(P, torch, prob, energies_idx=[0, 100, 255, 256, 383, 511], tol=MIXED_TOL,
                     precision="mixed")
+
+
+def test_mixed_variable_sizes_many_energies(P, torch):
+    prob = make_problem(14, b=None, size_range=(2, 60), w=1, n_energies=9, eta=1e-3, seed=15)
+    run_and_compare(P, torch, prob, tol=MIXED_TOL, precision="mixed")

@@ -177,3 +177,21 @@ def test_argument_errors(P, torch):
     assert P.negf_solve(plan.handle, None, None, None, 0, None, None, None, None) == P.NEGF_ERR_ARG
     assert P.negf_transmission(plan.handle, None, None, None, 0, None, None, None) == P.NEGF_ERR_ARG
     plan.close()
+
+
+def test_variable_sizes_many_energies_concurrent_groups(P, torch):
+    # energy groups run concurrently on forked streams and sit at different
+    # layers of different block sizes: the shared window slots must not overlap
+    prob = make_problem(14, b=None, size_range=(2, 60), w=1, n_energies=9, eta=1e-3, seed=15)
+    run_and_compare(P, torch, prob)
+    prob = make_problem(12, b=None, size_range=(2, 40), w=2, n_energies=7, eta=1e-3, seed=16)
+    run_and_compare(P, torch, prob)
+
+
+def test_single_layer_with_distinct_leads(P, torch):
+    # N = 1: Sigma_L and Sigma_R both act on the one layer and must both enter
+    rng = np.random.default_rng(12)
+    prob = make_problem(1, b=6, w=1, n_energies=2, eta=1e-2, seed=12)
+    prob.sigma_L = -0.3j * np.eye(6) + 0.2 * rng.normal(size=(6, 6))
+    prob.sigma_R = -0.7j * np.eye(6) + 0.1 * rng.normal(size=(6, 6))
+    run_and_compare(P, torch, prob)
