@@ -56,6 +56,22 @@ cudaError_t assemble_diag(const double2* H, const double2* E, const double2* ext
 cudaError_t copy_blocks(const double2* src, int64_t sSrc, double2* dst, int64_t sDst, int64_t elems,
                         int batch, cudaStream_t st);
 
+// Strided 2-D block copy / update over a batch:
+//   dst[e](r, c) = (acc ? dst[e](r, c) : 0) + scale * src[e](r, c)
+// src[e] = src + e * sSrc (sSrc = 0 broadcasts), row-major with leading
+// dimensions ldSrc / ldDst.
+cudaError_t copy2d(const double2* src, int64_t sSrc, int ldSrc, double2* dst, int64_t sDst, int ldDst,
+                   int rows, int cols, double scale, int acc, int batch, cudaStream_t st);
+
+// dst[e] = zeros(rows x cols) with ones at (i, off + i) (cols_mode) or
+// (off + i, i) (rows mode), i = 0 .. nid-1.
+cudaError_t set_eye(double2* dst, int64_t sDst, int ld, int rows, int cols, int off, int nid, int rows_mode,
+                    int batch, cudaStream_t st);
+
+// dst[e](i, i) += scale * s[e] for i < n (s: per-energy complex scalars, stride sS).
+cudaError_t add_diag(double2* dst, int64_t sDst, int ld, int n, const double2* s, int64_t sS, double scale,
+                     int batch, cudaStream_t st);
+
 // D[e] = I (b x b).
 cudaError_t set_identity(double2* D, int64_t sD, int b, int batch, cudaStream_t st);
 

@@ -93,6 +93,51 @@ __global__ void set_identity_kernel(double2* __restrict__ D, int64_t sD, int b) 
   }
 }
 
+__global__ void copy2d_kernel(const double2* __restrict__ src, int64_t sSrc, int ldSrc, double2* __restrict__ dst,
+                              int64_t sDst, int ldDst, int rows, int cols, double scale, int acc) {
+  const int e = blockIdx.y;
+  const double2* sp = src + (int64_t)e * sSrc;
+  double2* dp = dst + (int64_t)e * sDst;
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / cols), c = (int)(idx - (int64_t)r * cols);
+    const double2 v = sp[(int64_t)r * ldSrc + c];
+    double2 o = acc ? dp[(int64_t)r * ldDst + c] : make_double2(0.0, 0.0);
+    o.x = fma(scale, v.x, o.x);
+    o.y = fma(scale, v.y, o.y);
+    dp[(int64_t)r * ldDst + c] = o;
+  }
+}
+
+__global__ void set_eye_kernel(double2* __restrict__ dst, int64_t sDst, int ld, int rows, int cols, int off,
+                               int nid, int rows_mode) {
+  const int e = blockIdx.y;
+  double2* dp = dst + (int64_t)e * sDst;
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / cols), c = (int)(idx - (int64_t)r * cols);
+    const int i = rows_mode ? r - off : c - off;
+    const int j = rows_mode ? c : r;
+    const bool one = (i >= 0 && i < nid && i == j);
+    dp[(int64_t)r * ld + c] = make_double2(one ? 1.0 : 0.0, 0.0);
+  }
+}
+
+__global__ void add_diag_kernel(double2* __restrict__ dst, int64_t sDst, int ld, int n, const double2* __restrict__ sv,
+                                int64_t sS, double scale) {
+  const int e = blockIdx.y;
+  double2* dp = dst + (int64_t)e * sDst;
+  const double2 v = sv[(int64_t)e * sS];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double2 o = dp[(int64_t)i * ld + i];
+    o.x = fma(scale, v.x, o.x);
+    o.y = fma(scale, v.y, o.y);
+    dp[(int64_t)i * ld + i] = o;
+  }
+}
+
 inline int grid_x_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
@@ -113,6 +158,30 @@ cudaError_t copy_blocks(const double2* src, int64_t sSrc, double2* dst, int64_t 
   if (batch <= 0 || elems <= 0) return cudaSuccess;
   dim3 grid(grid_x_for(elems, 256), batch);
   copy_blocks_kernel<<<grid, 256, 0, st>>>(src, sSrc, dst, sDst, elems);
+  return cudaGetLastError();
+}
+
+cudaError_t copy2d(const double2* src, int64_t sSrc, int ldSrc, double2* dst, int64_t sDst, int ldDst,
+                   int rows, int cols, double scale, int acc, int batch, cudaStream_t st) {
+  if (batch <= 0 || rows <= 0 || cols <= 0) return cudaSuccess;
+  dim3 grid(grid_x_for((int64_t)rows * cols, 256), batch);
+  copy2d_kernel<<<grid, 256, 0, st>>>(src, sSrc, ldSrc, dst, sDst, ldDst, rows, cols, scale, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t set_eye(double2* dst, int64_t sDst, int ld, int rows, int cols, int off, int nid, int rows_mode,
+                    int batch, cudaStream_t st) {
+  if (batch <= 0 || rows <= 0 || cols <= 0) return cudaSuccess;
+  dim3 grid(grid_x_for((int64_t)rows * cols, 256), batch);
+  set_eye_kernel<<<grid, 256, 0, st>>>(dst, sDst, ld, rows, cols, off, nid, rows_mode);
+  return cudaGetLastError();
+}
+
+cudaError_t add_diag(double2* dst, int64_t sDst, int ld, int n, const double2* s, int64_t sS, double scale,
+                     int batch, cudaStream_t st) {
+  if (batch <= 0 || n <= 0) return cudaSuccess;
+  dim3 grid(grid_x_for(n, 128), batch);
+  add_diag_kernel<<<grid, 128, 0, st>>>(dst, sDst, ld, n, s, sS, scale);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,71 @@
+"""Parity of the CUDA DDRGF path (Alg. 2: per-domain extended RGF, FP64
+interface Schur system, stitching) with the oracle, through the C-ABI."""
+import numpy as np
+import pytest
+
+from gpu_parity import FP64_TOL, MIXED_TOL, band_rel_err, rel_err, to_dev
+from oracle import rgf as O
+from workloads import make_problem, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2605_19910_gb300 as P
+    return P
+
+
+def run_dd(P, prob, n_domains, first=None, idx=None, tol=FP64_TOL, precision="fp64", check_ddrgf_oracle=False):
+    import torch
+    Hp, sL, sR, E = to_dev(prob, torch)
+    nE = len(prob.energies)
+    plan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, n_domains=n_domains, domain_first_block=first,
+                  precision=precision, outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_G1N | P.NEGF_OUT_TRANSMISSION)
+    Gb, G1 = plan.solve(Hp, sL, sR, E)
+    T = plan.transmission(Hp, sL, sR, E)
+    assert not plan.info.cpu().numpy().any()
+    plan.close()
+    Gb, G1, T = Gb.cpu().numpy(), G1.cpu().numpy(), T.cpu().numpy()
+    for e in (range(nE) if idx is None else idx):
+        M = O.system_blocks(prob, prob.energies[e])
+        ref = O.rgf_selected(M, prob.sizes, prob.w, first_row=True)
+        assert band_rel_err(Gb[e], ref["band"], prob.sizes, prob.w) < tol, e
+        assert rel_err(G1[e], ref["G1N"]) < tol, e
+        Tref = O.transmission(ref["G1N"], prob.sigma_L, prob.sigma_R)
+        assert abs(T[e] - Tref) < tol * max(1.0, abs(Tref)), (e, T[e], Tref)
+        if check_ddrgf_oracle:
+            dd = O.ddrgf_selected(M, prob.sizes, prob.w, n_domains, first)
+            assert band_rel_err(Gb[e], dd["band"], prob.sizes, prob.w) < tol, e
+
+
+@pytest.mark.parametrize("w,N,nd", [(1, 20, 4), (1, 9, 2), (2, 24, 3), (2, 30, 5)])
+def test_ddrgf_uniform(P, w, N, nd):
+    prob = make_problem(N, b=8, w=w, n_energies=3, eta=1e-3, seed=40 + N)
+    run_dd(P, prob, nd, check_ddrgf_oracle=True)
+
+
+def test_ddrgf_variable_sizes_and_explicit_split(P):
+    prob = make_problem(17, b=None, size_range=(3, 20), w=1, n_energies=4, eta=1e-3, seed=47)
+    run_dd(P, prob, 3, first=[0, 5, 12])
+    prob = make_problem(19, b=None, size_range=(2, 12), w=2, n_energies=3, eta=1e-3, seed=48)
+    run_dd(P, prob, 3, first=[0, 6, 11])
+
+
+def test_ddrgf_default_split_balances_block_weights(P):
+    prob = make_problem(16, b=None, size_range=(4, 30), w=1, n_energies=2, eta=1e-3, seed=49)
+    run_dd(P, prob, 4)
+
+
+def test_ddrgf_mixed_precision(P):
+    prob = make_problem(24, b=32, w=2, n_energies=4, eta=1e-6, seed=50)
+    run_dd(P, prob, 3, tol=MIXED_TOL, precision="mixed")
+
+
+def test_ddrgf_penta256x32_full_size_sampled(P):
+    """256 blocks x b = 32, n = 5, 1024 energies, 8 domains, mixed precision
+    with the FP64 interface system: sampled energies against the oracle."""
+    prob = workload("penta256x32")
+    run_dd(P, prob, 8, idx=[0, 301, 511, 512, 1023], tol=MIXED_TOL, precision="mixed")
