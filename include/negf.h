@@ -86,8 +86,14 @@ typedef struct {
   const int32_t* block_sizes;         /* host array of N sizes b_i, 1 <= b_i <= NEGF_MAX_BLOCK */
   int32_t band_n;                     /* n = 3 or 5 (w = (n-1)/2)              */
   int32_t n_energies;                 /* >= 1                                  */
-  int32_t n_domains;                  /* 1 = plain RGF, >1 = single-level DDRGF */
-  const int32_t* domain_first_block;  /* host, n_domains entries or NULL       */
+  int32_t n_domains;                  /* 1 = plain RGF, >1 = single-level DDRGF
+                                         (Alg. 2; always computed in FP64)     */
+  const int32_t* domain_first_block;  /* host, n_domains entries or NULL: first
+                                         layer of each (D2, D1) pair; pair j is
+                                         D2_j then a separator D1_j of w layers;
+                                         entry 0 must be 0, every pair must have
+                                         at least 2w layers.  NULL balances the
+                                         pairs by sum of b_i^3 (Sec. 3).        */
   int32_t precision;                  /* negf_precision                        */
   int32_t refine_steps;               /* 0 or 1 (NEGF_MIXED only)              */
   int32_t outputs;                    /* NEGF_OUT_* bit mask                   */

@@ -569,6 +569,10 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   if (!p) return NEGF_ERR_NOMEM;
   p->N = d->n_blocks; p->w = w; p->nE = d->n_energies; p->n_domains = d->n_domains;
   p->precision = d->precision; p->refine = d->refine_steps; p->outputs = d->outputs;
+  // DDRGF runs in FP64 throughout: its sub-domains are closed systems (only
+  // the broadening eta), where the halo chains amplify rounding far beyond
+  // what 32-bit products leave.
+  if (p->n_domains > 1) p->precision = NEGF_FP64;
   p->ckpt = d->checkpoint_every;
   p->b.assign(d->block_sizes, d->block_sizes + d->n_blocks);
   p->stream = (cudaStream_t)cuda_stream;

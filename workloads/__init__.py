@@ -66,7 +66,7 @@ def rect_identity(m, n):
 
 def make_problem(n_blocks, b=None, w=1, n_energies=1, eta=1e-6, seed=0,
                  energy=None, size_range=None, coupling_noise=0.1,
-                 next_coupling=0.3, sigma=-0.5j):
+                 next_coupling=0.3, sigma=-0.5j, diag_shift=0.0):
     """Build one synthetic nanowire-shaped problem.
 
     ``b``: uniform block size, or ``None`` with ``size_range=(lo, hi)`` for
@@ -83,7 +83,7 @@ def make_problem(n_blocks, b=None, w=1, n_energies=1, eta=1e-6, seed=0,
     H = {}
     for i in range(N):
         A = cn(rng, (sizes[i], sizes[i]), 1.0 / sizes[i])
-        H[(i, i)] = (A + A.conj().T) / 2.0
+        H[(i, i)] = (A + A.conj().T) / 2.0 + diag_shift * np.eye(sizes[i])
     for i in range(N - 1):
         C = cn(rng, (sizes[i], sizes[i + 1]), 1.0 / sizes[i])
         H[(i, i + 1)] = rect_identity(sizes[i], sizes[i + 1]) + coupling_noise * C
