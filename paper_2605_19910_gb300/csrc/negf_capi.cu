@@ -90,9 +90,10 @@ struct negf_plan_s {
   double2* band_ws = nullptr;   // band of one chunk when the caller keeps no band output
 
   // independent energy groups run on forked streams (graph branches)
-  int groups = 2;
+  int groups = 4;
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;   // [0] fork, [1..] joins
+  std::vector<cudaEvent_t> stagger;   // group g -> g + 1 start dependency
 
   // optional per-launch timing (negf_profile_enable)
   bool profiling = false;
@@ -142,6 +143,7 @@ struct Sweep {
   int e0, ne;         // energy range of this sweep
   int wofs = 0;       // energy offset of this range inside the chunk workspace
   int gb_e0 = 0;      // energy index of Gband[0] (0: caller's buffer; chunk start: internal buffer)
+  cudaEvent_t after_first_inv = nullptr;   // recorded once, after this sweep's first inversion
 
   // Every kernel launch of the schedule goes through here so that the
   // optional profiler can bracket it with events on the launching stream.
@@ -170,9 +172,14 @@ struct Sweep {
     return launch(NEGF_PROF_GEMM_F64, gemm_flops(g), [&] { return negf::zgemm_f64(g, st); });
   }
   cudaError_t inv(const double2* S, int64_t sS, double2* T, int64_t sT, int b, int batch, int layer1) {
-    return launch(NEGF_PROF_INV, 8.0 * b * (double)b * b * batch, [&] {
+    NEGF_TRY(launch(NEGF_PROF_INV, 8.0 * b * (double)b * b * batch, [&] {
       return negf::zinv_f64(S, sS, T, sT, b, batch, info + e0, layer1, p->d_err, st);
-    });
+    }));
+    if (after_first_inv) {
+      NEGF_TRY(cudaEventRecord(after_first_inv, st));
+      after_first_inv = nullptr;
+    }
+    return cudaSuccess;
   }
   template <class F>
   cudaError_t misc(F f) { return launch(NEGF_PROF_MISC, 0.0, f); }
@@ -752,9 +759,11 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
       p->side.push_back(s2);
     }
     for (int g = 0; g < p->groups; ++g) {
-      cudaEvent_t e2 = nullptr;
+      cudaEvent_t e2 = nullptr, e3 = nullptr;
       if (cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
       p->ev.push_back(e2);
+      if (cudaEventCreateWithFlags(&e3, cudaEventDisableTiming) != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
+      p->stagger.push_back(e3);
     }
   }
   *out = p;
@@ -777,6 +786,7 @@ void negf_destroy(negf_plan_t* p) {
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   for (auto s2 : p->side) cudaStreamDestroy(s2);
   for (auto e2 : p->ev) cudaEventDestroy(e2);
+  for (auto e3 : p->stagger) cudaEventDestroy(e3);
   cudaFree(p->ws);
   cudaFree(p->d_err);
   delete p;
@@ -1172,6 +1182,11 @@ cudaError_t for_groups(negf_plan_s* p, Sweep base, F f) {
     s.e0 = base.e0 + lo;
     s.ne = hi - lo;
     s.wofs = base.wofs + lo;
+    // Stagger: group g starts after the first inversion of group g-1, so
+    // that one group's block products (tensor / integer pipes) run while the
+    // next group inverts (FP64 pipe) instead of both alternating in step.
+    if (g > 0) NEGF_TRY(cudaStreamWaitEvent(s.st, p->stagger[g - 1], 0));
+    if (g + 1 < G) s.after_first_inv = p->stagger[g];
     NEGF_TRY(f(s));
   }
   for (int g = 1; g < G; ++g) {

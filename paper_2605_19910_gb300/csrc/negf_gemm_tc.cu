@@ -47,7 +47,8 @@ namespace {
 
 constexpr int TC_THREADS = 256;             // two warpgroups
 constexpr int MC = 64;                       // complex rows per CTA (M = 128 real)
-constexpr int KC = 32;                       // complex K per chunk
+constexpr int KC = 16;                       // complex K per chunk
+constexpr int KG = KC / 8;                   // 8-element K groups per chunk and part
 constexpr int KR = 2 * KC;                   // real K per chunk (BF16 elements per row)
 constexpr int CORE = 128;                    // 8 rows x 16 bytes
 constexpr int LBO = CORE;                    // bytes between 16-byte K groups
@@ -296,8 +297,8 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles
     // Pass 2a: slices of A, 8 consecutive K per thread item, one 16-byte
     // core-matrix row per store.  Row r holds [Re A | -Im A], row 64 + r
     // holds [Im A | Re A].
-    for (int item = tid; item < MC * (KC / 8); item += TC_THREADS) {
-      const int r = item >> 2, kg = item & 3;
+    for (int item = tid; item < MC * KG; item += TC_THREADS) {
+      const int r = item / KG, kg = item % KG;
       const int gr = m0 + r;
       const int er = e_row[r];
       u64 fre[8], fim[8];
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles
       }
     }
     // Pass 2b: slices of B^T (K-major): row c holds [Re B(:, c) | Im B(:, c)].
-    for (int item = tid; item < n_mma * (KC / 8); item += TC_THREADS) {
+    for (int item = tid; item < n_mma * KG; item += TC_THREADS) {
       const int c = item % n_mma, kg = item / n_mma;
       const int ec = e_col[c];
       u64 fre[8], fim[8];
@@ -398,32 +399,66 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-  u64* stage = reinterpret_cast<u64*>(smem);   // 128 x n_mma doubles as bits (operands are dead)
+  // Epilogue in passes of EP columns (keeps the staging buffer small so that
+  // this kernel can share an SM with the FP64 inversion kernel).
+  constexpr int EP = 32;
+  u64* stage = reinterpret_cast<u64*>(smem);   // 128 x (EP + 1) doubles as bits (operands are dead)
+  constexpr int lds = EP + 1;                   // padded rows: conflict-free per-lane row writes
+  double2* C = g.C + (int64_t)e * g.sC;
+  const double2* C1 = (g.C1 && g.beta1.x != 0.0) ? g.C1 + (int64_t)e * g.sC1 : nullptr;
+  const double2* C2 = (g.C2 && g.beta2.x != 0.0) ? g.C2 + (int64_t)e * g.sC2 : nullptr;
+  const bool na = g.alpha.x < 0, n1 = g.beta1.x < 0, n2 = g.beta2.x < 0, ng = g.gamma.x < 0;
+  const bool has_d = g.dshift && g.gamma.x != 0.0;
+  ulonglong2 dsh = make_ulonglong2(0ull, 0ull);
+  if (has_d) dsh = ld_bits(g.dshift + (int64_t)e * g.sD);
   if (ok) {
-    // Epilogue 1: combine the levels of this thread's TMEM lane (real row R).
-    // Warp w reads lanes 32 (w % 4) .. + 31; the two warpgroups split the columns.
-    const int q = warp & 3, half = warp >> 2;
+    const int q = warp & 3, half = warp >> 2;   // warp w reads TMEM lanes 32 (w % 4) .. + 31
     const int R = q * 32 + lane;
     const int er = e_row[R & (MC - 1)];
-    const int cw = round_up((n_mma + 1) / 2, 16);
-    const int cbeg = half * cw, cend = min(n_mma, cbeg + cw);
-    for (int c0 = cbeg; c0 < cend; c0 += 16) {
-      long long T[16];
+    for (int p0 = 0; p0 < n_mma; p0 += EP) {
+      // Epilogue 1: combine the levels of this lane's real row for 16 columns
+      const int c0 = p0 + 16 * half;
+      if (c0 < n_mma) {
+        long long T[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) T[i] = 0;
-      for (int d = 0; d < L; ++d) {
-        uint32_t v[16];
-        tmem_ld16(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * n_mma + c0), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int sh = s * (L - 1 - d);
+        for (int i = 0; i < 16; ++i) T[i] = 0;
+        for (int d = 0; d < L; ++d) {
+          uint32_t v[16];
+          tmem_ld16(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * n_mma + c0), v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int sh = s * (L - 1 - d);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) T[i] += acc_int(v[i]) << sh;
+          for (int i = 0; i < 16; ++i) T[i] += acc_int(v[i]) << sh;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          stage[R * lds + 16 * half + i] = i64_scaled_bits(T[i], er + e_col[c0 + i] - s * (L + 1));
       }
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int c = c0 + i;
-        stage[R * n_mma + c] = i64_scaled_bits(T[i], er + e_col[c] - s * (L + 1));
+      __syncthreads();
+      // Epilogue 2: alpha = +-1, + beta1 C1 + beta2 C2 + gamma dshift I (all +-1), FP64 store.
+      const int pc = min(EP, nt - p0);
+      for (int idx = tid; idx < mt * pc; idx += TC_THREADS) {
+        const int r = idx / pc, cl = idx % pc;
+        const int gr = m0 + r, gc = n0 + p0 + cl;
+        u64 re = flip(stage[r * lds + cl], na);
+        u64 im = flip(stage[(MC + r) * lds + cl], na);
+        if (C1) {
+          const ulonglong2 x = ld_bits(C1 + (int64_t)gr * g.ldc1 + gc);
+          re = add_bits(re, flip(x.x, n1));
+          im = add_bits(im, flip(x.y, n1));
+        }
+        if (C2) {
+          const ulonglong2 x = ld_bits(C2 + (int64_t)gr * g.ldc2 + gc);
+          re = add_bits(re, flip(x.x, n2));
+          im = add_bits(im, flip(x.y, n2));
+        }
+        if (has_d && gr == gc) {
+          re = add_bits(re, flip(dsh.x, ng));
+          im = add_bits(im, flip(dsh.y, ng));
+        }
+        *reinterpret_cast<ulonglong2*>(C + (int64_t)gr * g.ldc + gc) = make_ulonglong2(re, im);
       }
+      __syncthreads();
     }
   } else {
     mbar_wait(mb, last_parity);       // second bounded wait for MMAs still in flight
@@ -433,37 +468,6 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_d), "r"(cfg.tmem_cols));
-  }
-  if (!ok) return;
-
-  // Epilogue 2: alpha = +-1, + beta1 C1 + beta2 C2 + gamma dshift I (all +-1), FP64 store.
-  double2* C = g.C + (int64_t)e * g.sC;
-  const double2* C1 = (g.C1 && g.beta1.x != 0.0) ? g.C1 + (int64_t)e * g.sC1 : nullptr;
-  const double2* C2 = (g.C2 && g.beta2.x != 0.0) ? g.C2 + (int64_t)e * g.sC2 : nullptr;
-  const bool na = g.alpha.x < 0, n1 = g.beta1.x < 0, n2 = g.beta2.x < 0, ng = g.gamma.x < 0;
-  const bool has_d = g.dshift && g.gamma.x != 0.0;
-  ulonglong2 dsh = make_ulonglong2(0ull, 0ull);
-  if (has_d) dsh = ld_bits(g.dshift + (int64_t)e * g.sD);
-  for (int idx = tid; idx < mt * nt; idx += TC_THREADS) {
-    const int r = idx / nt, c = idx % nt;
-    const int gr = m0 + r, gc = n0 + c;
-    u64 re = flip(stage[r * n_mma + c], na);
-    u64 im = flip(stage[(MC + r) * n_mma + c], na);
-    if (C1) {
-      const ulonglong2 x = ld_bits(C1 + (int64_t)gr * g.ldc1 + gc);
-      re = add_bits(re, flip(x.x, n1));
-      im = add_bits(im, flip(x.y, n1));
-    }
-    if (C2) {
-      const ulonglong2 x = ld_bits(C2 + (int64_t)gr * g.ldc2 + gc);
-      re = add_bits(re, flip(x.x, n2));
-      im = add_bits(im, flip(x.y, n2));
-    }
-    if (has_d && gr == gc) {
-      re = add_bits(re, flip(dsh.x, ng));
-      im = add_bits(im, flip(dsh.y, ng));
-    }
-    *reinterpret_cast<ulonglong2*>(C + (int64_t)gr * g.ldc + gc) = make_ulonglong2(re, im);
   }
 }
 
@@ -488,7 +492,7 @@ TcCfg tc_config(int n, int k) {
 
 size_t tc_smem_bytes(const TcCfg& c) {
   size_t op = (size_t)c.L * A_SLICE_BYTES + (size_t)c.L * c.n_mma * KR * 2;
-  size_t st = (size_t)128 * c.n_mma * 8;
+  size_t st = (size_t)128 * (32 + 1) * 8;
   return op > st ? op : st;
 }
 

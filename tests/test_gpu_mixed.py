@@ -61,3 +61,8 @@ def test_mixed_full_batched64x64_sampled(P, torch):
 def test_mixed_variable_sizes_many_energies(P, torch):
     prob = make_problem(14, b=None, size_range=(2, 60), w=1, n_energies=9, eta=1e-3, seed=15)
     run_and_compare(P, torch, prob, tol=MIXED_TOL, precision="mixed")
+
+
+def test_mixed_nanowire_block_sizes_96_to_160(P, torch):
+    prob = make_problem(6, b=None, size_range=(96, 160), w=1, n_energies=2, eta=1e-3, seed=61)
+    run_and_compare(P, torch, prob, tol=MIXED_TOL, precision="mixed")

@@ -195,3 +195,15 @@ def test_single_layer_with_distinct_leads(P, torch):
     prob.sigma_L = -0.3j * np.eye(6) + 0.2 * rng.normal(size=(6, 6))
     prob.sigma_R = -0.7j * np.eye(6) + 0.1 * rng.normal(size=(6, 6))
     run_and_compare(P, torch, prob)
+
+
+@pytest.mark.parametrize("b", [120, 127, 160])
+def test_large_blocks_cluster_inversion(P, torch, b):
+    # blocks above one CTA's shared memory: two-CTA cluster inversion
+    prob = make_problem(3, b=b, w=1, n_energies=3, eta=1e-3, seed=b)
+    run_and_compare(P, torch, prob)
+
+
+def test_nanowire_block_sizes_96_to_160(P, torch):
+    prob = make_problem(6, b=None, size_range=(96, 160), w=1, n_energies=2, eta=1e-3, seed=61)
+    run_and_compare(P, torch, prob)
