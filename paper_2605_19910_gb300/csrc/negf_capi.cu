@@ -66,7 +66,7 @@ struct negf_plan_s {
   double2* LC_ws = nullptr;     // grad: last column g_i (b_i x b_N)
   std::vector<int64_t> p_off;
   int64_t p_elems = 0;
-  double2* Gint = nullptr;      // grad: internal first-row / scratch
+  double2* RF_ws = nullptr;     // refinement: correction blocks (b_i x b_N)
   double2* scratch = nullptr;   // transmission: Gamma_L, Gamma_R, P, Q per energy
   int64_t scr_elems = 0;
   double2* G1N_ws = nullptr;    // G_1N when the caller does not keep it
@@ -403,44 +403,118 @@ struct Sweep {
   //   P_{N} = I,  P_i = -Y_{i,i+1} P_{i+1}            (U^{-1} e_N)
   //   G_{1,N}' = t_1 P_1,  G_{i,N} = t_i P_i - X_{i,i-1} G_{i-1,N}.
   cudaError_t last_column() {
-    const int N = p->N, C = ne, bN = p->b[N - 1];
-    const int64_t sI = sq(bN);
-    // P_{N-1} = I: assemble_diag with E = 1 and H = 0 is not available; use a
-    // k = 0 product: C = gamma * 1 * I with dshift = 1 from a constant.
-    for (int i = N - 1; i >= 0; --i) {
+    const int N = p->N, w = p->w, C = ne, bN = p->b[N - 1];
+    for (int i = N - 1; i >= 0; --i) {   // P = U^{-1} e_N
       const int bi = p->b[i];
       if (i == N - 1) {
-        NEGF_TRY(misc([&] { return negf::set_identity(Pblk(i), sI, bN, C, st); }));
+        NEGF_TRY(misc([&] { return negf::set_identity(Pblk(i), sq(bN), bN, C, st); }));
         continue;
       }
-      ZGemm g;   // P_i = -Y_{i,i+1} P_{i+1}
-      g.m = bi; g.n = bN; g.k = p->b[i + 1];
-      g.A = Yblk(i, i + 1); g.sA = (int64_t)bi * p->b[i + 1]; g.lda = p->b[i + 1];
-      g.B = Pblk(i + 1); g.sB = (int64_t)p->b[i + 1] * bN; g.ldb = bN;
-      g.C = Pblk(i); g.sC = (int64_t)bi * bN; g.ldc = bN; g.alpha = {-1.0, 0.0};
-      g.batch = C;
-      NEGF_TRY(gemm(g));
+      for (int c = i + 1; c <= std::min(N - 1, i + w); ++c) {   // P_i = -sum_c Y_{i,c} P_c
+        ZGemm g;
+        g.m = bi; g.n = bN; g.k = p->b[c];
+        g.A = Yblk(i, c); g.sA = (int64_t)bi * p->b[c]; g.lda = p->b[c];
+        g.B = Pblk(c); g.sB = (int64_t)p->b[c] * bN; g.ldb = bN;
+        g.C = Pblk(i); g.sC = (int64_t)bi * bN; g.ldc = bN; g.alpha = {-1.0, 0.0};
+        if (c > i + 1) { g.C1 = Pblk(i); g.sC1 = (int64_t)bi * bN; g.ldc1 = bN; g.beta1 = {1.0, 0.0}; }
+        g.batch = C;
+        NEGF_TRY(gemm(g));
+      }
     }
-    for (int i = 0; i < N; ++i) {
+    for (int i = 0; i < N; ++i) {        // G_{i,N} = t_i P_i - sum_c X_{i,c} G_{c,N}
       const int bi = p->b[i];
-      ZGemm g;   // G_{i,N} = t_i P_i (- X_{i,i-1} G_{i-1,N} below)
+      ZGemm g;
       g.m = bi; g.n = bN; g.k = bi;
       g.A = Tblk(i); g.sA = sq(bi); g.lda = bi;
       g.B = Pblk(i); g.sB = (int64_t)bi * bN; g.ldb = bN;
       g.C = LCblk(i); g.sC = (int64_t)bi * bN; g.ldc = bN;
       g.batch = C;
       NEGF_TRY(gemm(g));
-      if (i > 0) {
+      for (int c = std::max(0, i - w); c < i; ++c) {
         ZGemm h;
-        h.m = bi; h.n = bN; h.k = p->b[i - 1];
-        h.A = Xblk(i, i - 1); h.sA = (int64_t)bi * p->b[i - 1]; h.lda = p->b[i - 1];
-        h.B = LCblk(i - 1); h.sB = (int64_t)p->b[i - 1] * bN; h.ldb = bN;
+        h.m = bi; h.n = bN; h.k = p->b[c];
+        h.A = Xblk(i, c); h.sA = (int64_t)bi * p->b[c]; h.lda = p->b[c];
+        h.B = LCblk(c); h.sB = (int64_t)p->b[c] * bN; h.ldb = bN;
         h.C = LCblk(i); h.sC = (int64_t)bi * bN; h.ldc = bN; h.alpha = {-1.0, 0.0};
         h.C1 = LCblk(i); h.sC1 = (int64_t)bi * bN; h.ldc1 = bN; h.beta1 = {1.0, 0.0};
         h.batch = C;
         NEGF_TRY(gemm(h));
       }
     }
+    return cudaSuccess;
+  }
+
+  // One step of iterative refinement of the last block column x = M^{-1} e_N
+  // (mixed precision; gives G_1N = x_1 and T(E) to FP64-level accuracy):
+  //   r = e_N - M x with FP64-accurate products (56-bit tensor-core split,
+  //       exact integer accumulation, the E x term in FP64),
+  //   d = L^{-1} D^{-1} U^{-1} r with the stored mixed factors, x <- x + d.
+  // r / v live in the P region (free after last_column), q / d in RF.
+  double2* RFblk(int i) const { return p->RF_ws + p->p_off[i] * p->chunk + (int64_t)wofs * p->b[i] * p->b[p->N - 1]; }
+  cudaError_t refine_last_column() {
+    const int N = p->N, w = p->w, C = ne, bN = p->b[N - 1];
+    auto hx = [&](int i, int c, const double2* Aop, int64_t sA, int lda, double2* out, bool acc) {
+      ZGemm g;   // out (+)= Aop * x_c, 56-bit products
+      g.m = p->b[i]; g.n = bN; g.k = p->b[c];
+      g.A = Aop; g.sA = sA; g.lda = lda;
+      g.B = LCblk(c); g.sB = (int64_t)p->b[c] * bN; g.ldb = bN;
+      g.C = out; g.sC = (int64_t)p->b[i] * bN; g.ldc = bN;
+      if (acc) { g.C1 = out; g.sC1 = g.sC; g.ldc1 = bN; g.beta1 = {1.0, 0.0}; }
+      g.bits = 56;
+      g.batch = C;
+      return gemm(g);
+    };
+    for (int i = 0; i < N; ++i) {   // r_i = delta_{i,N} I + sum_c H_{i,c} x_c - E x_i + Sigma_i x_i
+      const int bi = p->b[i];
+      bool acc = false;
+      for (int c = std::max(0, i - w); c <= std::min(N - 1, i + w); ++c) {
+        NEGF_TRY(hx(i, c, Hblk(i, c), 0, p->b[c], Pblk(i), acc));
+        acc = true;
+      }
+      if (i == 0 && sigL) NEGF_TRY(hx(0, 0, sigmaL(), sig_stride, bi, Pblk(0), true));
+      if (i == N - 1 && sigR) NEGF_TRY(hx(i, i, sigmaR(), sig_stride, bi, Pblk(i), true));
+      NEGF_TRY(misc([&] {
+        return negf::axpy_scalar(Pblk(i), (int64_t)bi * bN, LCblk(i), (int64_t)bi * bN, E + e0, -1.0, bi, bN, bN, C, st);
+      }));
+      if (i == N - 1)
+        NEGF_TRY(misc([&] { return negf::add_diag(Pblk(i), sq(bN), bN, bN, nullptr, 0, 1.0, C, st); }));
+    }
+    for (int i = N - 2; i >= 0; --i)   // v = U^{-1} r (in place)
+      for (int c = i + 1; c <= std::min(N - 1, i + w); ++c) {
+        ZGemm g;
+        g.m = p->b[i]; g.n = bN; g.k = p->b[c];
+        g.A = Yblk(i, c); g.sA = (int64_t)p->b[i] * p->b[c]; g.lda = p->b[c];
+        g.B = Pblk(c); g.sB = (int64_t)p->b[c] * bN; g.ldb = bN;
+        g.C = Pblk(i); g.sC = (int64_t)p->b[i] * bN; g.ldc = bN; g.alpha = {-1.0, 0.0};
+        g.C1 = Pblk(i); g.sC1 = g.sC; g.ldc1 = bN; g.beta1 = {1.0, 0.0};
+        g.batch = C;
+        NEGF_TRY(gemm(g));
+      }
+    for (int i = 0; i < N; ++i) {      // d = L^{-1} D^{-1} v, then x += d
+      const int bi = p->b[i];
+      ZGemm g;
+      g.m = bi; g.n = bN; g.k = bi;
+      g.A = Tblk(i); g.sA = sq(bi); g.lda = bi;
+      g.B = Pblk(i); g.sB = (int64_t)bi * bN; g.ldb = bN;
+      g.C = RFblk(i); g.sC = (int64_t)bi * bN; g.ldc = bN;
+      g.batch = C;
+      NEGF_TRY(gemm(g));
+      for (int c = std::max(0, i - w); c < i; ++c) {
+        ZGemm h;
+        h.m = bi; h.n = bN; h.k = p->b[c];
+        h.A = Xblk(i, c); h.sA = (int64_t)bi * p->b[c]; h.lda = p->b[c];
+        h.B = RFblk(c); h.sB = (int64_t)p->b[c] * bN; h.ldb = bN;
+        h.C = RFblk(i); h.sC = (int64_t)bi * bN; h.ldc = bN; h.alpha = {-1.0, 0.0};
+        h.C1 = RFblk(i); h.sC1 = h.sC; h.ldc1 = bN; h.beta1 = {1.0, 0.0};
+        h.batch = C;
+        NEGF_TRY(gemm(h));
+      }
+    }
+    for (int i = 0; i < N; ++i)
+      NEGF_TRY(misc([&] {
+        return negf::copy2d(RFblk(i), (int64_t)p->b[i] * bN, bN, LCblk(i), (int64_t)p->b[i] * bN, bN, p->b[i], bN,
+                            1.0, 1, C, st);
+      }));
     return cudaSuccess;
   }
 
@@ -691,12 +765,14 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   p->p_off.resize(N);
   int64_t pe = 0;
   for (int i = 0; i < N; ++i) { p->p_off[i] = pe; pe += (int64_t)p->b[i] * bN; }
-  p->p_elems = grad ? pe : 0;
+  const bool refine = d->refine_steps > 0 && d->precision == NEGF_MIXED && d->n_domains == 1;
+  p->refine = refine ? 1 : 0;
+  p->p_elems = (grad || refine) ? pe : 0;
   // Gamma_L, Gamma_R, P, Q, G_1N, and two more b1 x bN temporaries (gradient)
   p->scr_elems = sq(b0) + sq(bN) + 5 * (int64_t)b0 * bN;
 
   int64_t per_e = te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot +
-                  (grad ? re : (int64_t)(w + 1) * b0 * bmax) + 2 * p->p_elems + p->scr_elems + dd_e;
+                  (grad ? re : (int64_t)(w + 1) * b0 * bmax) + 3 * p->p_elems + p->scr_elems + dd_e;
   // chunk energies so that the workspace stays within a budget
   const int64_t budget_elems = (int64_t)(24.0 * (1ull << 30)) / (int64_t)sizeof(double2);
   int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(p->nE, budget_elems / std::max<int64_t>(per_e, 1)));
@@ -716,6 +792,7 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   p->R_ws = q; q += (grad ? re : (int64_t)(w + 1) * b0 * bmax) * chunk;
   p->P_ws = q; q += p->p_elems * chunk;
   p->LC_ws = q; q += p->p_elems * chunk;
+  p->RF_ws = q; q += p->p_elems * chunk;
   p->scratch = q; q += p->scr_elems * chunk;
   p->G1N_ws = p->scratch + (sq(b0) + sq(bN) + 2 * (int64_t)b0 * bN) * chunk;
   if (p->n_domains > 1) {
@@ -1260,8 +1337,15 @@ negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigm
         continue;
       }
       NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
-        NEGF_TRY(s.upward(G_band != nullptr));
+        NEGF_TRY(s.upward(G_band != nullptr || (G_1N && p->refine)));
         if (G_band) NEGF_TRY(s.downward());
+        if (G_1N && p->refine) {   // G_1N = first block of the refined last column
+          NEGF_TRY(s.last_column());
+          NEGF_TRY(s.refine_last_column());
+          return s.misc([&] {
+            return negf::copy_blocks(s.LCblk(0), s1, (double2*)G_1N + (int64_t)s.e0 * s1, s1, s1, s.ne, s.st);
+          });
+        }
         if (G_1N) NEGF_TRY(s.first_row((double2*)G_1N + (int64_t)s.e0 * s1, s1));
         return cudaSuccess;
       }));
@@ -1295,6 +1379,11 @@ negf_status negf_transmission(negf_plan_t* p, const negf_c128* H, const negf_c12
         double2* g1n = p->G1N_ws + (int64_t)s.wofs * s1;
         if (p->n_domains > 1) {
           NEGF_TRY(DD(p, s).run(false, g1n, s1));
+        } else if (p->refine) {
+          NEGF_TRY(s.upward(true));
+          NEGF_TRY(s.last_column());
+          NEGF_TRY(s.refine_last_column());
+          NEGF_TRY(s.misc([&] { return negf::copy_blocks(s.LCblk(0), s1, g1n, s1, s1, s.ne, s.st); }));
         } else {
           NEGF_TRY(s.upward(false));
           NEGF_TRY(s.first_row(g1n, s1));

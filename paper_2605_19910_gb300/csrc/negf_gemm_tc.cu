@@ -121,6 +121,28 @@ __device__ __forceinline__ u64 i64_scaled_bits(long long T, int e2) {
   return (sgn << 63) | ((u64)be << 52) | (m & 0xFFFFFFFFFFFFFull);
 }
 
+// Signed 128-bit integer T times 2^e2 as IEEE double bits (round to nearest even)
+__device__ __forceinline__ u64 i128_scaled_bits(__int128 T, int e2) {
+  if (T == 0) return 0ull;
+  const u64 sgn = T < 0 ? 1ull : 0ull;
+  unsigned __int128 u = T < 0 ? (unsigned __int128)(-T) : (unsigned __int128)T;
+  const u64 hi = (u64)(u >> 64), lo = (u64)u;
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  u <<= lz;                                   // leading one at bit 127
+  int e = 127 - lz + e2;
+  u64 m = (u64)(u >> 75);                     // 53 bits with the leading one
+  const unsigned __int128 rem = u & (((unsigned __int128)1 << 75) - 1);
+  const unsigned __int128 half = (unsigned __int128)1 << 74;
+  if (rem > half || (rem == half && (m & 1ull))) {
+    m += 1;
+    if (m >> 53) { m >>= 1; e += 1; }
+  }
+  const int be = e + 1023;
+  if (be <= 0) return sgn << 63;
+  if (be >= 2047) return (sgn << 63) | (0x7FFull << 52);
+  return (sgn << 63) | ((u64)be << 52) | (m & 0xFFFFFFFFFFFFFull);
+}
+
 // a + b on IEEE double bit patterns with integer operations (round to nearest).
 // Zeros and normals are handled, denormal results flush to zero; non-finite
 // operands (never produced by the sweep) propagate as NaN.
@@ -227,6 +249,7 @@ __device__ __forceinline__ long long acc_int(uint32_t bits) {
   return (bits >> 31) ? -v : v;
 }
 
+template <bool WIDE>   // WIDE: products longer than 64-bit level combination allows
 __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
@@ -418,7 +441,7 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles
     for (int p0 = 0; p0 < n_mma; p0 += EP) {
       // Epilogue 1: combine the levels of this lane's real row for 16 columns
       const int c0 = p0 + 16 * half;
-      if (c0 < n_mma) {
+      if (!WIDE && c0 < n_mma) {                 // levels combine within 64 bits
         long long T[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) T[i] = 0;
@@ -433,6 +456,21 @@ __global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles
 #pragma unroll
         for (int i = 0; i < 16; ++i)
           stage[R * lds + 16 * half + i] = i64_scaled_bits(T[i], er + e_col[c0 + i] - s * (L + 1));
+      } else if (WIDE && c0 < n_mma) {           // long products: 128-bit combination
+        __int128 T[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) T[i] = 0;
+        for (int d = 0; d < L; ++d) {
+          uint32_t v[16];
+          tmem_ld16(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * n_mma + c0), v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int sh = s * (L - 1 - d);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) T[i] += (__int128)acc_int(v[i]) << sh;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          stage[R * lds + 16 * half + i] = i128_scaled_bits(T[i], er + e_col[c0 + i] - s * (L + 1));
       }
       __syncthreads();
       // Epilogue 2: alpha = +-1, + beta1 C1 + beta2 C2 + gamma dshift I (all +-1), FP64 store.
@@ -476,10 +514,21 @@ int g_tc_smem_optin = 0;
 bool is_pm1(double2 z) { return z.y == 0.0 && (z.x == 1.0 || z.x == -1.0); }
 bool is_pm1_or_0(double2 z) { return z.y == 0.0 && (z.x == 1.0 || z.x == -1.0 || z.x == 0.0); }
 
-TcCfg tc_config(int n, int k) {
+TcCfg tc_config(int n, int k, int bits) {
   TcCfg c;
-  // exact FP32 level-0 sums: K_real * (2^s - 1)^2 < 2^24
-  if (2 * k <= 256) { c.s = 8; c.L = 4; } else { c.s = 7; c.L = 5; }
+  if (bits <= 0) bits = 32;
+  // Exact FP32 level sums: (products per level) * K_real * (2^s - 1)^2 < 2^24.
+  // The default (32 bits) only needs level 0 exact (deeper levels carry
+  // weights below 2^-32); longer products need every level exact.
+  const double kr = 2.0 * k;
+  int best_s = 1, best_L = 1;
+  for (int s = 8; s >= 2; --s) {
+    const int L = (bits + s - 1) / s;
+    const double per_level = bits <= 32 ? 1.0 : (double)L;
+    if (per_level * kr * ((1 << s) - 1) * ((1 << s) - 1) < 16777216.0) { best_s = s; best_L = L; break; }
+  }
+  c.s = best_s;
+  c.L = best_L;
   const int cap = (512 / c.L) / 16 * 16;          // TMEM columns per level
   int nm = round_up(n < 16 ? 16 : n, 16);
   if (nm > cap) nm = cap;
@@ -503,17 +552,19 @@ bool zgemm_tc_available() { return true; }
 cudaError_t zgemm_tc(const ZGemm& g, cudaStream_t st) {
   if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.k <= 0) return zgemm_f64(g, st);
-  if (g.opA != OP_N || g.opB != OP_N || g.reduce || g.k > 512 || !is_pm1(g.alpha) ||
+  if (g.opA != OP_N || g.opB != OP_N || g.reduce || g.k > 512 || g.bits > 56 || !is_pm1(g.alpha) ||
       (g.C1 && !is_pm1_or_0(g.beta1)) || (g.C2 && !is_pm1_or_0(g.beta2)) ||
       (g.dshift && !is_pm1_or_0(g.gamma)))
     return cudaErrorNotSupported;
-  const TcCfg cfg = tc_config(g.n, g.k);
+  const TcCfg cfg = tc_config(g.n, g.k, g.bits);
+  if (cfg.L > 8) return zgemm_f64(g, st);   // too long for exact slices: the FP64 product
   const int tiles_m = (g.m + MC - 1) / MC, tiles_n = (g.n + cfg.n_mma - 1) / cfg.n_mma;
   const size_t sm = tc_smem_bytes(cfg);
   if ((int)sm > g_tc_smem_optin) return cudaErrorInvalidValue;
   dim3 grid(tiles_m * tiles_n, g.batch);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  zgemm_tc_kernel<<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  if (cfg.s * (cfg.L - 1) <= 36) zgemm_tc_kernel<false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  else zgemm_tc_kernel<true><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
   return cudaGetLastError();
 }
 
@@ -526,10 +577,12 @@ cudaError_t kernels_init() {
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, zgemm_tc_kernel);
+  e = cudaFuncGetAttributes(&fa, zgemm_tc_kernel<true>);
   if (e != cudaSuccess) return e;
   int dyn = optin - (int)fa.sharedSizeBytes - 1024;
-  e = cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  e = cudaFuncSetAttribute(zgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(zgemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
   if (e != cudaSuccess) return e;
   g_tc_smem_optin = dyn;
   return cudaSuccess;

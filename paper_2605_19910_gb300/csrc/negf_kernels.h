@@ -27,6 +27,7 @@ struct ZGemm {
   double2 alpha = {1.0, 0.0}, beta1 = {0.0, 0.0}, beta2 = {0.0, 0.0}, gamma = {0.0, 0.0};
   const double* weight = nullptr;
   int* errword = nullptr;   // device error word for bounded-wait timeouts (tensor-core path)
+  int bits = 0;             // tensor-core path: significant bits of the product (0 = 32; up to 56)
   int batch = 1;
   int reduce = 0;
 };
@@ -71,6 +72,10 @@ cudaError_t set_eye(double2* dst, int64_t sDst, int ld, int rows, int cols, int 
 // dst[e](i, i) += scale * s[e] for i < n (s: per-energy complex scalars, stride sS).
 cudaError_t add_diag(double2* dst, int64_t sDst, int ld, int n, const double2* s, int64_t sS, double scale,
                      int batch, cudaStream_t st);
+
+// dst[e] += scale * E[e] * src[e]  (rows x cols, leading dimension ld, FP64).
+cudaError_t axpy_scalar(double2* dst, int64_t sDst, const double2* src, int64_t sSrc, const double2* E,
+                        double scale, int rows, int cols, int ld, int batch, cudaStream_t st);
 
 // D[e] = I (b x b).
 cudaError_t set_identity(double2* D, int64_t sD, int b, int batch, cudaStream_t st);

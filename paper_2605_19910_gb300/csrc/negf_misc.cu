@@ -129,12 +129,31 @@ __global__ void add_diag_kernel(double2* __restrict__ dst, int64_t sDst, int ld,
                                 int64_t sS, double scale) {
   const int e = blockIdx.y;
   double2* dp = dst + (int64_t)e * sDst;
-  const double2 v = sv[(int64_t)e * sS];
+  const double2 v = sv ? sv[(int64_t)e * sS] : make_double2(1.0, 0.0);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double2 o = dp[(int64_t)i * ld + i];
     o.x = fma(scale, v.x, o.x);
     o.y = fma(scale, v.y, o.y);
     dp[(int64_t)i * ld + i] = o;
+  }
+}
+
+__global__ void axpy_scalar_kernel(double2* __restrict__ dst, int64_t sDst, const double2* __restrict__ src,
+                                   int64_t sSrc, const double2* __restrict__ E, double scale, int rows, int cols,
+                                   int ld) {
+  const int e = blockIdx.y;
+  double2* d = dst + (int64_t)e * sDst;
+  const double2* x = src + (int64_t)e * sSrc;
+  const double2 z = make_double2(scale * E[e].x, scale * E[e].y);
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / cols), c = (int)(idx - (int64_t)r * cols);
+    const double2 v = x[(int64_t)r * ld + c];
+    double2 o = d[(int64_t)r * ld + c];
+    o.x = fma(z.x, v.x, fma(-z.y, v.y, o.x));
+    o.y = fma(z.x, v.y, fma(z.y, v.x, o.y));
+    d[(int64_t)r * ld + c] = o;
   }
 }
 
@@ -182,6 +201,14 @@ cudaError_t add_diag(double2* dst, int64_t sDst, int ld, int n, const double2* s
   if (batch <= 0 || n <= 0) return cudaSuccess;
   dim3 grid(grid_x_for(n, 128), batch);
   add_diag_kernel<<<grid, 128, 0, st>>>(dst, sDst, ld, n, s, sS, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t axpy_scalar(double2* dst, int64_t sDst, const double2* src, int64_t sSrc, const double2* E,
+                        double scale, int rows, int cols, int ld, int batch, cudaStream_t st) {
+  if (batch <= 0 || rows <= 0 || cols <= 0) return cudaSuccess;
+  dim3 grid(grid_x_for((int64_t)rows * cols, 256), batch);
+  axpy_scalar_kernel<<<grid, 256, 0, st>>>(dst, sDst, src, sSrc, E, scale, rows, cols, ld);
   return cudaGetLastError();
 }
 

@@ -66,3 +66,37 @@ def test_mixed_variable_sizes_many_energies(P, torch):
 def test_mixed_nanowire_block_sizes_96_to_160(P, torch):
     prob = make_problem(6, b=None, size_range=(96, 160), w=1, n_energies=2, eta=1e-3, seed=61)
     run_and_compare(P, torch, prob, tol=MIXED_TOL, precision="mixed")
+
+
+def _g1n_err(P, torch, prob, refine):
+    import numpy as np
+    from gpu_parity import rel_err, to_dev
+    from oracle import rgf as O
+    Hp, sL, sR, E = to_dev(prob, torch)
+    nE = len(prob.energies)
+    plan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision="mixed", refine_steps=refine,
+                  outputs=P.NEGF_OUT_G1N | P.NEGF_OUT_TRANSMISSION)
+    _, G1 = plan.solve(Hp, sL, sR, E, band=False)
+    T = plan.transmission(Hp, sL, sR, E).cpu().numpy()
+    plan.close()
+    G1 = G1.cpu().numpy()
+    eg, et = 0.0, 0.0
+    for e in range(nE):
+        ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, prob.w, first_row=True)
+        Tref = O.transmission(ref["G1N"], prob.sigma_L, prob.sigma_R)
+        eg = max(eg, rel_err(G1[e], ref["G1N"]))
+        et = max(et, abs(T[e] - Tref) / abs(Tref))
+    return eg, et
+
+
+@pytest.mark.parametrize("w,N,b", [(1, 12, 64), (1, 9, 37), (2, 10, 24)])
+def test_refinement_recovers_fp64_level_g1n_and_transmission(P, torch, w, N, b):
+    """One step of iterative refinement of the last block column (FP64-accurate
+    residual from 56-bit tensor products, correction with the mixed factors)
+    brings G_1N and T(E) from the mixed level to the FP64 level."""
+    prob = make_problem(N, b=b, w=w, n_energies=6, eta=1e-6, seed=70 + N)
+    e0, t0 = _g1n_err(P, torch, prob, 0)
+    e1, t1 = _g1n_err(P, torch, prob, 1)
+    assert e0 < MIXED_TOL and t0 < MIXED_TOL
+    assert e1 < 1e-10 and t1 < 1e-10, (e0, e1, t0, t1)
+    assert e1 < e0 / 100
