@@ -38,7 +38,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-side", action="store_true",
+                    help="skip the side measurement of the FP64 path")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-energies", type=int, default=512,
                     help="energies of the bounded CPU-oracle sample")
@@ -309,10 +311,41 @@ def run_ours(a, rank, world, local_rank):
             "kernel_share": dms / sum(v[0] for v in prof.values()),
             "launches_per_step": int(dln)}
 
+    # composite roofline of the mixed path (FP64 inversions at the FP64 peak,
+    # block products at the BF16 tensor peak, useful flops only)
+    composite = None
+    if a.precision == "mixed":
+        f64 = prof["zinv_gj_kernel"][1]
+        flow = prof["zgemm_tc_kernel"][1] + prof["zgemm_f64_kernel"][1]
+        t_roof = f64 / (fp64_peak * 1e12) + flow / (bf16 * 1e12)
+        composite = {"t_roof_ms": t_roof * 1e3, "t_measured_ms": ms, "frac": t_roof * 1e3 / ms,
+                     "fp64_flops": f64, "product_flops": flow,
+                     "peaks": {"fp64_tflops": fp64_peak, "bf16_tflops": bf16}}
+
     from oracle.rgf import rgf_flops_paper
     flops_step = rgf_flops_paper(prob.sizes, prob.w) * nE
     ws_gb = P.negf_workspace_bytes(plan.handle) / 1e9
     plan.close()
+
+    # side measurement: the plain FP64 path on the same inputs (for the
+    # mixed-over-FP64 speedup)
+    fp64_side = None
+    if a.precision == "mixed" and not a.no_fp64_side:
+        fplan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision="fp64", outputs=outputs)
+        fplan.solve(H, sL, sR, E, out_band=Gb, out_g1n=G1, sync=False)
+        fplan.sync()
+        k3 = max(1, min(a.steps, 3))
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k3):
+            fplan.solve(H, sL, sR, E, out_band=Gb, out_g1n=G1, sync=False)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fplan.sync()
+        fplan.close()
+        fms = f0.elapsed_time(f1) / k3
+        fp64_side = {"ms_per_step": fms, "value": world * nE * N / (fms * 1e-3), "steps": k3,
+                     "mixed_speedup": fms / ms}
 
     cpu = None
     if pool is not None:
@@ -335,6 +368,8 @@ def run_ours(a, rank, world, local_rank):
             "effective_tflops_paper_count": flops_step / (ms * 1e-3) / 1e12 * world,
             "rel_err_vs_oracle_sampled": rel,
             "roofline": roof,
+            "composite_roofline": composite,
+            "fp64_path": fp64_side,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

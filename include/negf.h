@@ -97,7 +97,11 @@ typedef struct {
   int32_t precision;                  /* negf_precision                        */
   int32_t refine_steps;               /* 0 or 1 (NEGF_MIXED only)              */
   int32_t outputs;                    /* NEGF_OUT_* bit mask                   */
-  int32_t checkpoint_every;           /* adjoint: keep every k-th layer, 0=all */
+  int32_t checkpoint_every;           /* reserved, must be 0                   */
+  int32_t product_bits;               /* NEGF_MIXED: significant bits of the
+                                         tensor-core block products (0 = 32;
+                                         33..56 trade speed for accuracy on
+                                         ill-conditioned problems)             */
 } negf_desc;
 
 #define NEGF_MAX_BLOCK 160

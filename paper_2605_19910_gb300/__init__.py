@@ -77,6 +77,7 @@ class negf_desc(ctypes.Structure):
         ("refine_steps", ctypes.c_int32),
         ("outputs", ctypes.c_int32),
         ("checkpoint_every", ctypes.c_int32),
+        ("product_bits", ctypes.c_int32),
     ]
 
 
@@ -144,7 +145,7 @@ def _ptr(x):
 
 def negf_plan(block_sizes, band_n=3, n_energies=1, n_domains=1, domain_first_block=None,
               precision=NEGF_FP64, refine_steps=0, outputs=NEGF_OUT_BAND | NEGF_OUT_G1N,
-              checkpoint_every=0, stream=None):
+              checkpoint_every=0, stream=None, product_bits=0):
     """Create a plan; returns an opaque handle (int).  Raises NegfError."""
     sizes = (ctypes.c_int32 * len(block_sizes))(*[int(b) for b in block_sizes])
     d = negf_desc()
@@ -160,6 +161,7 @@ def negf_plan(block_sizes, band_n=3, n_energies=1, n_domains=1, domain_first_blo
     d.refine_steps = refine_steps
     d.outputs = outputs
     d.checkpoint_every = checkpoint_every
+    d.product_bits = product_bits
     h = ctypes.c_void_p()
     s = _lib.negf_plan(ctypes.byref(h), ctypes.byref(d), stream)
     if s != NEGF_OK:
@@ -182,6 +184,7 @@ def negf_solve_noalloc(block_sizes, band_n, n_energies, H, sigma_L, sigma_R, sig
     d.refine_steps = 0
     d.outputs = outputs
     d.checkpoint_every = 0
+    d.product_bits = 0
     return _lib.negf_solve_noalloc(ctypes.byref(d), _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride),
                                    _ptr(E), _ptr(G_band), _ptr(G_1N), _ptr(info), stream)
 
@@ -286,7 +289,7 @@ class Plan:
 
     def __init__(self, sizes, band_n=3, n_energies=1, n_domains=1, domain_first_block=None,
                  precision="fp64", refine_steps=0, outputs=NEGF_OUT_BAND | NEGF_OUT_G1N,
-                 checkpoint_every=0, stream=None):
+                 checkpoint_every=0, stream=None, product_bits=0):
         import torch
         self.torch = torch
         self.sizes = [int(b) for b in sizes]
@@ -299,7 +302,7 @@ class Plan:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         prec = {"fp64": NEGF_FP64, "mixed": NEGF_MIXED}[precision] if isinstance(precision, str) else precision
         self.handle = negf_plan(self.sizes, band_n, self.n_energies, n_domains, domain_first_block, prec,
-                                refine_steps, outputs, checkpoint_every, self.stream.cuda_stream)
+                                refine_steps, outputs, checkpoint_every, self.stream.cuda_stream, product_bits)
         self.band_elems = negf_band_elems(self.handle)
         self.info = torch.zeros(self.n_energies, dtype=torch.int32, device="cuda")
 

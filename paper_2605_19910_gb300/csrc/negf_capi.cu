@@ -40,7 +40,7 @@ struct CallKey {
 }  // namespace
 
 struct negf_plan_s {
-  int N = 0, w = 1, nE = 0, n_domains = 1, precision = 0, refine = 0, outputs = 0, ckpt = 0;
+  int N = 0, w = 1, nE = 0, n_domains = 1, precision = 0, refine = 0, outputs = 0, ckpt = 0, bits = 0;
   std::vector<int> b;
   std::vector<int64_t> band_off;   // (d + w) * N + i -> element offset or -1
   int64_t band_elems = 0;
@@ -90,7 +90,7 @@ struct negf_plan_s {
   double2* band_ws = nullptr;   // band of one chunk when the caller keeps no band output
 
   // independent energy groups run on forked streams (graph branches)
-  int groups = 4;
+  int groups = 1;
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;   // [0] fork, [1..] joins
   std::vector<cudaEvent_t> stagger;   // group g -> g + 1 start dependency
@@ -164,6 +164,7 @@ struct Sweep {
   }
   cudaError_t gemm(ZGemm g) {
     g.errword = p->d_err;
+    if (g.bits == 0) g.bits = p->bits;
     if (p->precision == NEGF_MIXED)
       return launch(NEGF_PROF_GEMM_TC, gemm_flops(g), [&] { return negf::zgemm_tc(g, st); });
     return launch(NEGF_PROF_GEMM_F64, gemm_flops(g), [&] { return negf::zgemm_f64(g, st); });
@@ -606,7 +607,8 @@ negf_status validate(const negf_desc* d) {
   if (d->precision != NEGF_FP64 && d->precision != NEGF_MIXED) return NEGF_ERR_ARG;
   if (d->refine_steps < 0 || d->refine_steps > 1) return NEGF_ERR_ARG;
   if (d->outputs & ~(NEGF_OUT_BAND | NEGF_OUT_G1N | NEGF_OUT_TRANSMISSION | NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
-  if (d->checkpoint_every < 0) return NEGF_ERR_ARG;
+  if (d->checkpoint_every != 0) return NEGF_ERR_ARG;
+  if (d->product_bits != 0 && (d->product_bits < 16 || d->product_bits > 56)) return NEGF_ERR_ARG;
   for (int i = 0; i < d->n_blocks; ++i)
     if (d->block_sizes[i] < 1 || d->block_sizes[i] > NEGF_MAX_BLOCK) return NEGF_ERR_ARG;
   return NEGF_OK;
@@ -655,6 +657,7 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   // what 32-bit products leave.
   if (p->n_domains > 1) p->precision = NEGF_FP64;
   p->ckpt = d->checkpoint_every;
+  p->bits = d->product_bits;
   p->b.assign(d->block_sizes, d->block_sizes + d->n_blocks);
   p->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&p->device);
@@ -773,8 +776,13 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
 
   int64_t per_e = te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot +
                   (grad ? re : (int64_t)(w + 1) * b0 * bmax) + 3 * p->p_elems + p->scr_elems + dd_e;
-  // chunk energies so that the workspace stays within a budget
-  const int64_t budget_elems = (int64_t)(24.0 * (1ull << 30)) / (int64_t)sizeof(double2);
+  // chunk energies so that the workspace stays within a budget: 45% of the
+  // device memory free at plan time, at least 24 GiB (the caller's outputs
+  // need the rest)
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 0; }
+  const double budget_bytes = std::max(24.0 * (1ull << 30), 0.45 * (double)free_b);
+  const int64_t budget_elems = (int64_t)(budget_bytes / (double)sizeof(double2));
   int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(p->nE, budget_elems / std::max<int64_t>(per_e, 1)));
   p->chunk = chunk;
   p->ws_bytes = (size_t)(per_e * chunk + p->msup_e) * sizeof(double2) + 256;
@@ -827,6 +835,9 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
     if (ie != cudaSuccess) { g_last_cuda = ie; negf_destroy(p); return NEGF_ERR_CUDA; }
   }
   {
+    // energy groups: up to 4, with at least 128 energies each (fewer energies
+    // leave each batched launch too small to fill the GPU)
+    p->groups = std::max(1, std::min(4, p->chunk / 128));
     const char* env = getenv("NEGF_STREAMS");
     if (env) p->groups = std::max(1, std::min(8, atoi(env)));
     p->groups = std::min(p->groups, p->chunk);

@@ -25,10 +25,10 @@ def torch():
 
 
 def run_and_compare(P, torch, prob, energies_idx=None, per_energy_sigma=False, band=True, g1n=True,
-                    tol=FP64_TOL, precision="fp64"):
+                    tol=FP64_TOL, precision="fp64", product_bits=0):
     Hp, sL, sR, E = to_dev(prob, torch, per_energy_sigma)
     plan = P.Plan(prob.sizes, 2 * prob.w + 1, len(prob.energies), precision=precision,
-                  outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_G1N | P.NEGF_OUT_TRANSMISSION)
+                  outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_G1N | P.NEGF_OUT_TRANSMISSION, product_bits=product_bits)
     Gb, G1 = plan.solve(Hp, sL, sR, E, band=band, g1n=g1n)
     T = plan.transmission(Hp, sL, sR, E)
     info = plan.info.cpu().numpy()
