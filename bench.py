@@ -31,6 +31,27 @@ WORKLOAD = "batched64x64"
 METRIC = "selected-G^R energies x blocks / s"
 UNIT = "energy-blocks/s"
 
+# product width per workload on the mixed path: the 1024-layer nanowire has
+# localised states at eta = 1e-6 whose blocks need 48-bit products for 1e-5
+PRODUCT_BITS = {"wire1024": 48}
+
+# DRAM traffic per unit (one block inversion) of the dominant kernel from an
+# ncu capture, valid only while the kernel source is the one captured; the
+# summary and its command are in profiles/zinv_gj_kernel_b64_512E_full.md
+NCU_TRAFFIC = {
+    ("zinv_gj_kernel", 64): {
+        "bytes_per_unit": (33.589760e6 + 0.620032e6) / 512,
+        "src": "paper_2605_19910_gb300/csrc/negf_inv.cu",
+        "sha256": "830c7535bd1799fadf5a00a958c7eb2b20897263ca7101417841c21c28bfe569",
+    },
+}
+
+# FP64 peaks (TFLOP/s): the GJ inversion is plain DFMA arithmetic (bound
+# "alu"), rated at the GB300's nominal FP64 rate at the 2070 MHz maximum SM
+# clock; the DMMA block product is a contraction, rated at the measured BF16
+# sustained peak times the nominal FP64:BF16 ratio
+FP64_NOMINAL_TFLOPS = 1.25
+
 
 def _args():
     ap = argparse.ArgumentParser()
@@ -47,6 +68,9 @@ def _args():
     ap.add_argument("--n-blocks", type=int, default=None, help="override the workload's block count")
     ap.add_argument("--n-energies", type=int, default=None, help="override the workload's energy count")
     ap.add_argument("--block-size", type=int, default=None, help="override the workload's block size")
+    ap.add_argument("--product-bits", type=int, default=None,
+                    help="bits of the tensor-core block products on the mixed path "
+                         "(default: 48 for the 1024-layer nanowire, 32 otherwise)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -187,7 +211,9 @@ def run_ours(a, rank, world, local_rank):
     Eh = torch.tensor(prob.energies).pin_memory()
     H, sL, sR, E = (x.to(dev) for x in (Hh, sLh, sRh, Eh))
     outputs = P.NEGF_OUT_BAND | P.NEGF_OUT_G1N | P.NEGF_OUT_TRANSMISSION
-    plan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision=a.precision, outputs=outputs)
+    bits = a.product_bits if a.product_bits is not None else PRODUCT_BITS.get(a.workload, 0)
+    bits = bits if a.precision == "mixed" else 0
+    plan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision=a.precision, outputs=outputs, product_bits=bits)
     Gb = torch.empty(nE, plan.band_elems, dtype=torch.complex128, device=dev)
     G1 = torch.empty(nE, prob.sizes[0], prob.sizes[-1], dtype=torch.complex128, device=dev)
 
@@ -203,7 +229,7 @@ def run_ours(a, rank, world, local_rank):
     # energy groups do not inflate each other's durations
     old_env = os.environ.get("NEGF_STREAMS")
     os.environ["NEGF_STREAMS"] = "1"
-    pplan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision=a.precision, outputs=outputs)
+    pplan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision=a.precision, outputs=outputs, product_bits=bits)
     if old_env is None:
         del os.environ["NEGF_STREAMS"]
     else:
@@ -299,32 +325,49 @@ def run_ours(a, rank, world, local_rank):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
+    src = "MEASURED_PEAKS" if "bf16_tflops_sustained" in peaks else "fallback"
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-    fp64_peak = bf16 * (1.25 / 2250.0)          # FP64 nominal : bf16 nominal
+    dmma_peak = bf16 * (1.25 / 2250.0)          # FP64 nominal : bf16 nominal
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     name, (dms, dfl, dln) = dom
     achieved = dfl / (dms * 1e-3) / 1e12 if dms > 0 else 0.0
-    roof = {"kernel": name, "bound": "tensor" if name == "zgemm_f64_kernel" else "alu",
-            "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-            "traffic": None,
-            "peak_source": "MEASURED_PEAKS bf16 sustained x nominal FP64:bf16 (1.25:2250)",
+    if name == "zgemm_f64_kernel":
+        bound, peak = "tensor", dmma_peak
+        psrc = f"of measured: {src} bf16 sustained x nominal FP64:bf16 (1.25:2250)"
+    else:
+        bound, peak = "alu", FP64_NOMINAL_TFLOPS
+        psrc = "nominal GB300 FP64 at the 2070 MHz maximum SM clock (DFMA pipe)"
+    traffic = None
+    uniform_b = prob.sizes[0] if len(set(prob.sizes)) == 1 else None
+    t = NCU_TRAFFIC.get((name, uniform_b))
+    if t is not None:
+        import hashlib
+        with open(os.path.join(ROOT, t["src"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() == t["sha256"]:
+                traffic = t["bytes_per_unit"] * (N * nE / dln)
+    roof = {"kernel": name, "bound": bound,
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_source": psrc,
             "kernel_share": dms / sum(v[0] for v in prof.values()),
             "launches_per_step": int(dln)}
 
-    # composite roofline of the mixed path (FP64 inversions at the FP64 peak,
+    # composite roofline of the mixed path (FP64 inversions at the FP64 rate,
     # block products at the BF16 tensor peak, useful flops only)
     composite = None
     if a.precision == "mixed":
         f64 = prof["zinv_gj_kernel"][1]
-        flow = prof["zgemm_tc_kernel"][1] + prof["zgemm_f64_kernel"][1]
-        t_roof = f64 / (fp64_peak * 1e12) + flow / (bf16 * 1e12)
+        fdm = prof["zgemm_f64_kernel"][1]
+        flow = prof["zgemm_tc_kernel"][1]
+        t_roof = f64 / (FP64_NOMINAL_TFLOPS * 1e12) + fdm / (dmma_peak * 1e12) + flow / (bf16 * 1e12)
         composite = {"t_roof_ms": t_roof * 1e3, "t_measured_ms": ms, "frac": t_roof * 1e3 / ms,
-                     "fp64_flops": f64, "product_flops": flow,
-                     "peaks": {"fp64_tflops": fp64_peak, "bf16_tflops": bf16}}
+                     "fp64_inverse_flops": f64, "fp64_product_flops": fdm, "tensor_product_flops": flow,
+                     "peaks": {"fp64_alu_tflops": FP64_NOMINAL_TFLOPS, "fp64_dmma_tflops": dmma_peak,
+                               "bf16_tflops": bf16}}
 
     from oracle.rgf import rgf_flops_paper
     flops_step = rgf_flops_paper(prob.sizes, prob.w) * nE
     ws_gb = P.negf_workspace_bytes(plan.handle) / 1e9
+    plan_bits = bits or 32
     plan.close()
 
     # side measurement: the plain FP64 path on the same inputs (for the
@@ -357,10 +400,12 @@ def run_ours(a, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64" if a.precision == "fp64" else "mixed: exact bf16-slice tensor products (4 x 8 bit), f64 inverses",
+            "dtype": "f64" if a.precision == "fp64" else
+                     f"mixed: exact bf16-slice tensor products ({plan_bits} bit), f64 inverses",
             "data": "synthetic",
             "config": {"workload": a.workload, "n_blocks": N, "block_size": prob.sizes[0], "band_n": 2 * prob.w + 1,
                        "n_energies": nE, "eta": 1e-6, "precision": a.precision,
+                       "product_bits": plan_bits if a.precision == "mixed" else None,
                        "outputs": "band + G_1N per energy",
                        "l2": "no flush: each step writes %.1f GB of selected blocks and %.1f GB of sweep "
                              "workspace, both far above the 129 MB L2" % (Gb.numel() * 16 / 1e9, ws_gb),
