@@ -67,10 +67,14 @@ typedef enum {
 
 /* Arithmetic of the sweep.
  * NEGF_FP64:  every product and every per-block inverse in double precision.
- * NEGF_MIXED: block products on the tensor cores in an FP32-accurate split
- *             (each operand split into bf16 parts, FP32 accumulation),
- *             per-block inverses (and the DDRGF interface system) in FP64;
- *             inputs and outputs stay complex128. */
+ * NEGF_MIXED: block products on the tensor cores from exact BF16 slices
+ *             (each operand cut into integer slices below a power-of-two
+ *             scale per row / column, every slice product and FP32 sum exact;
+ *             negf_desc.product_bits significant bits, 32 by default),
+ *             per-block inverses in FP64; inputs and outputs stay complex128.
+ *             DDRGF plans (n_domains > 1) keep the interface system (T_S, its
+ *             RGF) in FP64.  Closed sub-domains at small eta amplify product
+ *             rounding: there product_bits = 48..56 is the setting. */
 typedef enum { NEGF_FP64 = 0, NEGF_MIXED = 1 } negf_precision;
 
 /* Output selection bits (negf_desc.outputs). */
@@ -87,7 +91,9 @@ typedef struct {
   int32_t band_n;                     /* n = 3 or 5 (w = (n-1)/2)              */
   int32_t n_energies;                 /* >= 1                                  */
   int32_t n_domains;                  /* 1 = plain RGF, >1 = single-level DDRGF
-                                         (Alg. 2; always computed in FP64)     */
+                                         (Alg. 2): sub-domain sweeps in the
+                                         plan's precision, interface Schur
+                                         system and its RGF in FP64            */
   const int32_t* domain_first_block;  /* host, n_domains entries or NULL: first
                                          layer of each (D2, D1) pair; pair j is
                                          D2_j then a separator D1_j of w layers;
@@ -97,7 +103,18 @@ typedef struct {
   int32_t precision;                  /* negf_precision                        */
   int32_t refine_steps;               /* 0 or 1 (NEGF_MIXED only)              */
   int32_t outputs;                    /* NEGF_OUT_* bit mask                   */
-  int32_t checkpoint_every;           /* reserved, must be 0                   */
+  int32_t checkpoint_every;           /* adjoint plans (NEGF_OUT_GRAD): 0 keeps
+                                         the whole forward factorisation of an
+                                         energy chunk; k > 0 keeps rings of k + 1
+                                         layers and one checkpoint (S_i, P_i) per
+                                         segment of k layers, and negf_grad
+                                         recomputes each segment (one extra
+                                         upward sweep; memory ~ (N/k + 3k) blocks
+                                         per energy instead of ~6N).  Such a plan
+                                         serves negf_transmission and G_1N-only
+                                         negf_solve; a band request returns
+                                         NEGF_ERR_UNSUPPORTED.  Ignored without
+                                         NEGF_OUT_GRAD.  < 0: NEGF_ERR_ARG.     */
   int32_t product_bits;               /* NEGF_MIXED: significant bits of the
                                          tensor-core block products (0 = 32;
                                          33..56 trade speed for accuracy on

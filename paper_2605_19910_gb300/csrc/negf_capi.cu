@@ -71,6 +71,17 @@ struct negf_plan_s {
   int64_t scr_elems = 0;
   double2* G1N_ws = nullptr;    // G_1N when the caller does not keep it
   double* Tdummy = nullptr;
+  bool full_row = false;        // R_ws holds the whole first row (adjoint without checkpoints)
+
+  // Checkpointed adjoint (checkpoint_every = k > 0): the sweep quantities
+  // t_i, X_{i,i-1}, Y_{i-1,i}, P_i and the last column live in rings of k + 1
+  // layers (fixed per-energy strides bmax^2 and bmax * b_N); the Schur
+  // complement S_hi and P_hi at the top layer of every segment of k layers are
+  // kept and the segment is recomputed from them in the reverse pass.
+  int ck_k = 0, ck_nseg = 0;
+  double2* CKS = nullptr;       // ck_nseg slots of bmax^2 per energy
+  double2* CKP = nullptr;       // ck_nseg slots of bmax * b_N per energy
+  int64_t bmax2 = 0, bmaxN = 0;
 
   // DDRGF (Alg. 2): n_domains (D2, D1) pairs; D2_j = [dom_f[j], dom_l[j]], its
   // right separator D1_j = [dom_l[j] + 1, dom_l[j] + w].
@@ -199,7 +210,7 @@ struct Sweep {
   // Per-energy stride inside a shared slot is fixed (bmax^2, b_1 * bmax):
   // concurrent energy groups can be at different layers of different sizes.
   int64_t sS() const { return p->s_slot; }
-  int64_t sR(int j) const { return (p->outputs & NEGF_OUT_GRAD) ? (int64_t)p->b[0] * p->b[j] : (int64_t)p->b[0] * p->r_elems; }
+  int64_t sR(int j) const { return p->full_row ? (int64_t)p->b[0] * p->b[j] : (int64_t)p->b[0] * p->r_elems; }
   double2* Gb(int a, int bb) const {
     return Gband + (int64_t)(e0 - gb_e0) * p->band_elems + p->band_off[(bb - a + p->w) * p->N + a];
   }
@@ -347,14 +358,14 @@ struct Sweep {
   // row); R_ws holds either the whole row (gradient) or a ring of w + 1.
   double2* Rblk(int j) const {
     const int64_t o = (int64_t)wofs * sR(j);
-    if (p->outputs & NEGF_OUT_GRAD) return p->R_ws + p->r_off[j] * p->chunk + o;
+    if (p->full_row) return p->R_ws + p->r_off[j] * p->chunk + o;
     return p->R_ws + (int64_t)(j % (p->w + 1)) * (int64_t)p->b[0] * p->r_elems * p->chunk + o;
   }
   cudaError_t first_row(double2* g1n_out, int64_t s_out) {
     const int N = p->N, w = p->w, C = ne;
     const int b0 = p->b[0];
     if (N == 1) {
-      if (p->outputs & NEGF_OUT_GRAD)
+      if (p->full_row)
         NEGF_TRY(misc([&] { return negf::copy_blocks(Tblk(0), sq(b0), Rblk(0), sR(0), sq(b0), C, st); }));
       return misc([&] { return negf::copy_blocks(Tblk(0), sq(b0), g1n_out, s_out, sq(b0), C, st); });
     }
@@ -375,7 +386,7 @@ struct Sweep {
         g.batch = C;
         NEGF_TRY(gemm(g));
       }
-      if (last && (p->outputs & NEGF_OUT_GRAD))
+      if (last && p->full_row)
         NEGF_TRY(misc([&] { return negf::copy_blocks(out, so, Rblk(j), sR(j), (int64_t)b0 * bj, C, st); }));
     }
     return cudaSuccess;
@@ -523,6 +534,24 @@ struct Sweep {
   // every layer a, written over P (no longer needed).
   cudaError_t grad_prep(const double2* g1n, int64_t sG) {
     const int N = p->N, C = ne, b0 = p->b[0], bN = p->b[N - 1];
+    NEGF_TRY(grad_K(g1n, sG));
+    double2* K = scr(6);
+    for (int a = 0; a < N; ++a) {   // U_a = K G_{1,a}
+      const int ba = p->b[a];
+      ZGemm g;
+      g.m = bN; g.n = ba; g.k = b0;
+      g.A = K; g.sA = (int64_t)bN * b0; g.lda = b0;
+      g.B = Rblk(a); g.sB = sR(a); g.ldb = ba;
+      g.C = Pblk(a); g.sC = (int64_t)ba * bN; g.ldc = ba;
+      g.batch = C;
+      NEGF_TRY(gemm(g));
+    }
+    return cudaSuccess;
+  }
+
+  // Gamma_L, Gamma_R (scratch 0, 1) and K = Gamma_R G_1N^H Gamma_L (scratch 6).
+  cudaError_t grad_K(const double2* g1n, int64_t sG) {
+    const int N = p->N, C = ne, b0 = p->b[0], bN = p->b[N - 1];
     const int nsig = sig_stride ? C : 1;
     double2* gL = scr(0);
     double2* gR = scr(1);
@@ -548,15 +577,183 @@ struct Sweep {
       g.batch = C;
       NEGF_TRY(gemm64(g));
     }
-    for (int a = 0; a < N; ++a) {   // U_a = K G_{1,a}
-      const int ba = p->b[a];
+    return cudaSuccess;
+  }
+
+  // ---- checkpointed adjoint (block tridiagonal) ----------------------------
+  // Rings of k + 1 layers with fixed per-energy strides (bmax^2 for t, X, Y;
+  // bmax * b_N for P / U and the last column); X_{i,i-1} and Y_{i-1,i} sit in
+  // the slot of layer i.  Segment sg covers layers [sg k, min(N, (sg+1) k) - 1].
+  int ck_slot(int i) const { return i % (p->ck_k + 1); }
+  double2* ck_ring(double2* base, int i, int64_t stride) const {
+    return base + (int64_t)ck_slot(i) * stride * p->chunk + (int64_t)wofs * stride;
+  }
+  double2* cT(int i) const { return ck_ring(p->T_ws, i, p->bmax2); }
+  double2* cX(int i) const { return ck_ring(p->X_ws, i, p->bmax2); }
+  double2* cY(int i) const { return ck_ring(p->Y_ws, i, p->bmax2); }
+  double2* cP(int i) const { return ck_ring(p->P_ws, i, p->bmaxN); }
+  double2* cL(int i) const { return ck_ring(p->LC_ws, i, p->bmaxN); }
+  double2* ckS(int sg) const { return p->CKS + (int64_t)sg * p->bmax2 * p->chunk + (int64_t)wofs * p->bmax2; }
+  double2* ckP(int sg) const { return p->CKP + (int64_t)sg * p->bmaxN * p->chunk + (int64_t)wofs * p->bmaxN; }
+  int seg_lo(int sg) const { return sg * p->ck_k; }
+  int seg_hi(int sg) const { return std::min(p->N, (sg + 1) * p->ck_k) - 1; }
+
+  // Eliminate layer i: t_i = S_i^{-1}; for i > 0 the multipliers
+  // X_{i,i-1} = t_i M_{i,i-1} (if want_x) and Y_{i-1,i} = M_{i-1,i} t_i; if
+  // want_next also S_{i-1} = M_{i-1,i-1} - Y_{i-1,i} M_{i,i-1} and the suffix
+  // product P_{i-1} = -Y_{i-1,i} P_i of U^{-1} e_N.
+  cudaError_t ck_eliminate(int i, bool want_x, bool want_next) {
+    const int C = ne, bi = p->b[i], bN = p->b[p->N - 1];
+    const int64_t s2 = p->bmax2, sN = p->bmaxN;
+    NEGF_TRY(inv(Sslot(i, i), sS(), cT(i), s2, bi, C, i + 1));
+    if (i == 0) return cudaSuccess;
+    const int bc = p->b[i - 1];
+    if (want_x) {   // X_{i,i-1} = -t_i H_{i,i-1}
       ZGemm g;
-      g.m = bN; g.n = ba; g.k = b0;
-      g.A = K; g.sA = (int64_t)bN * b0; g.lda = b0;
-      g.B = Rblk(a); g.sB = sR(a); g.ldb = ba;
-      g.C = Pblk(a); g.sC = (int64_t)ba * bN; g.ldc = ba;
+      g.m = bi; g.n = bc; g.k = bi;
+      g.A = cT(i); g.sA = s2; g.lda = bi;
+      g.B = Hblk(i, i - 1); g.sB = 0; g.ldb = bc; g.alpha = {-1.0, 0.0};
+      g.C = cX(i); g.sC = s2; g.ldc = bc;
       g.batch = C;
       NEGF_TRY(gemm(g));
+    }
+    {   // Y_{i-1,i} = -H_{i-1,i} t_i
+      ZGemm g;
+      g.m = bc; g.n = bi; g.k = bi;
+      g.A = Hblk(i - 1, i); g.sA = 0; g.lda = bi; g.alpha = {-1.0, 0.0};
+      g.B = cT(i); g.sB = s2; g.ldb = bi;
+      g.C = cY(i); g.sC = s2; g.ldc = bi;
+      g.batch = C;
+      NEGF_TRY(gemm(g));
+    }
+    if (!want_next) return cudaSuccess;
+    {   // S_{i-1} = E I - H_{i-1,i-1} (- Sigma_L on layer 0) + Y_{i-1,i} H_{i,i-1}
+      ZGemm g;
+      g.m = bc; g.n = bc; g.k = bi;
+      g.A = cY(i); g.sA = s2; g.lda = bi;
+      g.B = Hblk(i, i - 1); g.sB = 0; g.ldb = bc; g.alpha = {1.0, 0.0};
+      double2* out = Sslot(i - 1, i - 1);
+      g.C = out; g.sC = sS(); g.ldc = bc;
+      g.C1 = Hblk(i - 1, i - 1); g.sC1 = 0; g.ldc1 = bc; g.beta1 = {-1.0, 0.0};
+      g.dshift = E + e0; g.sD = 1; g.gamma = {1.0, 0.0};
+      if (i - 1 == 0 && sigL) { g.C2 = sigmaL(); g.sC2 = sig_stride; g.ldc2 = bc; g.beta2 = {-1.0, 0.0}; }
+      g.batch = C;
+      NEGF_TRY(gemm(g));
+    }
+    {   // P_{i-1} = -Y_{i-1,i} P_i
+      ZGemm g;
+      g.m = bc; g.n = bN; g.k = bi;
+      g.A = cY(i); g.sA = s2; g.lda = bi;
+      g.B = cP(i); g.sB = sN; g.ldb = bN; g.alpha = {-1.0, 0.0};
+      g.C = cP(i - 1); g.sC = sN; g.ldc = bN;
+      g.batch = C;
+      NEGF_TRY(gemm(g));
+    }
+    return cudaSuccess;
+  }
+
+  // Forward pass: the whole upward sweep with P_{N-1} = I and the suffix
+  // products alongside, a checkpoint (S_hi, P_hi) before the top layer of
+  // every segment but the first (the first stays in the rings), and
+  // G_1N = t_1 P_1 (first block of the last column) at the end.
+  cudaError_t ck_forward(double2* g1n_out, int64_t s_out) {
+    const int N = p->N, C = ne, b0 = p->b[0], bN = p->b[N - 1], bl = p->b[N - 1];
+    {   // S_{N-1} = E I - H - Sigma_R (- Sigma_L when N = 1)
+      double2* dst = Sslot(N - 1, N - 1);
+      NEGF_TRY(misc([&] {
+        return negf::assemble_diag(Hblk(N - 1, N - 1), E + e0, sigmaR(), sig_stride, dst, sS(), bl, C, st);
+      }));
+      if (N == 1 && sigL) {
+        ZGemm g;
+        g.m = bl; g.n = bl; g.k = 0;
+        g.A = dst; g.B = dst; g.lda = bl; g.ldb = bl;
+        g.C = dst; g.sC = sS(); g.ldc = bl;
+        g.C1 = dst; g.sC1 = sS(); g.ldc1 = bl; g.beta1 = {1.0, 0.0};
+        g.C2 = sigmaL(); g.sC2 = sig_stride; g.ldc2 = bl; g.beta2 = {-1.0, 0.0};
+        g.batch = C;
+        NEGF_TRY(gemm64(g));
+      }
+    }
+    NEGF_TRY(misc([&] { return negf::set_identity(cP(N - 1), p->bmaxN, bN, C, st); }));
+    for (int i = N - 1; i >= 0; --i) {
+      const int sg = i / p->ck_k, bi = p->b[i];
+      if (sg >= 1 && i == seg_hi(sg)) {
+        NEGF_TRY(misc([&] { return negf::copy_blocks(Sslot(i, i), sS(), ckS(sg), p->bmax2, sq(bi), C, st); }));
+        NEGF_TRY(misc([&] {
+          return negf::copy_blocks(cP(i), p->bmaxN, ckP(sg), p->bmaxN, (int64_t)bi * bN, C, st);
+        }));
+      }
+      NEGF_TRY(ck_eliminate(i, sg == 0, true));
+    }
+    ZGemm g;   // G_1N = t_1 P_1
+    g.m = b0; g.n = bN; g.k = b0;
+    g.A = cT(0); g.sA = p->bmax2; g.lda = b0;
+    g.B = cP(0); g.sB = p->bmaxN; g.ldb = bN;
+    g.C = g1n_out; g.sC = s_out; g.ldc = bN;
+    g.batch = C;
+    return gemm(g);
+  }
+
+  // Recompute segment sg >= 1 from its checkpoint: layers hi .. lo, keeping
+  // t, X, Y and P in the rings (the previous segment's top layer stays).
+  cudaError_t ck_recompute(int sg) {
+    const int C = ne, lo = seg_lo(sg), hi = seg_hi(sg), bh = p->b[hi], bN = p->b[p->N - 1];
+    NEGF_TRY(misc([&] { return negf::copy_blocks(ckS(sg), p->bmax2, Sslot(hi, hi), sS(), sq(bh), C, st); }));
+    NEGF_TRY(misc([&] { return negf::copy_blocks(ckP(sg), p->bmaxN, cP(hi), p->bmaxN, (int64_t)bh * bN, C, st); }));
+    for (int i = hi; i >= lo; --i) NEGF_TRY(ck_eliminate(i, true, i > lo));
+    return cudaSuccess;
+  }
+
+  // Reverse pass over segment sg, increasing layers: first row
+  // G_{1,i} = -G_{1,i-1} Y_{i-1,i} (ring of two), last column
+  // G_{i,N} = t_i P_i - X_{i,i-1} G_{i-1,N}, then U_i = K G_{1,i} over P_i.
+  cudaError_t ck_chains(int sg) {
+    const int C = ne, b0 = p->b[0], bN = p->b[p->N - 1];
+    const int64_t s2 = p->bmax2, sN = p->bmaxN;
+    double2* K = scr(6);
+    for (int i = seg_lo(sg); i <= seg_hi(sg); ++i) {
+      const int bi = p->b[i];
+      if (i == 0) {
+        NEGF_TRY(misc([&] { return negf::copy_blocks(cT(0), s2, Rblk(0), sR(0), sq(b0), C, st); }));
+      } else {
+        const int bc = p->b[i - 1];
+        ZGemm g;
+        g.m = b0; g.n = bi; g.k = bc;
+        g.A = Rblk(i - 1); g.sA = sR(i - 1); g.lda = bc;
+        g.B = cY(i); g.sB = s2; g.ldb = bi;
+        g.C = Rblk(i); g.sC = sR(i); g.ldc = bi; g.alpha = {-1.0, 0.0};
+        g.batch = C;
+        NEGF_TRY(gemm(g));
+      }
+      {
+        ZGemm g;   // G_{i,N} = t_i P_i
+        g.m = bi; g.n = bN; g.k = bi;
+        g.A = cT(i); g.sA = s2; g.lda = bi;
+        g.B = cP(i); g.sB = sN; g.ldb = bN;
+        g.C = cL(i); g.sC = sN; g.ldc = bN;
+        g.batch = C;
+        NEGF_TRY(gemm(g));
+      }
+      if (i > 0) {
+        const int bc = p->b[i - 1];
+        ZGemm h;   // G_{i,N} -= X_{i,i-1} G_{i-1,N}
+        h.m = bi; h.n = bN; h.k = bc;
+        h.A = cX(i); h.sA = s2; h.lda = bc;
+        h.B = cL(i - 1); h.sB = sN; h.ldb = bN;
+        h.C = cL(i); h.sC = sN; h.ldc = bN; h.alpha = {-1.0, 0.0};
+        h.C1 = cL(i); h.sC1 = sN; h.ldc1 = bN; h.beta1 = {1.0, 0.0};
+        h.batch = C;
+        NEGF_TRY(gemm(h));
+      }
+      {
+        ZGemm g;   // U_i = K G_{1,i}
+        g.m = bN; g.n = bi; g.k = b0;
+        g.A = K; g.sA = (int64_t)bN * b0; g.lda = b0;
+        g.B = Rblk(i); g.sB = sR(i); g.ldb = bi;
+        g.C = cP(i); g.sC = sN; g.ldc = bi;
+        g.batch = C;
+        NEGF_TRY(gemm(g));
+      }
     }
     return cudaSuccess;
   }
@@ -607,7 +804,7 @@ negf_status validate(const negf_desc* d) {
   if (d->precision != NEGF_FP64 && d->precision != NEGF_MIXED) return NEGF_ERR_ARG;
   if (d->refine_steps < 0 || d->refine_steps > 1) return NEGF_ERR_ARG;
   if (d->outputs & ~(NEGF_OUT_BAND | NEGF_OUT_G1N | NEGF_OUT_TRANSMISSION | NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
-  if (d->checkpoint_every != 0) return NEGF_ERR_ARG;
+  if (d->checkpoint_every < 0) return NEGF_ERR_ARG;
   if (d->product_bits != 0 && (d->product_bits < 16 || d->product_bits > 56)) return NEGF_ERR_ARG;
   for (int i = 0; i < d->n_blocks; ++i)
     if (d->block_sizes[i] < 1 || d->block_sizes[i] > NEGF_MAX_BLOCK) return NEGF_ERR_ARG;
@@ -652,10 +849,6 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   if (!p) return NEGF_ERR_NOMEM;
   p->N = d->n_blocks; p->w = w; p->nE = d->n_energies; p->n_domains = d->n_domains;
   p->precision = d->precision; p->refine = d->refine_steps; p->outputs = d->outputs;
-  // DDRGF runs in FP64 throughout: its sub-domains are closed systems (only
-  // the broadening eta), where the halo chains amplify rounding far beyond
-  // what 32-bit products leave.
-  if (p->n_domains > 1) p->precision = NEGF_FP64;
   p->ckpt = d->checkpoint_every;
   p->bits = d->product_bits;
   p->b.assign(d->block_sizes, d->block_sizes + d->n_blocks);
@@ -757,25 +950,42 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
       p->y_off[(size_t)i * w + (i - c - 1)] = ye; ye += (int64_t)p->b[c] * p->b[i];
     }
   }
-  p->t_elems = te; p->x_elems = xe; p->y_elems = ye;
   p->s_slot = sq(bmax);
   const bool grad = (d->outputs & NEGF_OUT_GRAD) != 0;
+  const int bN = p->b[N - 1], b0 = p->b[0];
+  p->bmax2 = sq(bmax);
+  p->bmaxN = (int64_t)bmax * bN;
+  if (grad && d->checkpoint_every > 0) {
+    // rings of k + 1 layers with fixed per-energy strides, plus one
+    // checkpoint (S_hi, P_hi) per segment of k layers
+    p->ck_k = std::min(d->checkpoint_every, N);
+    p->ck_nseg = (N + p->ck_k - 1) / p->ck_k;
+    te = xe = ye = (int64_t)(p->ck_k + 1) * p->bmax2;
+  }
+  p->t_elems = te; p->x_elems = xe; p->y_elems = ye;
+  p->full_row = grad && p->ck_k == 0;
   p->r_off.resize(N);
   int64_t re = 0;
   for (int j = 0; j < N; ++j) { p->r_off[j] = re; re += (int64_t)p->b[0] * p->b[j]; }
-  p->r_elems = grad ? re : bmax;   // ring: (w+1) slots of b0 x bmax
-  const int bN = p->b[N - 1], b0 = p->b[0];
+  p->r_elems = p->full_row ? re : bmax;   // ring: (w+1) slots of b0 x bmax
   p->p_off.resize(N);
   int64_t pe = 0;
   for (int i = 0; i < N; ++i) { p->p_off[i] = pe; pe += (int64_t)p->b[i] * bN; }
-  const bool refine = d->refine_steps > 0 && d->precision == NEGF_MIXED && d->n_domains == 1;
+  const bool refine = d->refine_steps > 0 && d->precision == NEGF_MIXED && d->n_domains == 1 && p->ck_k == 0;
   p->refine = refine ? 1 : 0;
   p->p_elems = (grad || refine) ? pe : 0;
+  int64_t rf_elems = refine ? pe : 0;
+  int64_t ck_elems = 0;
+  if (p->ck_k > 0) {
+    p->p_elems = (int64_t)(p->ck_k + 1) * p->bmaxN;
+    ck_elems = (int64_t)p->ck_nseg * (p->bmax2 + p->bmaxN);
+  }
   // Gamma_L, Gamma_R, P, Q, G_1N, and two more b1 x bN temporaries (gradient)
   p->scr_elems = sq(b0) + sq(bN) + 5 * (int64_t)b0 * bN;
 
   int64_t per_e = te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot +
-                  (grad ? re : (int64_t)(w + 1) * b0 * bmax) + 3 * p->p_elems + p->scr_elems + dd_e;
+                  (p->full_row ? re : (int64_t)(w + 1) * b0 * bmax) + 2 * p->p_elems + rf_elems + ck_elems +
+                  p->scr_elems + dd_e;
   // chunk energies so that the workspace stays within a budget: 45% of the
   // device memory free at plan time, at least 24 GiB (the caller's outputs
   // need the rest)
@@ -797,10 +1007,14 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   p->X_ws = q; q += xe * chunk;
   p->Y_ws = q; q += ye * chunk;
   p->S_ws = q; q += (int64_t)(w + 1) * (w + 1) * p->s_slot * chunk;
-  p->R_ws = q; q += (grad ? re : (int64_t)(w + 1) * b0 * bmax) * chunk;
+  p->R_ws = q; q += (p->full_row ? re : (int64_t)(w + 1) * b0 * bmax) * chunk;
   p->P_ws = q; q += p->p_elems * chunk;
   p->LC_ws = q; q += p->p_elems * chunk;
-  p->RF_ws = q; q += p->p_elems * chunk;
+  p->RF_ws = q; q += rf_elems * chunk;
+  if (p->ck_k > 0) {
+    p->CKS = q; q += (int64_t)p->ck_nseg * p->bmax2 * chunk;
+    p->CKP = q; q += (int64_t)p->ck_nseg * p->bmaxN * chunk;
+  }
   p->scratch = q; q += p->scr_elems * chunk;
   p->G1N_ws = p->scratch + (sq(b0) + sq(bN) + 2 * (int64_t)b0 * bN) * chunk;
   if (p->n_domains > 1) {
@@ -1258,7 +1472,7 @@ enum CallKind { CALL_SOLVE = 1, CALL_TRANS = 2, CALL_GRAD = 3 };
 // ranges, forks them onto the plan's side streams and joins them back, so
 // that one range's block products run while another range inverts.
 template <class F>
-cudaError_t for_groups(negf_plan_s* p, Sweep base, F f) {
+cudaError_t for_groups(negf_plan_s* p, Sweep base, F f, bool stagger = true) {
   const int G = std::min(p->groups, base.ne);
   if (G <= 1) return f(base);
   NEGF_TRY(cudaEventRecord(p->ev[0], p->stream));
@@ -1273,8 +1487,8 @@ cudaError_t for_groups(negf_plan_s* p, Sweep base, F f) {
     // Stagger: group g starts after the first inversion of group g-1, so
     // that one group's block products (tensor / integer pipes) run while the
     // next group inverts (FP64 pipe) instead of both alternating in step.
-    if (g > 0) NEGF_TRY(cudaStreamWaitEvent(s.st, p->stagger[g - 1], 0));
-    if (g + 1 < G) s.after_first_inv = p->stagger[g];
+    if (stagger && g > 0) NEGF_TRY(cudaStreamWaitEvent(s.st, p->stagger[g - 1], 0));
+    if (stagger && g + 1 < G) s.after_first_inv = p->stagger[g];
     NEGF_TRY(f(s));
   }
   for (int g = 1; g < G; ++g) {
@@ -1324,9 +1538,9 @@ negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigm
                        negf_c128* G_band, negf_c128* G_1N, int32_t* info) {
   if (!p || !H || !E || !info || sigma_E_stride < 0) return NEGF_ERR_ARG;
   if (!G_band && !G_1N) return NEGF_ERR_ARG;
-  if (p->precision == NEGF_MIXED) {
-    // mixed products are dispatched per launch; nothing else to check here
-  }
+  // a checkpointed adjoint plan keeps rings of k + 1 layers, not the whole
+  // factorisation the band needs
+  if (p->ck_k > 0 && G_band) return NEGF_ERR_UNSUPPORTED;
   CallKey key{};
   key.kind = CALL_SOLVE;
   key.stride = sigma_E_stride;
@@ -1348,6 +1562,7 @@ negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigm
         continue;
       }
       NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
+        if (p->ck_k > 0) return s.ck_forward((double2*)G_1N + (int64_t)s.e0 * s1, s1);
         NEGF_TRY(s.upward(G_band != nullptr || (G_1N && p->refine)));
         if (G_band) NEGF_TRY(s.downward());
         if (G_1N && p->refine) {   // G_1N = first block of the refined last column
@@ -1390,6 +1605,8 @@ negf_status negf_transmission(negf_plan_t* p, const negf_c128* H, const negf_c12
         double2* g1n = p->G1N_ws + (int64_t)s.wofs * s1;
         if (p->n_domains > 1) {
           NEGF_TRY(DD(p, s).run(false, g1n, s1));
+        } else if (p->ck_k > 0) {      // checkpointed plan: G_1N = t_1 (U^{-1} e_N)_1
+          NEGF_TRY(s.ck_forward(g1n, s1));
         } else if (p->refine) {
           NEGF_TRY(s.upward(true));
           NEGF_TRY(s.last_column());
@@ -1419,6 +1636,7 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
   std::memcpy(key.p, ptrs, sizeof(ptrs));
   const int N = p->N, b0 = p->b[0], bN = p->b[N - 1];
   const int64_t s1 = (int64_t)b0 * bN;
+  const bool ck = p->ck_k > 0;
   return run_captured(p, key, [&]() -> cudaError_t {
     NEGF_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * p->nE, p->stream));
     for (int e0 = 0; e0 < p->nE; e0 += p->chunk) {
@@ -1426,29 +1644,73 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
       const bool first = (e0 == 0);
       Sweep base{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
                  sigma_E_stride, (const double2*)E, nullptr, nullptr, info, e0, ne};
-      NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
-        double2* g1n = s.scr(4);
-        NEGF_TRY(s.upward(true));
-        NEGF_TRY(s.first_row(g1n, s1));
-        NEGF_TRY(s.last_column());
-        if (T) NEGF_TRY(s.transmission(g1n, s1, T));
-        return s.grad_prep(g1n, s1);
-      }));
-      // Energy-reduced adjoint products on the plan stream, over the chunk:
-      //   dH_ab (+)= 2 sum_e w_e (G_{b,N} U_a)^H = 2 sum_e w_e U_a^H G_{b,N}^H
-      Sweep s = base;   // wofs = 0: the whole chunk
-      for (int a = 0; a < N; ++a) {
-        for (int bb = std::max(0, a - 1); bb <= std::min(N - 1, a + 1); ++bb) {
-          const int ba = p->b[a], bbs = p->b[bb];
-          double2* out = (double2*)dH + p->band_off[(size_t)(bb - a + p->w) * N + a];
-          ZGemm g;
-          g.m = ba; g.n = bbs; g.k = bN;
-          g.A = s.Pblk(a); g.sA = (int64_t)ba * bN; g.lda = ba; g.opA = negf::OP_C;
-          g.B = s.LCblk(bb); g.sB = (int64_t)bbs * bN; g.ldb = bN; g.opB = negf::OP_C;
-          g.C = out; g.ldc = bbs; g.alpha = {2.0, 0.0};
-          if (!first) { g.C1 = out; g.ldc1 = bbs; g.beta1 = {1.0, 0.0}; }
-          g.weight = dL_dT + e0; g.reduce = 1; g.batch = ne;
-          NEGF_TRY(s.gemm64(g));
+      Sweep s = base;   // wofs = 0: the whole chunk, for the energy-reduced products
+
+      // dH_ab (+)= 2 sum_e w_e (G_{b,N} U_a)^H = 2 sum_e w_e U_a^H G_{b,N}^H
+      auto dh_pair = [&](int a, int bb, const double2* Ua, int64_t sUa, const double2* Lb, int64_t sLb) {
+        const int ba = p->b[a], bbs = p->b[bb];
+        double2* out = (double2*)dH + p->band_off[(size_t)(bb - a + p->w) * N + a];
+        ZGemm g;
+        g.m = ba; g.n = bbs; g.k = bN;
+        g.A = Ua; g.sA = sUa; g.lda = ba; g.opA = negf::OP_C;
+        g.B = Lb; g.sB = sLb; g.ldb = bN; g.opB = negf::OP_C;
+        g.C = out; g.ldc = bbs; g.alpha = {2.0, 0.0};
+        if (!first) { g.C1 = out; g.ldc1 = bbs; g.beta1 = {1.0, 0.0}; }
+        g.weight = dL_dT + e0; g.reduce = 1; g.batch = ne;
+        return s.gemm64(g);
+      };
+      // per-energy Sigma: the M-path part 2 w_e (G_{i,N} U_i)^H of layer 0 / N-1
+      auto sigma_mpath = [&](int side, const double2* Ui, int64_t sUi, const double2* Li, int64_t sLi) {
+        negf_c128* dS = side == 0 ? dSigma_L : dSigma_R;
+        if (!dS || sigma_E_stride == 0) return cudaSuccess;
+        const int bs = side == 0 ? b0 : bN;
+        ZGemm h;
+        h.m = bs; h.n = bs; h.k = bN;
+        h.A = Ui; h.sA = sUi; h.lda = bs; h.opA = negf::OP_C;
+        h.B = Li; h.sB = sLi; h.ldb = bN; h.opB = negf::OP_C;
+        h.C = (double2*)dS + (int64_t)e0 * sigma_E_stride; h.sC = sigma_E_stride; h.ldc = bs;
+        h.alpha = {2.0, 0.0}; h.weight = dL_dT + e0; h.batch = ne;
+        return s.gemm64(h);
+      };
+
+      if (!ck) {
+        NEGF_TRY(for_groups(p, base, [&](Sweep& sw) -> cudaError_t {
+          double2* g1n = sw.scr(4);
+          NEGF_TRY(sw.upward(true));
+          NEGF_TRY(sw.first_row(g1n, s1));
+          NEGF_TRY(sw.last_column());
+          if (T) NEGF_TRY(sw.transmission(g1n, s1, T));
+          return sw.grad_prep(g1n, s1);
+        }));
+        for (int a = 0; a < N; ++a)
+          for (int bb = std::max(0, a - 1); bb <= std::min(N - 1, a + 1); ++bb)
+            NEGF_TRY(dh_pair(a, bb, s.Pblk(a), (int64_t)p->b[a] * bN, s.LCblk(bb), (int64_t)p->b[bb] * bN));
+        NEGF_TRY(sigma_mpath(0, s.Pblk(0), s1, s.LCblk(0), s1));
+        NEGF_TRY(sigma_mpath(1, s.Pblk(N - 1), sq(bN), s.LCblk(N - 1), sq(bN)));
+      } else {
+        // checkpointed: forward sweep with checkpoints, then segment by
+        // segment (increasing layers) recompute, chains and reductions
+        NEGF_TRY(for_groups(p, base, [&](Sweep& sw) -> cudaError_t {
+          double2* g1n = sw.scr(4);
+          NEGF_TRY(sw.ck_forward(g1n, s1));
+          if (T) NEGF_TRY(sw.transmission(g1n, s1, T));
+          return sw.grad_K(g1n, s1);
+        }));
+        for (int sg = 0; sg < p->ck_nseg; ++sg) {
+          NEGF_TRY(for_groups(p, base, [&](Sweep& sw) -> cudaError_t {
+            if (sg > 0) NEGF_TRY(sw.ck_recompute(sg));
+            return sw.ck_chains(sg);
+          }, sg > 0));
+          const int lo = s.seg_lo(sg), hi = s.seg_hi(sg);
+          for (int i = lo; i <= hi; ++i) {
+            NEGF_TRY(dh_pair(i, i, s.cP(i), p->bmaxN, s.cL(i), p->bmaxN));
+            if (i > 0) {
+              NEGF_TRY(dh_pair(i - 1, i, s.cP(i - 1), p->bmaxN, s.cL(i), p->bmaxN));
+              NEGF_TRY(dh_pair(i, i - 1, s.cP(i), p->bmaxN, s.cL(i - 1), p->bmaxN));
+            }
+          }
+          if (lo == 0) NEGF_TRY(sigma_mpath(0, s.cP(0), p->bmaxN, s.cL(0), p->bmaxN));
+          if (hi == N - 1) NEGF_TRY(sigma_mpath(1, s.cP(N - 1), p->bmaxN, s.cL(N - 1), p->bmaxN));
         }
       }
       // Sigma terms.  Sigma enters M like H (the X_11 / X_NN parts are the
@@ -1492,21 +1754,12 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
         if (sigma_E_stride == 0) {
           g.C = (double2*)dS; g.ldc = bs; g.reduce = 1;
           if (!first) { g.C1 = (double2*)dS; g.ldc1 = bs; g.beta1 = {1.0, 0.0}; }
-          NEGF_TRY(s.gemm64(g));
-        } else {
-          // per energy: M-path part 2 w_e (G_{i,N} U_i)^H first, then the Gamma part
-          const int layer = side == 0 ? 0 : N - 1;
-          ZGemm h;
-          h.m = bs; h.n = bs; h.k = bN;
-          h.A = s.Pblk(layer); h.sA = (int64_t)bs * bN; h.lda = bs; h.opA = negf::OP_C;
-          h.B = s.LCblk(layer); h.sB = (int64_t)bs * bN; h.ldb = bN; h.opB = negf::OP_C;
-          h.C = (double2*)dS + (int64_t)e0 * sigma_E_stride; h.sC = sigma_E_stride; h.ldc = bs;
-          h.alpha = {2.0, 0.0}; h.weight = dL_dT + e0; h.batch = ne;
-          NEGF_TRY(s.gemm64(h));
-          g.C = h.C; g.sC = sigma_E_stride; g.ldc = bs;
-          g.C1 = h.C; g.sC1 = sigma_E_stride; g.ldc1 = bs; g.beta1 = {1.0, 0.0};
-          NEGF_TRY(s.gemm64(g));
+        } else {   // per energy, onto the M-path part written above
+          double2* out = (double2*)dS + (int64_t)e0 * sigma_E_stride;
+          g.C = out; g.sC = sigma_E_stride; g.ldc = bs;
+          g.C1 = out; g.sC1 = sigma_E_stride; g.ldc1 = bs; g.beta1 = {1.0, 0.0};
         }
+        NEGF_TRY(s.gemm64(g));
       }
     }
     if (sigma_E_stride == 0) {   // add the M-path parts dH_00 / dH_NN once, after all chunks

@@ -249,8 +249,10 @@ __device__ __forceinline__ long long acc_int(uint32_t bits) {
   return (bits >> 31) ? -v : v;
 }
 
-template <bool WIDE>   // WIDE: products longer than 64-bit level combination allows
-__global__ void __launch_bounds__(TC_THREADS) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
+// WIDE: products longer than 64-bit level combination allows.  The default
+// build is held to 64 registers so that four CTAs fit an SM.
+template <bool WIDE>
+__global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base_s;
@@ -583,6 +585,15 @@ cudaError_t kernels_init() {
   e = cudaFuncSetAttribute(zgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(zgemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  if (e != cudaSuccess) return e;
+  // all of the SM's unified L1 as shared memory: four 51 KB CTAs per SM (the
+  // 64-register build), and the same split the inversion kernel needs, so
+  // the two co-reside without reconfiguring the SM
+  e = cudaFuncSetAttribute(zgemm_tc_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(zgemm_tc_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   g_tc_smem_optin = dyn;
   return cudaSuccess;

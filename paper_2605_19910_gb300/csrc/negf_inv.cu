@@ -143,6 +143,9 @@ cudaError_t zinv_init() {
   size_t dyn = (size_t)optin - fa.sharedSizeBytes;
   e = cudaFuncSetAttribute(zinv_gj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(zinv_gj_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   g_inv_dyn_max = dyn;
   return cudaSuccess;
 }
@@ -332,6 +335,9 @@ cudaError_t zinv_cluster_init() {
   if (e != cudaSuccess) return e;
   const size_t dyn = (size_t)optin - fa.sharedSizeBytes;
   e = cudaFuncSetAttribute(zinv_gj_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(zinv_gj_cluster_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   g_cl_dyn_max = dyn;
   return cudaSuccess;

@@ -68,10 +68,11 @@ def test_ddrgf_default_split_balances_block_weights(P):
     run_dd(P, prob, 4)
 
 
-def test_ddrgf_mixed_request_runs_fp64(P):
-    # a mixed-precision DDRGF plan computes in FP64 (the FP64 bar applies)
-    prob = make_problem(24, b=32, w=2, n_energies=4, eta=1e-6, seed=50, diag_shift=DOM)
-    run_dd(P, prob, 3, precision="mixed")
+@pytest.mark.parametrize("w,N,nd,b", [(2, 24, 3, 32), (1, 40, 4, 48)])
+def test_ddrgf_mixed_bulk_fp64_interface(P, w, N, nd, b):
+    # sub-domain sweeps on the tensor cores, interface system in FP64
+    prob = make_problem(N, b=b, w=w, n_energies=4, eta=1e-6, seed=50 + N, diag_shift=DOM)
+    run_dd(P, prob, nd, precision="mixed", tol=MIXED_TOL)
 
 
 def test_ddrgf_penta256x32_full_size_error_bound(P):

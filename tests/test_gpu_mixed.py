@@ -1,4 +1,4 @@
-"""Parity of the mixed-precision CUDA path (tcgen05 split-TF32 block products,
+"""Parity of the mixed-precision CUDA path (tcgen05 block products from exact BF16 slices,
 FP64 block inversions) with the FP64 oracle, through the C-ABI: relative
 Frobenius error per energy and per output kind below 1e-5."""
 import pytest
