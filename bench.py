@@ -31,18 +31,19 @@ WORKLOAD = "batched64x64"
 METRIC = "selected-G^R energies x blocks / s"
 UNIT = "energy-blocks/s"
 
-# product width per workload on the mixed path: the 1024-layer nanowire has
-# localised states at eta = 1e-6 whose blocks need 48-bit products for 1e-5
-PRODUCT_BITS = {"wire1024": 48}
+# product width per workload on the mixed path: the 1024-layer nanowire and
+# the pentadiagonal chain at eta = 1e-6 have near-singular layers (localised
+# states) whose blocks need 48-bit products for 1e-5 (32 bits: 7e-4, 2e-4)
+PRODUCT_BITS = {"wire1024": 48, "penta256x32": 48}
 
 # DRAM traffic per unit (one block inversion) of the dominant kernel from an
 # ncu capture, valid only while the kernel source is the one captured; the
 # summary and its command are in profiles/zinv_gj_kernel_b64_512E_full.md
 NCU_TRAFFIC = {
     ("zinv_gj_kernel", 64): {
-        "bytes_per_unit": (33.589760e6 + 0.620032e6) / 512,
+        "bytes_per_unit": (33.590272e6 + 0.707584e6) / 512,
         "src": "paper_2605_19910_gb300/csrc/negf_inv.cu",
-        "sha256": "830c7535bd1799fadf5a00a958c7eb2b20897263ca7101417841c21c28bfe569",
+        "sha256": "822754194672a1cbd60c34eab0d70b7732c3e368ef01f55ae1df4212b2eaba73",
     },
 }
 

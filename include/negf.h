@@ -90,7 +90,9 @@ typedef struct {
   const int32_t* block_sizes;         /* host array of N sizes b_i, 1 <= b_i <= NEGF_MAX_BLOCK */
   int32_t band_n;                     /* n = 3 or 5 (w = (n-1)/2)              */
   int32_t n_energies;                 /* >= 1                                  */
-  int32_t n_domains;                  /* 1 = plain RGF, >1 = single-level DDRGF
+  int32_t n_domains;                  /* 1 = plain RGF, >1 = single-level DDRGF,
+                                         0 = chosen by negf_auto_domains (plain
+                                         RGF for plans with NEGF_OUT_GRAD)
                                          (Alg. 2): sub-domain sweeps in the
                                          plan's precision, interface Schur
                                          system and its RGF in FP64            */
@@ -116,9 +118,13 @@ typedef struct {
                                          NEGF_ERR_UNSUPPORTED.  Ignored without
                                          NEGF_OUT_GRAD.  < 0: NEGF_ERR_ARG.     */
   int32_t product_bits;               /* NEGF_MIXED: significant bits of the
-                                         tensor-core block products (0 = 32;
-                                         33..56 trade speed for accuracy on
-                                         ill-conditioned problems)             */
+                                         tensor-core block products, 16..56
+                                         (0 = 32 for RGF, 56 for DDRGF plans);
+                                         more bits trade speed for accuracy on
+                                         ill-conditioned problems.  Products
+                                         too long for exact slices at that
+                                         width (K x slices beyond the FP32
+                                         sums) run as FP64 DMMA products.      */
 } negf_desc;
 
 #define NEGF_MAX_BLOCK 160
@@ -134,6 +140,24 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream);
 
 /* Bytes of device workspace the plan holds. */
 size_t negf_workspace_bytes(const negf_plan_t* p);
+
+/* The plan's number of DDRGF (D2, D1) pairs (1 = plain RGF); -1 for NULL. */
+int32_t negf_plan_n_domains(const negf_plan_t* p);
+
+/* RGF / DDRGF choice made for n_domains = 0 (pure host arithmetic, no device
+ * call).  Cost model in launch waves: plain RGF takes N layer steps over n_E
+ * block inversions; DDRGF with d (D2, D1) pairs runs its d sub-domains
+ * concurrently (N/d steps over d n_E inversions, about 3x the work per step)
+ * followed by the interface RGF (d steps over n_E inversions of w-layer
+ * super-blocks, about w^3 the work); a step over x inversions costs
+ * ceil(x / slots) waves, slots = CTAs of the inversion kernel resident on
+ * sm_count SMs for the largest block (Sec. 3 cost model, restated for a GPU).
+ * Returns 1 or the power of two d >= 2 (pairs of at least 4w layers) of least
+ * cost; 1 for invalid arguments.  The paper recommends independent RGF runs
+ * when they fill the machine and DDRGF otherwise, with an "orchestrator" to
+ * choose (Sec. 4, DDRGF results, closing paragraphs). */
+int32_t negf_auto_domains(int32_t n_blocks, const int32_t* block_sizes, int32_t band_n, int32_t n_energies,
+                          int32_t sm_count);
 
 /* Element offset of block (i, i + d) in band-packed storage, or -1 if that
  * block does not exist (|d| > w or i + d outside [0, N)). */

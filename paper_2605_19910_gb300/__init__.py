@@ -49,6 +49,7 @@ PROF_NAMES = ["zinv_gj_kernel", "zgemm_f64_kernel", "zgemm_tc_kernel", "misc"]
 
 EXPORTED = [
     "negf_plan", "negf_workspace_bytes", "negf_band_offset", "negf_band_elems", "negf_solve",
+    "negf_plan_n_domains", "negf_auto_domains",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
 ]
@@ -118,6 +119,10 @@ def _load():
     lib.negf_last_cuda_error.restype = ctypes.c_char_p
     lib.negf_status_string.argtypes = [st]
     lib.negf_status_string.restype = ctypes.c_char_p
+    lib.negf_plan_n_domains.argtypes = [vp]
+    lib.negf_plan_n_domains.restype = i32
+    lib.negf_auto_domains.argtypes = [i32, ctypes.POINTER(i32), i32, i32, i32]
+    lib.negf_auto_domains.restype = i32
     return lib
 
 
@@ -191,6 +196,15 @@ def negf_solve_noalloc(block_sizes, band_n, n_energies, H, sigma_L, sigma_R, sig
 
 def negf_workspace_bytes(plan):
     return int(_lib.negf_workspace_bytes(plan))
+
+
+def negf_plan_n_domains(plan):
+    return int(_lib.negf_plan_n_domains(plan))
+
+
+def negf_auto_domains(block_sizes, band_n, n_energies, sm_count):
+    sizes = (ctypes.c_int32 * len(block_sizes))(*[int(b) for b in block_sizes])
+    return int(_lib.negf_auto_domains(len(block_sizes), sizes, int(band_n), int(n_energies), int(sm_count)))
 
 
 def negf_band_offset(plan, d, i):
@@ -304,6 +318,7 @@ class Plan:
         self.handle = negf_plan(self.sizes, band_n, self.n_energies, n_domains, domain_first_block, prec,
                                 refine_steps, outputs, checkpoint_every, self.stream.cuda_stream, product_bits)
         self.band_elems = negf_band_elems(self.handle)
+        self.n_domains = negf_plan_n_domains(self.handle)   # the choice made for n_domains = 0
         self.info = torch.zeros(self.n_energies, dtype=torch.int32, device="cuda")
 
     def close(self):

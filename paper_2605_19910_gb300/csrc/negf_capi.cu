@@ -105,6 +105,10 @@ struct negf_plan_s {
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;   // [0] fork, [1..] joins
   std::vector<cudaEvent_t> stagger;   // group g -> g + 1 start dependency
+  // DDRGF: the sub-domains of one energy group run concurrently, domain j of
+  // group g on dstream[g * n_domains + j] (j = 0 on the group's own stream)
+  std::vector<cudaStream_t> dstream;
+  std::vector<cudaEvent_t> dfork, djoin;
 
   // optional per-launch timing (negf_profile_enable)
   bool profiling = false;
@@ -154,6 +158,8 @@ struct Sweep {
   int e0, ne;         // energy range of this sweep
   int wofs = 0;       // energy offset of this range inside the chunk workspace
   int gb_e0 = 0;      // energy index of Gband[0] (0: caller's buffer; chunk start: internal buffer)
+  int grp = 0;        // energy group (stream set) of this sweep
+  int sdom = 0;       // DDRGF sub-domain: selects its own Schur-window slots
   cudaEvent_t after_first_inv = nullptr;   // recorded once, after this sweep's first inversion
 
   // Every kernel launch of the schedule goes through here so that the
@@ -205,7 +211,7 @@ struct Sweep {
   }
   double2* Sslot(int a, int bb) const {
     int r = p->w + 1;
-    return p->S_ws + (int64_t)((a % r) * r + (bb % r)) * p->s_slot * p->chunk + (int64_t)wofs * p->s_slot;
+    return p->S_ws + ((int64_t)sdom * r * r + (a % r) * r + (bb % r)) * p->s_slot * p->chunk + (int64_t)wofs * p->s_slot;
   }
   // Per-energy stride inside a shared slot is fixed (bmax^2, b_1 * bmax):
   // concurrent energy groups can be at different layers of different sizes.
@@ -800,7 +806,7 @@ negf_status validate(const negf_desc* d) {
   const int w = (d->band_n - 1) / 2;
   if (d->n_blocks <= w && d->n_blocks > 1) return NEGF_ERR_ARG;
   if (d->n_energies < 1) return NEGF_ERR_ARG;
-  if (d->n_domains < 1) return NEGF_ERR_ARG;
+  if (d->n_domains < 0 || (d->n_domains == 0 && d->domain_first_block)) return NEGF_ERR_ARG;
   if (d->precision != NEGF_FP64 && d->precision != NEGF_MIXED) return NEGF_ERR_ARG;
   if (d->refine_steps < 0 || d->refine_steps > 1) return NEGF_ERR_ARG;
   if (d->outputs & ~(NEGF_OUT_BAND | NEGF_OUT_G1N | NEGF_OUT_TRANSMISSION | NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
@@ -829,11 +835,54 @@ const char* negf_status_string(negf_status s) {
   return "negf: unknown status";
 }
 
-negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) {
+// RGF / DDRGF choice (n_domains = 0).  The batched sweep runs one CTA per
+// block inversion, so a layer step over x independent inversions takes
+// ceil(x / slots) waves (slots: CTAs of the inversion kernel resident on the
+// GPU).  Plain RGF: N layer steps over n_E inversions.  DDRGF with d
+// (D2, D1) pairs: the d sub-domains run concurrently, N/d layer steps over
+// d n_E inversions at about three times the work per step (halo rows and
+// columns, W / V, stitching), then the interface RGF: d steps over n_E
+// inversions of w-layer super-blocks (about w^3 the work).  The cheapest
+// d among 1 and the powers of two that leave pairs of at least 4w layers.
+int32_t negf_auto_domains(int32_t n_blocks, const int32_t* block_sizes, int32_t band_n, int32_t n_energies,
+                          int32_t sm_count) {
+  if (n_blocks < 1 || !block_sizes || band_n < 3 || n_energies < 1 || sm_count < 1) return 1;
+  const int w = (band_n - 1) / 2;
+  int bmax = 1;
+  for (int i = 0; i < n_blocks; ++i) bmax = std::max(bmax, (int)block_sizes[i]);
+  const double per_cta = (double)bmax * (bmax + 1) * 16.0 + 1024.0;
+  const double slots = bmax <= 119 ? (double)sm_count * std::max(1.0, std::floor(233472.0 / per_cta))
+                                   : std::max(1.0, std::floor(sm_count / 2.0));
+  auto waves = [&](double x) { return std::ceil(x / slots); };
+  double best = (double)n_blocks * waves(n_energies);
+  int best_d = 1;
+  for (int d = 2; n_blocks / d >= 4 * w; d *= 2) {
+    const double t = (double)n_blocks / d * waves((double)n_energies * d) * 3.0 +
+                     (double)d * waves(n_energies) * w * w * w;
+    if (t < best) { best = t; best_d = d; }
+  }
+  return best_d;
+}
+
+int32_t negf_plan_n_domains(const negf_plan_t* p) { return p ? p->n_domains : -1; }
+
+negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream) {
   if (!out) return NEGF_ERR_ARG;
   *out = nullptr;
-  negf_status v = validate(d);
+  negf_status v = validate(din);
   if (v != NEGF_OK) return v;
+  negf_desc dd_auto = *din;
+  const negf_desc* d = &dd_auto;
+  if (dd_auto.n_domains == 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    dd_auto.n_domains = (din->outputs & NEGF_OUT_GRAD)
+                            ? 1
+                            : negf_auto_domains(din->n_blocks, din->block_sizes, din->band_n, din->n_energies, sms);
+  }
   const int w = (d->band_n - 1) / 2;
   if (d->n_domains > 1 && (d->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_UNSUPPORTED;
   if (d->precision == NEGF_MIXED && !negf::zgemm_tc_available()) return NEGF_ERR_UNSUPPORTED;
@@ -851,6 +900,11 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   p->precision = d->precision; p->refine = d->refine_steps; p->outputs = d->outputs;
   p->ckpt = d->checkpoint_every;
   p->bits = d->product_bits;
+  // DDRGF sub-domains are closed systems (broadened by eta only): near their
+  // internal resonances the halo chains amplify product rounding by up to
+  // ~1e7 (measured on the pentadiagonal 256 x 32 workload at eta = 1e-6), so
+  // mixed DDRGF defaults to 56-bit products
+  if (p->n_domains > 1 && p->precision == NEGF_MIXED && p->bits == 0) p->bits = 56;
   p->b.assign(d->block_sizes, d->block_sizes + d->n_blocks);
   p->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&p->device);
@@ -983,7 +1037,7 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   // Gamma_L, Gamma_R, P, Q, G_1N, and two more b1 x bN temporaries (gradient)
   p->scr_elems = sq(b0) + sq(bN) + 5 * (int64_t)b0 * bN;
 
-  int64_t per_e = te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot +
+  int64_t per_e = te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot * std::max(1, p->n_domains) +
                   (p->full_row ? re : (int64_t)(w + 1) * b0 * bmax) + 2 * p->p_elems + rf_elems + ck_elems +
                   p->scr_elems + dd_e;
   // chunk energies so that the workspace stays within a budget: 45% of the
@@ -1006,7 +1060,7 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
   p->T_ws = q; q += te * chunk;
   p->X_ws = q; q += xe * chunk;
   p->Y_ws = q; q += ye * chunk;
-  p->S_ws = q; q += (int64_t)(w + 1) * (w + 1) * p->s_slot * chunk;
+  p->S_ws = q; q += (int64_t)(w + 1) * (w + 1) * p->s_slot * std::max(1, p->n_domains) * chunk;
   p->R_ws = q; q += (p->full_row ? re : (int64_t)(w + 1) * b0 * bmax) * chunk;
   p->P_ws = q; q += p->p_elems * chunk;
   p->LC_ws = q; q += p->p_elems * chunk;
@@ -1067,6 +1121,25 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream) 
       if (cudaEventCreateWithFlags(&e3, cudaEventDisableTiming) != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
       p->stagger.push_back(e3);
     }
+    if (p->n_domains > 1) {
+      const int nd = p->n_domains;
+      p->dstream.assign((size_t)p->groups * nd, nullptr);
+      for (int g = 0; g < p->groups; ++g) {
+        cudaEvent_t f = nullptr;
+        if (cudaEventCreateWithFlags(&f, cudaEventDisableTiming) != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
+        p->dfork.push_back(f);
+        for (int j = 0; j < nd; ++j) {
+          cudaEvent_t jn = nullptr;
+          if (cudaEventCreateWithFlags(&jn, cudaEventDisableTiming) != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
+          p->djoin.push_back(jn);
+          if (j == 0) continue;
+          if (cudaStreamCreateWithFlags(&p->dstream[(size_t)g * nd + j], cudaStreamNonBlocking) != cudaSuccess) {
+            negf_destroy(p);
+            return NEGF_ERR_CUDA;
+          }
+        }
+      }
+    }
   }
   *out = p;
   return NEGF_OK;
@@ -1089,6 +1162,9 @@ void negf_destroy(negf_plan_t* p) {
   for (auto s2 : p->side) cudaStreamDestroy(s2);
   for (auto e2 : p->ev) cudaEventDestroy(e2);
   for (auto e3 : p->stagger) cudaEventDestroy(e3);
+  for (auto s3 : p->dstream) if (s3) cudaStreamDestroy(s3);
+  for (auto e4 : p->dfork) cudaEventDestroy(e4);
+  for (auto e5 : p->djoin) cudaEventDestroy(e5);
   cudaFree(p->ws);
   cudaFree(p->d_err);
   delete p;
@@ -1455,12 +1531,39 @@ struct DD {
               (int64_t)P0 * Pn, Pn, out, sOut, b(N - 1), -1.0, false);
   }
 
+  // Runs f(dd_j, j) for every sub-domain j concurrently: domain j of this
+  // energy group on its own stream (graph branch), joined back afterwards.
+  // Each domain sweeps in its own Schur-window slots; everything else a
+  // domain writes (its layers' halos, W / V / Z, band blocks next to its
+  // separators) is disjoint from the other domains'.
+  template <class F>
+  cudaError_t for_domains(F f) {
+    const int g = s.grp;
+    NEGF_TRY(cudaEventRecord(p->dfork[g], s.st));
+    for (int j = 1; j < nd; ++j) NEGF_TRY(cudaStreamWaitEvent(p->dstream[(size_t)g * nd + j], p->dfork[g], 0));
+    for (int j = 0; j < nd; ++j) {
+      Sweep sj = s;
+      sj.sdom = j;
+      if (j > 0) {
+        sj.st = p->dstream[(size_t)g * nd + j];
+        sj.after_first_inv = nullptr;
+      }
+      DD dj(p, sj);
+      NEGF_TRY(f(dj, j));
+      if (j == 0) s.after_first_inv = sj.after_first_inv;
+    }
+    for (int j = 1; j < nd; ++j) {
+      NEGF_TRY(cudaEventRecord(p->djoin[(size_t)g * nd + j], p->dstream[(size_t)g * nd + j]));
+      NEGF_TRY(cudaStreamWaitEvent(s.st, p->djoin[(size_t)g * nd + j], 0));
+    }
+    return cudaSuccess;
+  }
+
   cudaError_t run(bool want_band, double2* g1n_out, int64_t s1) {
-    for (int j = 0; j < nd; ++j) NEGF_TRY(domain(j));
+    NEGF_TRY(for_domains([&](DD& d, int j) { return d.domain(j); }));
     NEGF_TRY(schur());
     NEGF_TRY(interface(g1n_out != nullptr));
-    if (want_band)
-      for (int j = 0; j < nd; ++j) NEGF_TRY(stitch(j));
+    if (want_band) NEGF_TRY(for_domains([&](DD& d, int j) { return d.stitch(j); }));
     if (g1n_out) NEGF_TRY(g1n(g1n_out, s1));
     return cudaSuccess;
   }
@@ -1481,6 +1584,7 @@ cudaError_t for_groups(negf_plan_s* p, Sweep base, F f, bool stagger = true) {
     const int lo = (int)((int64_t)base.ne * g / G), hi = (int)((int64_t)base.ne * (g + 1) / G);
     Sweep s = base;
     s.st = g == 0 ? p->stream : p->side[g - 1];
+    s.grp = g;
     s.e0 = base.e0 + lo;
     s.ne = hi - lo;
     s.wofs = base.wofs + lo;

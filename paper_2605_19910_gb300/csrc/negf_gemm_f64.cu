@@ -4,10 +4,14 @@
 // the three downward products; Sec. 2.3 for the n-diagonal window) are
 // dense b x b complex contractions batched over energies.  Each CTA computes
 // a 32 x 32 tile of one C[e]; the four warps each own a 16 x 16 sub-tile made
-// of 2 x 2 DMMA m8n8k4 tiles per real component.  A complex product is four
-// real DMMAs per k-step (re*re - im*im, re*im + im*re).  Operands are staged
-// through shared memory as separate real / imaginary planes so that the DMMA
-// fragments load with one 8-byte access per lane.
+// of 2 x 2 DMMA m8n8k4 tiles per real component.  A complex product takes
+// three real DMMAs per k-step (the 3M / Gauss form):
+//     T1 = Re A Re B,  T2 = Im A Im B,  T3 = (Re A + Im A)(Re B + Im B),
+//     Re C = T1 - T2,  Im C = T3 - T1 - T2,
+// three quarters of the four-product form's FP64 tensor work; the operand sums
+// are formed once per staged element.  Operands are staged through shared
+// memory as separate real / imaginary / sum planes so that the DMMA fragments
+// load with one 8-byte access per lane.
 #include "negf_common.cuh"
 #include "negf_kernels.h"
 
@@ -27,9 +31,11 @@ __device__ __forceinline__ void dmma884(double& c0, double& c1, double a, double
 
 __device__ __forceinline__ double2 cscale(double2 a, double2 s) { return cmul(a, s); }
 
-// Loads the BM x BK tile of op(A) (rows m0.., cols k0..) into planar smem.
+// Loads the BM x BK tile of op(A) (rows m0.., cols k0..) into planar smem
+// (real, imaginary, real + imaginary).
 __device__ __forceinline__ void load_a_tile(const double2* __restrict__ A, int lda, int opA, int m, int k,
-                                            int m0, int k0, double wgt, double* Ar, double* Ai, int tid) {
+                                            int m0, int k0, double wgt, double* Ar, double* Ai, double* As,
+                                            int tid) {
   for (int idx = tid; idx < BM * BK; idx += NTHREADS) {
     int r, c;
     if (opA == OP_N) { r = idx / BK; c = idx % BK; } else { c = idx / BM; r = idx % BM; }
@@ -39,14 +45,16 @@ __device__ __forceinline__ void load_a_tile(const double2* __restrict__ A, int l
       if (opA == OP_N) v = A[(int64_t)gr * lda + gc];
       else { v = A[(int64_t)gc * lda + gr]; v.y = -v.y; }
     }
-    Ar[r * LDA_S + c] = v.x * wgt;
-    Ai[r * LDA_S + c] = v.y * wgt;
+    if (wgt != 1.0) { v.x *= wgt; v.y *= wgt; }
+    Ar[r * LDA_S + c] = v.x;
+    Ai[r * LDA_S + c] = v.y;
+    As[r * LDA_S + c] = v.x + v.y;
   }
 }
 
 // Loads the BK x BN tile of op(B) (rows k0.., cols n0..) into planar smem.
 __device__ __forceinline__ void load_b_tile(const double2* __restrict__ B, int ldb, int opB, int k, int n,
-                                            int k0, int n0, double* Br, double* Bi, int tid) {
+                                            int k0, int n0, double* Br, double* Bi, double* Bs, int tid) {
   for (int idx = tid; idx < BK * BN; idx += NTHREADS) {
     int r, c;
     if (opB == OP_N) { r = idx / BN; c = idx % BN; } else { c = idx / BK; r = idx % BK; }
@@ -58,12 +66,13 @@ __device__ __forceinline__ void load_b_tile(const double2* __restrict__ B, int l
     }
     Br[r * LDB_S + c] = v.x;
     Bi[r * LDB_S + c] = v.y;
+    Bs[r * LDB_S + c] = v.x + v.y;
   }
 }
 
 __global__ void __launch_bounds__(NTHREADS) zgemm_f64_kernel(ZGemm g, int tiles_n) {
-  __shared__ double Ar[BM * LDA_S], Ai[BM * LDA_S];
-  __shared__ double Br[BK * LDB_S], Bi[BK * LDB_S];
+  __shared__ double Ar[BM * LDA_S], Ai[BM * LDA_S], As[BM * LDA_S];
+  __shared__ double Br[BK * LDB_S], Bi[BK * LDB_S], Bs[BK * LDB_S];
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -72,14 +81,13 @@ __global__ void __launch_bounds__(NTHREADS) zgemm_f64_kernel(ZGemm g, int tiles_
   const int tile = blockIdx.x;
   const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
 
-  double acc_re[2][2][2], acc_im[2][2][2];
+  double t1[2][2][2], t2[2][2][2], t3[2][2][2];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      acc_re[a][c][0] = acc_re[a][c][1] = 0.0;
-      acc_im[a][c][0] = acc_im[a][c][1] = 0.0;
-    }
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) t1[a][c][i] = t2[a][c][i] = t3[a][c][i] = 0.0;
 
   const int e_first = g.reduce ? 0 : blockIdx.y;
   const int e_last = g.reduce ? g.batch : blockIdx.y + 1;
@@ -89,33 +97,33 @@ __global__ void __launch_bounds__(NTHREADS) zgemm_f64_kernel(ZGemm g, int tiles_
     const double wgt = g.weight ? g.weight[e] : 1.0;   // per-batch real weight on A
     if (wgt == 0.0 && g.reduce) continue;
     for (int k0 = 0; k0 < g.k; k0 += BK) {
-      load_a_tile(A, g.lda, g.opA, g.m, g.k, m0, k0, wgt, Ar, Ai, tid);
-      load_b_tile(B, g.ldb, g.opB, g.k, g.n, k0, n0, Br, Bi, tid);
+      load_a_tile(A, g.lda, g.opA, g.m, g.k, m0, k0, wgt, Ar, Ai, As, tid);
+      load_b_tile(B, g.ldb, g.opB, g.k, g.n, k0, n0, Br, Bi, Bs, tid);
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; kk += 4) {
-        double are[2], aim[2], anim[2], bre[2], bim[2];
+        double are[2], aim[2], asum[2], bre[2], bim[2], bsum[2];
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
           int r = wm * 16 + a * 8 + gq;
           are[a] = Ar[r * LDA_S + kk + tq];
           aim[a] = Ai[r * LDA_S + kk + tq];
-          anim[a] = -aim[a];
+          asum[a] = As[r * LDA_S + kk + tq];
         }
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           int col = wn * 16 + c * 8 + gq;
           bre[c] = Br[(kk + tq) * LDB_S + col];
           bim[c] = Bi[(kk + tq) * LDB_S + col];
+          bsum[c] = Bs[(kk + tq) * LDB_S + col];
         }
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
-            dmma884(acc_re[a][c][0], acc_re[a][c][1], are[a], bre[c]);
-            dmma884(acc_re[a][c][0], acc_re[a][c][1], anim[a], bim[c]);
-            dmma884(acc_im[a][c][0], acc_im[a][c][1], are[a], bim[c]);
-            dmma884(acc_im[a][c][0], acc_im[a][c][1], aim[a], bre[c]);
+            dmma884(t1[a][c][0], t1[a][c][1], are[a], bre[c]);
+            dmma884(t2[a][c][0], t2[a][c][1], aim[a], bim[c]);
+            dmma884(t3[a][c][0], t3[a][c][1], asum[a], bsum[c]);
           }
       }
       __syncthreads();
@@ -137,7 +145,9 @@ __global__ void __launch_bounds__(NTHREADS) zgemm_f64_kernel(ZGemm g, int tiles_
         int row = m0 + wm * 16 + a * 8 + gq;
         int col = n0 + wn * 16 + c * 8 + 2 * tq + i;
         if (row < g.m && col < g.n) {
-          double2 v = cscale(make_double2(acc_re[a][c][i], acc_im[a][c][i]), g.alpha);
+          const double re = t1[a][c][i] - t2[a][c][i];
+          const double im = t3[a][c][i] - t1[a][c][i] - t2[a][c][i];
+          double2 v = cscale(make_double2(re, im), g.alpha);
           if (C1) {
             double2 x = cmul(g.beta1, C1[(int64_t)row * g.ldc1 + col]);
             v.x += x.x; v.y += x.y;

@@ -48,7 +48,8 @@ def test_invalid_descriptors_are_rejected_before_any_launch():
     bad = [dict(block_sizes=[4, 4], band_n=4), dict(block_sizes=[4, 0]), dict(block_sizes=[4, 4], n_energies=0),
            dict(block_sizes=[4, 4], band_n=5), dict(block_sizes=[4, 200]), dict(block_sizes=[4, 4], precision=7),
            dict(block_sizes=[4, 4], outputs=64), dict(block_sizes=[4, 4], refine_steps=3),
-           dict(block_sizes=[4, 4], checkpoint_every=-1), dict(block_sizes=[4, 4], product_bits=99)]
+           dict(block_sizes=[4, 4], checkpoint_every=-1), dict(block_sizes=[4, 4], product_bits=99),
+           dict(block_sizes=[4] * 8, n_domains=-1), dict(block_sizes=[4] * 8, n_domains=0, domain_first_block=[0])]
     for kw in bad:
         with pytest.raises(P.NegfError) as ei:
             P.negf_plan(**kw)

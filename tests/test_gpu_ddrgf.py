@@ -47,7 +47,7 @@ def run_dd(P, prob, n_domains, first=None, idx=None, tol=FP64_TOL, precision="fp
             assert band_rel_err(Gb[e], dd["band"], prob.sizes, prob.w) < tol, e
 
 
-DOM = 4.0   # diagonal shift: M diagonally dominant for |E| <= 2
+DOM = 4.0   # diagonal shift: layer blocks well conditioned for E < 2 (E = 2 touches the spectrum)
 
 
 @pytest.mark.parametrize("w,N,nd", [(1, 20, 4), (1, 9, 2), (2, 24, 3), (2, 30, 5)])
@@ -70,9 +70,31 @@ def test_ddrgf_default_split_balances_block_weights(P):
 
 @pytest.mark.parametrize("w,N,nd,b", [(2, 24, 3, 32), (1, 40, 4, 48)])
 def test_ddrgf_mixed_bulk_fp64_interface(P, w, N, nd, b):
-    # sub-domain sweeps on the tensor cores, interface system in FP64
+    # sub-domain sweeps on the tensor cores (56-bit products, the DDRGF
+    # default), interface system in FP64; E = 2 lies inside the spectrum of
+    # these shifted matrices, where 32-bit products miss the bar (5e-5)
     prob = make_problem(N, b=b, w=w, n_energies=4, eta=1e-6, seed=50 + N, diag_shift=DOM)
     run_dd(P, prob, nd, precision="mixed", tol=MIXED_TOL)
+
+
+def test_ddrgf_penta256x32_mixed_full_size_error_bound(P):
+    """The pentadiagonal workload (256 x 32, n = 5, 1024 energies, 8 domains,
+    eta = 1e-6) with mixed sub-domain sweeps at the 56-bit default: sampled
+    energies within the mixed bar (measured max 4.7e-7, FP64 DDRGF 1.3e-6)."""
+    import torch
+    prob = workload("penta256x32")
+    Hp, sL, sR, E = to_dev(prob, torch)
+    nE = len(prob.energies)
+    plan = P.Plan(prob.sizes, 5, nE, n_domains=8, precision="mixed", outputs=P.NEGF_OUT_BAND)
+    Gb, _ = plan.solve(Hp, sL, sR, E, g1n=False)
+    assert not plan.info.cpu().numpy().any()
+    plan.close()
+    errs = []
+    for e in range(0, nE, 128):
+        ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, 2)
+        errs.append(band_rel_err(Gb[e].cpu().numpy(), ref["band"], prob.sizes, 2))
+    assert max(errs) < MIXED_TOL, errs
+    assert np.median(errs) < 1e-8, errs
 
 
 def test_ddrgf_penta256x32_full_size_error_bound(P):
@@ -95,3 +117,20 @@ def test_ddrgf_penta256x32_full_size_error_bound(P):
         errs.append(band_rel_err(Gb[e], ref["band"], prob.sizes, 2))
     assert max(errs) < 1e-5, errs
     assert np.median(errs) < 1e-8, errs
+
+
+def test_auto_domains_plans_follow_the_cost_model(P):
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # one energy on a long chain: DDRGF; parity as for an explicit split
+    prob = make_problem(64, b=16, w=1, n_energies=1, eta=1e-3, seed=77, diag_shift=DOM)
+    d = P.negf_auto_domains(prob.sizes, 3, 1, sms)
+    assert d > 1
+    plan = P.Plan(prob.sizes, 3, 1, n_domains=0)
+    assert plan.n_domains == d
+    plan.close()
+    run_dd(P, prob, 0)
+    # many energies: plain RGF
+    plan = P.Plan([32] * 16, 3, 1024, n_domains=0)
+    assert plan.n_domains == 1
+    plan.close()
