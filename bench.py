@@ -72,6 +72,8 @@ def _args():
     ap.add_argument("--product-bits", type=int, default=None,
                     help="bits of the tensor-core block products on the mixed path "
                          "(default: 48 for the 1024-layer nanowire, 32 otherwise)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the plan's default energy-group count instead of negf_autotune's choice")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -220,6 +222,13 @@ def run_ours(a, rank, world, local_rank):
 
     def step():
         plan.solve(H, sL, sR, E, out_band=Gb, out_g1n=G1, sync=False)
+
+    # energy-group autotuner on these inputs (untimed, before the warm-up)
+    tune = None
+    if not a.no_autotune:
+        best, tms = plan.autotune(H, sL, sR, E, out_band=Gb, out_g1n=G1)
+        tune = {"energy_groups": best, "ms_per_solve_by_groups": {str(k): v for k, v in tms.items()}}
+    groups = P.negf_plan_groups(plan.handle)
 
     for _ in range(a.warmup):
         step()
@@ -410,7 +419,9 @@ def run_ours(a, rank, world, local_rank):
                        "outputs": "band + G_1N per energy",
                        "l2": "no flush: each step writes %.1f GB of selected blocks and %.1f GB of sweep "
                              "workspace, both far above the 129 MB L2" % (Gb.numel() * 16 / 1e9, ws_gb),
-                       "parallelism": f"replicas x{world} (energies)"},
+                       "parallelism": f"replicas x{world} (energies)",
+                       "energy_groups": groups},
+            "autotune": tune,
             "effective_tflops_paper_count": flops_step / (ms * 1e-3) / 1e12 * world,
             "rel_err_vs_oracle_sampled": rel,
             "roofline": roof,

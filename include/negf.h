@@ -128,6 +128,7 @@ typedef struct {
 } negf_desc;
 
 #define NEGF_MAX_BLOCK 160
+#define NEGF_MAX_GROUPS 8   /* energy groups (concurrent streams) per plan */
 
 typedef struct negf_plan_s negf_plan_t;   /* opaque plan handle */
 
@@ -145,17 +146,17 @@ size_t negf_workspace_bytes(const negf_plan_t* p);
 int32_t negf_plan_n_domains(const negf_plan_t* p);
 
 /* RGF / DDRGF choice made for n_domains = 0 (pure host arithmetic, no device
- * call).  Cost model in launch waves: plain RGF takes N layer steps over n_E
- * block inversions; DDRGF with d (D2, D1) pairs runs its d sub-domains
- * concurrently (N/d steps over d n_E inversions, about 3x the work per step)
- * followed by the interface RGF (d steps over n_E inversions of w-layer
- * super-blocks, about w^3 the work); a step over x inversions costs
- * ceil(x / slots) waves, slots = CTAs of the inversion kernel resident on
- * sm_count SMs for the largest block (Sec. 3 cost model, restated for a GPU).
- * Returns 1 or the power of two d >= 2 (pairs of at least 4w layers) of least
- * cost; 1 for invalid arguments.  The paper recommends independent RGF runs
- * when they fill the machine and DDRGF otherwise, with an "orchestrator" to
- * choose (Sec. 4, DDRGF results, closing paragraphs). */
+ * call).  Cost model: a layer step over x independent block problems costs
+ * max(lat, thr x / slots) latency-bound RGF layer steps, slots = inversion
+ * CTAs resident on sm_count SMs for the largest block.  Plain RGF: N steps
+ * over n_E problems (lat = thr = 1).  DDRGF with d (D2, D1) pairs: N/d steps
+ * over d n_E concurrent sub-domain problems (lat 4.5, thr 15: the extended
+ * sweep's extra launches and work, fitted to GB300 runs), then the interface
+ * RGF, d steps over n_E problems at w^3 the work.  Returns 1 or the power of
+ * two d >= 2 (pairs of at least 4w layers) of least cost; 1 for invalid
+ * arguments.  The paper recommends independent RGF runs when they fill the
+ * machine and DDRGF otherwise, with an "orchestrator" to choose (Sec. 4,
+ * DDRGF results, closing paragraphs). */
 int32_t negf_auto_domains(int32_t n_blocks, const int32_t* block_sizes, int32_t band_n, int32_t n_energies,
                           int32_t sm_count);
 
@@ -204,6 +205,38 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
                       const negf_c128* E, const double* dL_dT, double* T,
                       negf_c128* dH, negf_c128* dSigma_L, negf_c128* dSigma_R,
                       int32_t* info);
+
+/* A-posteriori accuracy of a band from the band alone (no oracle, no
+ * off-band block): the diagonal blocks of M G - I,
+ *   R_i = sum_{|c - i| <= w} M_{i,c} G_{c,i} - I,   M = E I - H - Sigma,
+ *   res[e] = sqrt( sum_i ||R_i||_F^2 / sum_i b_i ),
+ * with FP64 products.  G_band: n_energies band-packed matrices as written by
+ * negf_solve; res: n_energies doubles (device).  Asynchronous on the plan's
+ * stream like negf_solve; uses the plan's workspace, so it must not overlap
+ * another call on the same plan.  0 for the exact band; a band with relative
+ * error r typically gives res of order r * ||M|| ||G||. */
+negf_status negf_band_residual(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                               const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                               const negf_c128* G_band, double* res);
+
+/* Energy-group autotuner.  A plan splits the energies of a chunk into
+ * groups that run concurrently on forked streams (graph branches), so that
+ * one group's tensor-core products overlap another's inversions.  This call
+ * replays the plan's negf_solve schedule on the caller's buffers (same
+ * arguments as negf_solve) with 1, 2, 4 and 8 groups (at most
+ * NEGF_MAX_GROUPS, at most one group per energy of a chunk), `reps` timed
+ * repetitions each after one warm-up, and keeps the fastest count for the
+ * plan's later calls.  ms (nullable): 4 doubles, the time per solve for each
+ * candidate or -1 where skipped.  best_groups (nullable): the kept count.
+ * Synchronises the plan's stream.  NEGF_ERR_UNSUPPORTED for DDRGF and
+ * checkpointed plans (fixed stream sets). */
+negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                          const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                          negf_c128* G_band, negf_c128* G_1N, int32_t* info, int32_t reps,
+                          int32_t* best_groups, double* ms);
+
+/* The plan's current number of energy groups; -1 for NULL. */
+int32_t negf_plan_groups(const negf_plan_t* p);
 
 /* Wait for the plan's stream, then return the first error the device
  * reported since the previous negf_sync (and clear it). */

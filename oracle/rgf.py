@@ -503,3 +503,18 @@ def rgf_flops_paper(sizes, w):
     getrs = N * (2 * w + 1) - w * w - w
     gemm = (3 * w * w + w) * N - 2 * w ** 3 - 2 * w * w
     return (lu * 8.0 / 3.0 + getrs * 8.0 + gemm * 8.0) * b ** 3
+
+
+def band_diag_residual(M, sizes, w, band):
+    """A-posteriori check of a band of G = M^{-1} from band blocks alone: the
+    diagonal blocks of M G - I, R_i = sum_{|c - i| <= w} M_{i,c} G_{c,i} - I
+    (every block of M in row i meets only band blocks of G in column i), as
+    ``sqrt(sum_i ||R_i||_F^2 / sum_i b_i)``.  Zero for the exact band."""
+    N = len(sizes)
+    num = 0.0
+    for i in range(N):
+        R = -np.eye(sizes[i], dtype=np.complex128)
+        for c in range(max(0, i - w), min(N - 1, i + w) + 1):
+            R = R + M[(i, c)] @ band[(c, i)]
+        num += float(np.sum(np.abs(R) ** 2))
+    return float(np.sqrt(num / float(sum(sizes))))

@@ -49,7 +49,7 @@ PROF_NAMES = ["zinv_gj_kernel", "zgemm_f64_kernel", "zgemm_tc_kernel", "misc"]
 
 EXPORTED = [
     "negf_plan", "negf_workspace_bytes", "negf_band_offset", "negf_band_elems", "negf_solve",
-    "negf_plan_n_domains", "negf_auto_domains",
+    "negf_plan_n_domains", "negf_auto_domains", "negf_band_residual", "negf_autotune", "negf_plan_groups",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
 ]
@@ -119,6 +119,13 @@ def _load():
     lib.negf_last_cuda_error.restype = ctypes.c_char_p
     lib.negf_status_string.argtypes = [st]
     lib.negf_status_string.restype = ctypes.c_char_p
+    lib.negf_autotune.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, i32, ctypes.POINTER(i32),
+                                  ctypes.POINTER(ctypes.c_double)]
+    lib.negf_autotune.restype = st
+    lib.negf_plan_groups.argtypes = [vp]
+    lib.negf_plan_groups.restype = i32
+    lib.negf_band_residual.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+    lib.negf_band_residual.restype = st
     lib.negf_plan_n_domains.argtypes = [vp]
     lib.negf_plan_n_domains.restype = i32
     lib.negf_auto_domains.argtypes = [i32, ctypes.POINTER(i32), i32, i32, i32]
@@ -196,6 +203,24 @@ def negf_solve_noalloc(block_sizes, band_n, n_energies, H, sigma_L, sigma_R, sig
 
 def negf_workspace_bytes(plan):
     return int(_lib.negf_workspace_bytes(plan))
+
+
+def negf_band_residual(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, res):
+    return _lib.negf_band_residual(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
+                                   _ptr(G_band), _ptr(res))
+
+
+def negf_autotune(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info, reps=2):
+    """Returns ``(status, best_groups, [ms for 1, 2, 4, 8 groups])``."""
+    best = ctypes.c_int32(0)
+    ms = (ctypes.c_double * 4)()
+    st = _lib.negf_autotune(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
+                            _ptr(G_band), _ptr(G_1N), _ptr(info), int(reps), ctypes.byref(best), ms)
+    return st, int(best.value), list(ms)
+
+
+def negf_plan_groups(plan):
+    return int(_lib.negf_plan_groups(plan))
 
 
 def negf_plan_n_domains(plan):
@@ -392,6 +417,38 @@ class Plan:
         if sync:
             self.sync()
         return Gb, G1
+
+    def autotune(self, H, sigma_L, sigma_R, E, out_band=None, out_g1n=None, reps=2):
+        """Times the solve schedule with 1, 2, 4, 8 energy groups on these
+        inputs and keeps the fastest (negf_autotune).  Returns
+        ``(best_groups, {groups: ms})``."""
+        torch = self.torch
+        nE = self.n_energies
+        b0, bN = self.sizes[0], self.sizes[-1]
+        Gb = out_band if out_band is not None else torch.empty(nE, self.band_elems, dtype=torch.complex128,
+                                                               device="cuda")
+        G1 = out_g1n if out_g1n is not None else torch.empty(nE, b0, bN, dtype=torch.complex128, device="cuda")
+        sigma_L, sigma_R, stride = self._sigmas(sigma_L, sigma_R)
+        self._enter()
+        st, best, ms = negf_autotune(self.handle, H, sigma_L, sigma_R, stride, E, Gb, G1, self.info, reps)
+        self._leave()
+        self._check(st, "negf_autotune")
+        self.sync()
+        return best, {g: t for g, t in zip((1, 2, 4, 8), ms) if t >= 0}
+
+    def band_residual(self, H, sigma_L, sigma_R, E, G_band, sync=True):
+        """Per-energy ``sqrt(sum_i ||(M G)_ii - I||_F^2 / sum_i b_i)`` of a band
+        (negf_band_residual)."""
+        torch = self.torch
+        res = torch.empty(self.n_energies, dtype=torch.float64, device="cuda")
+        sigma_L, sigma_R, stride = self._sigmas(sigma_L, sigma_R)
+        self._enter()
+        st = negf_band_residual(self.handle, H, sigma_L, sigma_R, stride, E, G_band, res)
+        self._leave()
+        self._check(st, "negf_band_residual")
+        if sync:
+            self.sync()
+        return res
 
     def transmission(self, H, sigma_L, sigma_R, E, out=None, sync=True):
         torch = self.torch

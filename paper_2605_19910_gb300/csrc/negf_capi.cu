@@ -139,6 +139,12 @@ inline negf_status cuda_status(cudaError_t e) {
     if (_e != cudaSuccess) return _e;                        \
   } while (0)
 
+#define NEGF_TRY_STATUS(x)                                   \
+  do {                                                       \
+    cudaError_t _e = (x);                                    \
+    if (_e != cudaSuccess) return cuda_status(_e);           \
+  } while (0)
+
 int64_t sq(int x) { return (int64_t)x * x; }
 
 // ---------------------------------------------------------------------------
@@ -836,29 +842,35 @@ const char* negf_status_string(negf_status s) {
 }
 
 // RGF / DDRGF choice (n_domains = 0).  The batched sweep runs one CTA per
-// block inversion, so a layer step over x independent inversions takes
-// ceil(x / slots) waves (slots: CTAs of the inversion kernel resident on the
-// GPU).  Plain RGF: N layer steps over n_E inversions.  DDRGF with d
-// (D2, D1) pairs: the d sub-domains run concurrently, N/d layer steps over
-// d n_E inversions at about three times the work per step (halo rows and
-// columns, W / V, stitching), then the interface RGF: d steps over n_E
-// inversions of w-layer super-blocks (about w^3 the work).  The cheapest
-// d among 1 and the powers of two that leave pairs of at least 4w layers.
+// block inversion; a layer step over x independent block problems costs
+//     step(x; lat, thr) = max(lat, thr * x / slots)
+// in units of one latency-bound plain-RGF layer step (slots: inversion CTAs
+// resident on the GPU for the largest block).  Plain RGF: N steps over n_E
+// problems, step(n_E; 1, 1).  DDRGF with d (D2, D1) pairs: N/d steps over the
+// d n_E concurrent sub-domain problems with about 4.5x the launches of an
+// RGF step (halo rows and columns, W / V, stitching) when latency-bound and
+// about 15x its work when throughput-bound, then the interface RGF: d steps
+// over n_E problems of w-layer super-blocks (w^3 the work).  The constants
+// are fits to GB300 measurements (1024 x 64 and 4096 x 32 chains at 1, 8 and
+// 64 energies, FP64 and mixed).  The cheapest d among 1 and the powers of
+// two that leave pairs of at least 4w layers.
 int32_t negf_auto_domains(int32_t n_blocks, const int32_t* block_sizes, int32_t band_n, int32_t n_energies,
                           int32_t sm_count) {
   if (n_blocks < 1 || !block_sizes || band_n < 3 || n_energies < 1 || sm_count < 1) return 1;
   const int w = (band_n - 1) / 2;
   int bmax = 1;
   for (int i = 0; i < n_blocks; ++i) bmax = std::max(bmax, (int)block_sizes[i]);
+  // inversion CTAs per SM: shared memory (b (b+1) complex + 1 KB) and at most
+  // five 256-thread CTAs (registers); blocks above 119 take a 2-SM cluster
   const double per_cta = (double)bmax * (bmax + 1) * 16.0 + 1024.0;
-  const double slots = bmax <= 119 ? (double)sm_count * std::max(1.0, std::floor(233472.0 / per_cta))
+  const double slots = bmax <= 119 ? (double)sm_count * std::min(5.0, std::max(1.0, std::floor(233472.0 / per_cta)))
                                    : std::max(1.0, std::floor(sm_count / 2.0));
-  auto waves = [&](double x) { return std::ceil(x / slots); };
-  double best = (double)n_blocks * waves(n_energies);
+  auto step = [&](double x, double lat, double thr) { return std::max(lat, thr * x / slots); };
+  double best = (double)n_blocks * step(n_energies, 1.0, 1.0);
   int best_d = 1;
   for (int d = 2; n_blocks / d >= 4 * w; d *= 2) {
-    const double t = (double)n_blocks / d * waves((double)n_energies * d) * 3.0 +
-                     (double)d * waves(n_energies) * w * w * w;
+    const double t = (double)n_blocks / d * step((double)n_energies * d, 4.5, 15.0) +
+                     (double)d * step(n_energies, 1.0, 1.0) * w * w * w;
     if (t < best) { best = t; best_d = d; }
   }
   return best_d;
@@ -1107,14 +1119,17 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
     // leave each batched launch too small to fill the GPU)
     p->groups = std::max(1, std::min(4, p->chunk / 128));
     const char* env = getenv("NEGF_STREAMS");
-    if (env) p->groups = std::max(1, std::min(8, atoi(env)));
+    if (env) p->groups = std::max(1, std::min(NEGF_MAX_GROUPS, atoi(env)));
     p->groups = std::min(p->groups, p->chunk);
-    for (int g = 1; g < p->groups; ++g) {
+    // streams and events for up to NEGF_MAX_GROUPS groups (negf_autotune may
+    // change the count); DDRGF plans keep the count fixed
+    const int gcap = p->n_domains > 1 ? p->groups : std::max(p->groups, std::min(NEGF_MAX_GROUPS, p->chunk));
+    for (int g = 1; g < gcap; ++g) {
       cudaStream_t s2 = nullptr;
       if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
       p->side.push_back(s2);
     }
-    for (int g = 0; g < p->groups; ++g) {
+    for (int g = 0; g < gcap; ++g) {
       cudaEvent_t e2 = nullptr, e3 = nullptr;
       if (cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) { negf_destroy(p); return NEGF_ERR_CUDA; }
       p->ev.push_back(e2);
@@ -1889,6 +1904,104 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
 }  // extern "C"
 
 extern "C" {
+
+// Diagonal blocks of M G - I from the band alone (the check of a band that
+// needs no off-band block): R_i = sum_{|c - i| <= w} M_{i,c} G_{c,i} - I,
+// res[e] = sqrt(sum_i ||R_i||_F^2 / sum_i b_i), FP64 products.
+negf_status negf_band_residual(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                               const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                               const negf_c128* G_band, double* res) {
+  if (!p || !H || !E || !G_band || !res || sigma_E_stride < 0) return NEGF_ERR_ARG;
+  const int N = p->N, w = p->w;
+  int64_t sumb = 0;
+  for (int i = 0; i < N; ++i) sumb += p->b[i];
+  for (int e0 = 0; e0 < p->nE; e0 += p->chunk) {
+    const int ne = std::min(p->chunk, p->nE - e0);
+    Sweep s{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R, sigma_E_stride,
+            (const double2*)E, (double2*)G_band, nullptr, nullptr, e0, ne};
+    double2* R = s.Sslot(0, 0);
+    const int64_t sRr = s.sS(), sG = p->band_elems;
+    for (int i = 0; i < N; ++i) {
+      const int bi = p->b[i];
+      bool first = true;
+      for (int c = std::max(0, i - w); c <= std::min(N - 1, i + w); ++c) {   // R (+)= -H_{i,c} G_{c,i}
+        ZGemm g;
+        g.m = bi; g.n = bi; g.k = p->b[c];
+        g.A = s.Hblk(i, c); g.sA = 0; g.lda = p->b[c];
+        g.B = s.Gb(c, i); g.sB = sG; g.ldb = bi;
+        g.C = R; g.sC = sRr; g.ldc = bi; g.alpha = {-1.0, 0.0};
+        if (!first) { g.C1 = R; g.sC1 = sRr; g.ldc1 = bi; g.beta1 = {1.0, 0.0}; }
+        g.batch = ne;
+        NEGF_TRY_STATUS(s.gemm64(g));
+        first = false;
+      }
+      NEGF_TRY_STATUS(negf::axpy_scalar(R, sRr, s.Gb(i, i), sG, s.E + e0, 1.0, bi, bi, bi, ne, p->stream));
+      for (int side = 0; side < 2; ++side) {   // - Sigma G_ii on the lead layers
+        const double2* sg = side == 0 ? (i == 0 ? s.sigmaL() : nullptr) : (i == N - 1 ? s.sigmaR() : nullptr);
+        if (!sg) continue;
+        ZGemm g;
+        g.m = bi; g.n = bi; g.k = bi;
+        g.A = sg; g.sA = sigma_E_stride; g.lda = bi;
+        g.B = s.Gb(i, i); g.sB = sG; g.ldb = bi;
+        g.C = R; g.sC = sRr; g.ldc = bi; g.alpha = {-1.0, 0.0};
+        g.C1 = R; g.sC1 = sRr; g.ldc1 = bi; g.beta1 = {1.0, 0.0};
+        g.batch = ne;
+        NEGF_TRY_STATUS(s.gemm64(g));
+      }
+      NEGF_TRY_STATUS(negf::add_diag(R, sRr, bi, bi, nullptr, 0, -1.0, ne, p->stream));
+      NEGF_TRY_STATUS(negf::frob2(R, sRr, sq(bi), res + e0, ne, i > 0, p->stream));
+    }
+    NEGF_TRY_STATUS(negf::sqrt_scale(res + e0, ne, 1.0 / (double)sumb, p->stream));
+  }
+  return NEGF_OK;
+}
+
+// Energy-group autotuner: replays the plan's solve schedule with 1, 2, 4, 8
+// groups (those the plan's streams allow), times each with CUDA events on
+// the plan's stream, and keeps the fastest.
+negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L, const negf_c128* sigma_R,
+                          int64_t sigma_E_stride, const negf_c128* E, negf_c128* G_band, negf_c128* G_1N,
+                          int32_t* info, int32_t reps, int32_t* best_groups, double* ms) {
+  if (!p || reps < 1) return NEGF_ERR_ARG;
+  if (p->n_domains > 1 || p->ck_k > 0) return NEGF_ERR_UNSUPPORTED;
+  const int cand[4] = {1, 2, 4, 8};
+  const int gmax = (int)p->side.size() + 1;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return NEGF_ERR_CUDA;
+  const int g0 = p->groups;
+  int best = g0;
+  double best_ms = 1e300;
+  negf_status st = NEGF_OK;
+  for (int k = 0; k < 4; ++k) {
+    if (ms) ms[k] = -1.0;
+    const int G = cand[k];
+    if (G > gmax) continue;
+    p->groups = G;
+    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+    p->have_key = false;
+    st = negf_solve(p, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info);   // capture + warm-up
+    if (st != NEGF_OK) break;
+    if (cudaEventRecord(a, p->stream) != cudaSuccess) { st = NEGF_ERR_CUDA; break; }
+    for (int r = 0; r < reps && st == NEGF_OK; ++r)
+      st = negf_solve(p, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info);
+    if (st != NEGF_OK) break;
+    float t = 0.0f;
+    if (cudaEventRecord(b, p->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+        cudaEventElapsedTime(&t, a, b) != cudaSuccess) { st = NEGF_ERR_CUDA; break; }
+    const double per = (double)t / reps;
+    if (ms) ms[k] = per;
+    if (per < best_ms) { best_ms = per; best = G; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  p->groups = st == NEGF_OK ? best : g0;
+  if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+  p->have_key = false;
+  if (best_groups) *best_groups = p->groups;
+  return st;
+}
+
+int32_t negf_plan_groups(const negf_plan_t* p) { return p ? p->groups : -1; }
 
 negf_status negf_profile_enable(negf_plan_t* p, int32_t on) {
   if (!p) return NEGF_ERR_ARG;

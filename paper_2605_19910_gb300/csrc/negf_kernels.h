@@ -88,4 +88,10 @@ cudaError_t gamma_from_sigma(const double2* sig, int64_t sSig, double2* gam, int
 cudaError_t trace_prod(const double2* P, int64_t sP, const double2* Q, int64_t sQ, int rows, int cols,
                        double* T, int batch, double scale, int accumulate, cudaStream_t st);
 
+// out[e] (+)= sum |A[e]_k|^2 over n contiguous elements.
+cudaError_t frob2(const double2* A, int64_t sA, int64_t n, double* out, int batch, int accumulate, cudaStream_t st);
+
+// out[e] = sqrt(out[e] * scale).
+cudaError_t sqrt_scale(double* out, int n, double scale, cudaStream_t st);
+
 }  // namespace negf

@@ -82,6 +82,34 @@ __global__ void trace_prod_kernel(const double2* __restrict__ P, int64_t sP, con
   }
 }
 
+__global__ void frob2_kernel(const double2* __restrict__ A, int64_t sA, int64_t n, double* __restrict__ out,
+                             int accumulate) {
+  const int e = blockIdx.x;
+  const double2* a = A + (int64_t)e * sA;
+  double acc = 0.0;
+  for (int64_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const double2 v = a[idx];
+    acc = fma(v.x, v.x, acc);
+    acc = fma(v.y, v.y, acc);
+  }
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    acc = lane < nw ? red[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) out[e] = (accumulate ? out[e] : 0.0) + acc;
+  }
+}
+
+__global__ void sqrt_scale_kernel(double* __restrict__ out, int n, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = sqrt(out[i] * scale);
+}
+
 __global__ void set_identity_kernel(double2* __restrict__ D, int64_t sD, int b) {
   const int e = blockIdx.y;
   double2* d = D + (int64_t)e * sD;
@@ -231,6 +259,18 @@ cudaError_t trace_prod(const double2* P, int64_t sP, const double2* Q, int64_t s
                        double* T, int batch, double scale, int accumulate, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   trace_prod_kernel<<<batch, 256, 0, st>>>(P, sP, Q, sQ, rows, cols, T, scale, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t frob2(const double2* A, int64_t sA, int64_t n, double* out, int batch, int accumulate, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  frob2_kernel<<<batch, 256, 0, st>>>(A, sA, n, out, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t sqrt_scale(double* out, int n, double scale, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  sqrt_scale_kernel<<<(n + 255) / 256, 256, 0, st>>>(out, n, scale);
   return cudaGetLastError();
 }
 

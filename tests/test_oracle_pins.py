@@ -439,3 +439,26 @@ def test_paper_flop_count_normaliser():
     # 4 GEMM + 1 LU + 3 GETRS per block at large N: 58.67 b^3 real flops
     f = O.rgf_flops_paper([64] * 1000, 1) / 1000 / 64 ** 3
     assert abs(f - (32 + 8 / 3 + 24)) < 0.2
+
+
+@pytest.mark.parametrize("w", [1, 2])
+def test_band_diag_residual_zero_for_exact_band_and_closed_form_for_a_perturbation(w):
+    # exact band (dense LAPACK inverse): residual at rounding level
+    prob = make_problem(7, b=None, size_range=(2, 6), w=w, n_energies=1, eta=1e-2, seed=90 + w)
+    E = prob.energies[0]
+    M = O.system_blocks(prob, E)
+    ref = O.dense_selected(M, prob.sizes, w)["band"]
+    assert O.band_diag_residual(M, prob.sizes, w, ref) < 1e-13
+    nb = float(sum(prob.sizes))
+    delta = 1e-3
+    # G_kk += delta e_1 e_1^T enters only R_k, through M_kk's first column
+    k = 3
+    band = {key: v.copy() for key, v in ref.items()}
+    band[(k, k)][0, 0] += delta
+    expect = delta * np.linalg.norm(M[(k, k)][:, 0]) / np.sqrt(nb)
+    assert abs(O.band_diag_residual(M, prob.sizes, w, band) - expect) < 1e-6 * expect
+    # G_{k,k+w} += delta e_1 e_1^T enters only R_{k+w}, through M_{k+w,k}
+    band = {key: v.copy() for key, v in ref.items()}
+    band[(k, k + w)][0, 0] += delta
+    expect = delta * np.linalg.norm(M[(k + w, k)][:, 0]) / np.sqrt(nb)
+    assert abs(O.band_diag_residual(M, prob.sizes, w, band) - expect) < 1e-6 * expect
