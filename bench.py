@@ -347,6 +347,9 @@ def run_ours(a, rank, world, local_rank):
     else:
         bound, peak = "alu", FP64_NOMINAL_TFLOPS
         psrc = "nominal GB300 FP64 at the 2070 MHz maximum SM clock (DFMA pipe)"
+    issued = None
+    if name == "zgemm_f64_kernel":   # the 3M form issues 6 m n k of the 8 m n k counted
+        issued = {"achieved": achieved * 0.75, "frac": achieved * 0.75 / peak}
     traffic = None
     uniform_b = prob.sizes[0] if len(set(prob.sizes)) == 1 else None
     t = NCU_TRAFFIC.get((name, uniform_b))
@@ -358,8 +361,11 @@ def run_ours(a, rank, world, local_rank):
     roof = {"kernel": name, "bound": bound,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": psrc,
+            "flop_count": "the method's 8 m n k per complex product / 8 b^3 per inversion",
             "kernel_share": dms / sum(v[0] for v in prof.values()),
             "launches_per_step": int(dln)}
+    if issued:
+        roof["issued_dmma"] = issued
 
     # composite roofline of the mixed path (FP64 inversions at the FP64 rate,
     # block products at the BF16 tensor peak, useful flops only)

@@ -284,23 +284,27 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGem
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
 
-  // Pass 1: power-of-two scales of the rows of A and of the columns of B.
-  for (int r = warp; r < MC; r += TC_THREADS / 32) {
-    int mx = -100000;
-    if (m0 + r < g.m)
-      for (int k = lane; k < g.k; k += 32) {
-        const ulonglong2 v = ld_bits(A + (int64_t)(m0 + r) * g.lda + k);
-        mx = max(mx, max(exp_bound(v.x), exp_bound(v.y)));
-      }
-    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) e_row[r] = mx < -50000 ? ZERO_EXP : mx;
-  }
+  // Pass 1: power-of-two scales of the rows of A (warps 0-3) and of the
+  // columns of B (warps 4-7), concurrently.
   for (int c = tid; c < n_mma; c += TC_THREADS) e_col[c] = -100000;
   __syncthreads();
-  for (int idx = tid; idx < g.k * nt; idx += TC_THREADS) {   // coalesced over columns
-    const int k = idx / nt, c = idx - k * nt;
-    const ulonglong2 v = ld_bits(B + (int64_t)k * g.ldb + n0 + c);
-    atomicMax(&e_col[c], max(exp_bound(v.x), exp_bound(v.y)));
+  if (warp < 4) {
+    for (int r = warp; r < MC; r += 4) {
+      int mx = -100000;
+      if (m0 + r < g.m)
+        for (int k = lane; k < g.k; k += 32) {
+          const ulonglong2 v = ld_bits(A + (int64_t)(m0 + r) * g.lda + k);
+          mx = max(mx, max(exp_bound(v.x), exp_bound(v.y)));
+        }
+      for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (lane == 0) e_row[r] = mx < -50000 ? ZERO_EXP : mx;
+    }
+  } else {
+    for (int idx = tid - 128; idx < g.k * nt; idx += TC_THREADS - 128) {   // coalesced over columns
+      const int k = idx / nt, c = idx - k * nt;
+      const ulonglong2 v = ld_bits(B + (int64_t)k * g.ldb + n0 + c);
+      atomicMax(&e_col[c], max(exp_bound(v.x), exp_bound(v.y)));
+    }
   }
   __syncthreads();
   for (int c = tid; c < n_mma; c += TC_THREADS)
@@ -319,10 +323,12 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGem
   const int nchunks = (g.k + KC - 1) / KC;
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int k0 = ch * KC;
-    // Pass 2a: slices of A, 8 consecutive K per thread item, one 16-byte
-    // core-matrix row per store.  Row r holds [Re A | -Im A], row 64 + r
-    // holds [Im A | Re A].
-    for (int item = tid; item < MC * KG; item += TC_THREADS) {
+    // Pass 2: slices of A and of B^T, 8 consecutive K per thread item, one
+    // 16-byte core-matrix row per store; A and B concurrently on the two
+    // halves of the CTA.
+    const int half_t = TC_THREADS / 2;   // threads 0-127 slice A, 128-255 slice B
+    if (tid < half_t) for (int item = tid; item < MC * KG; item += half_t) {
+      // A: row r holds [Re A | -Im A], row 64 + r holds [Im A | Re A].
       const int r = item / KG, kg = item % KG;
       const int gr = m0 + r;
       const int er = e_row[r];
@@ -362,9 +368,8 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGem
         *reinterpret_cast<uint4*>(base + kmaj_off(MC + r, kg * 8)) = vi;
         *reinterpret_cast<uint4*>(base + kmaj_off(MC + r, KC + kg * 8)) = vr;
       }
-    }
-    // Pass 2b: slices of B^T (K-major): row c holds [Re B(:, c) | Im B(:, c)].
-    for (int item = tid; item < n_mma * KG; item += TC_THREADS) {
+    } else for (int item = tid - half_t; item < n_mma * KG; item += half_t) {
+      // B^T (K-major): row c holds [Re B(:, c) | Im B(:, c)].
       const int c = item % n_mma, kg = item / n_mma;
       const int ec = e_col[c];
       u64 fre[8], fim[8];
