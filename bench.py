@@ -230,29 +230,26 @@ def run_ours(a, rank, world, local_rank):
         tune = {"energy_groups": best, "ms_per_solve_by_groups": {str(k): v for k, v in tms.items()}}
     groups = P.negf_plan_groups(plan.handle)
 
-    for _ in range(a.warmup):
-        step()
-    plan.sync()
-
     # per-kernel profile of one extra step (CUDA events around every launch on
-    # its stream), on a single-stream plan so that concurrent launches of the
-    # energy groups do not inflate each other's durations
-    old_env = os.environ.get("NEGF_STREAMS")
-    os.environ["NEGF_STREAMS"] = "1"
-    pplan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision=a.precision, outputs=outputs, product_bits=bits)
-    if old_env is None:
-        del os.environ["NEGF_STREAMS"]
-    else:
-        os.environ["NEGF_STREAMS"] = old_env
-    P.negf_profile_enable(pplan.handle, 1)
-    pplan.solve(H, sL, sR, E, out_band=Gb, out_g1n=G1, sync=False)
-    prof = P.negf_profile_read(pplan.handle)
-    pplan.sync()
-    pplan.close()
+    # its stream) with the plan set to one energy group, so that concurrent
+    # launches of the groups do not inflate each other's durations (same
+    # chunking, hence the same launch shapes, as the timed plan)
+    P.negf_plan_set_groups(plan.handle, 1)
+    P.negf_profile_enable(plan.handle, 1)
+    for _ in range(2):                  # the second of two profiled steps
+        plan.solve(H, sL, sR, E, out_band=Gb, out_g1n=G1, sync=False)
+        prof = P.negf_profile_read(plan.handle)
+    P.negf_profile_enable(plan.handle, 0)
+    plan.sync()
+    P.negf_plan_set_groups(plan.handle, groups)
     P.negf_profile_enable(plan.handle, 1)
     step()
     launches_per_step = int(sum(v[2] for v in P.negf_profile_read(plan.handle).values()))
     P.negf_profile_enable(plan.handle, 0)
+    plan.sync()
+
+    for _ in range(a.warmup):
+        step()
     plan.sync()
 
     clocks = Clocks(local_rank)

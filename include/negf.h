@@ -238,6 +238,12 @@ negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* s
 /* The plan's current number of energy groups; -1 for NULL. */
 int32_t negf_plan_groups(const negf_plan_t* p);
 
+/* Set the number of energy groups of later calls (1 .. the count the plan's
+ * streams allow: NEGF_MAX_GROUPS, at most one per energy of a chunk; DDRGF
+ * plans keep theirs).  The next call captures a new graph.  NEGF_ERR_ARG for
+ * a count out of range, NEGF_ERR_UNSUPPORTED for changing a DDRGF plan. */
+negf_status negf_plan_set_groups(negf_plan_t* p, int32_t groups);
+
 /* Wait for the plan's stream, then return the first error the device
  * reported since the previous negf_sync (and clear it). */
 negf_status negf_sync(negf_plan_t* p);

@@ -518,3 +518,70 @@ def band_diag_residual(M, sizes, w, band):
             R = R + M[(i, c)] @ band[(c, i)]
         num += float(np.sum(np.abs(R) ** 2))
     return float(np.sqrt(num / float(sum(sizes))))
+
+
+# --------------------------------------------------------------------------
+# Keldysh equation G^< = G^R Sigma^< G^A (Sec. 1; the recursive solver is
+# future work in the paper, Sec. 5)
+# --------------------------------------------------------------------------
+def lesser_dense(M, sizes, w, sigma_less):
+    """The band of ``G^< = G^R Sigma^< G^A`` by its definition: ``G^R = M^{-1}``
+    (dense LAPACK inverse), ``G^A = (G^R)^H`` and a layer-local lesser
+    self-energy ``sigma_less = {layer: block}``.  Returns ``{(a, b): block}``
+    for ``|a - b| <= w``."""
+    N = len(sizes)
+    G = dense_inverse(M, sizes)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
+    S = np.zeros_like(G)
+    for i, blk in sigma_less.items():
+        S[off[i]:off[i + 1], off[i]:off[i + 1]] = blk
+    L = G @ S @ G.conj().T
+    return blocks_from_dense(L, sizes, band_pairs(N, w))
+
+
+def rgf_lesser(M, sizes, sigma_less):
+    """Selected blocks of ``G^<`` for a block tridiagonal ``M`` by recursion
+    over the factorisation of the upward sweep (Alg. 1; Eq.
+    2x2_UDL_factorization applied layer by layer): ``M = U D L`` with
+    ``U_{i,i+1} = M_{i,i+1} t_{i+1}``, ``D = diag(S_i)``,
+    ``L_{i+1,i} = t_{i+1} M_{i+1,i}``, so that ``G^< = L^{-1} D^{-1} U^{-1}
+    Sigma^< U^{-H} D^{-H} L^{-H}``.  With ``Q = U^{-1} Sigma^< U^{-H}``:
+
+    * upward, ``i = N..1``: ``Q_ii = Sigma^<_i + M_{i,i+1} g^<_{i+1}
+      M_{i,i+1}^H``, ``W_i = Q_ii t_i^H``, ``g^<_i = t_i W_i`` (the
+      right-connected lesser function);
+    * downward, ``G^<_11 = g^<_1`` and for ``i = 2..N``, with
+      ``X_{i,i-1} = t_i M_{i,i-1}`` and ``A_i = G^R_{i-1,i} W_i``:
+      ``G^<_{i,i-1} = -A_i^H - X_{i,i-1} G^<_{i-1,i-1}``,
+      ``G^<_{i-1,i} = -(G^<_{i,i-1})^H``,
+      ``G^<_ii = g^<_i - X_{i,i-1} A_i - G^<_{i,i-1} X_{i,i-1}^H``.
+
+    The cross term uses ``(L^{-1} D^{-1} U^{-1})_{i-1,i} = G^R_{i-1,i}`` and
+    the anti-Hermiticity of ``Sigma^<``.  Returns ``(lesser band, retarded
+    band)`` (block tridiagonal only)."""
+    N = len(sizes)
+    r = rgf_selected(M, sizes, 1)
+    GR = r["band"]
+    t = [None] * N
+    S = M[(N - 1, N - 1)].copy()
+    for i in range(N - 1, -1, -1):
+        t[i] = np.linalg.inv(S)
+        if i > 0:
+            S = M[(i - 1, i - 1)] - M[(i - 1, i)] @ t[i] @ M[(i, i - 1)]
+    Wm = [None] * N
+    gl = [None] * N
+    for i in range(N - 1, -1, -1):
+        Q = sigma_less.get(i, np.zeros((sizes[i], sizes[i]), complex)).astype(complex)
+        if i < N - 1:
+            Q = Q + M[(i, i + 1)] @ gl[i + 1] @ M[(i, i + 1)].conj().T
+        Wm[i] = Q @ t[i].conj().T
+        gl[i] = t[i] @ Wm[i]
+    GL = {(0, 0): gl[0]}
+    for i in range(1, N):
+        X = t[i] @ M[(i, i - 1)]
+        A = GR[(i - 1, i)] @ Wm[i]
+        low = -A.conj().T - X @ GL[(i - 1, i - 1)]
+        GL[(i, i - 1)] = low
+        GL[(i - 1, i)] = -low.conj().T
+        GL[(i, i)] = gl[i] - X @ A - low @ X.conj().T
+    return GL, GR

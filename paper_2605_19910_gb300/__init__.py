@@ -50,6 +50,7 @@ PROF_NAMES = ["zinv_gj_kernel", "zgemm_f64_kernel", "zgemm_tc_kernel", "misc"]
 EXPORTED = [
     "negf_plan", "negf_workspace_bytes", "negf_band_offset", "negf_band_elems", "negf_solve",
     "negf_plan_n_domains", "negf_auto_domains", "negf_band_residual", "negf_autotune", "negf_plan_groups",
+    "negf_plan_set_groups",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
 ]
@@ -124,6 +125,8 @@ def _load():
     lib.negf_autotune.restype = st
     lib.negf_plan_groups.argtypes = [vp]
     lib.negf_plan_groups.restype = i32
+    lib.negf_plan_set_groups.argtypes = [vp, i32]
+    lib.negf_plan_set_groups.restype = st
     lib.negf_band_residual.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
     lib.negf_band_residual.restype = st
     lib.negf_plan_n_domains.argtypes = [vp]
@@ -221,6 +224,10 @@ def negf_autotune(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, in
 
 def negf_plan_groups(plan):
     return int(_lib.negf_plan_groups(plan))
+
+
+def negf_plan_set_groups(plan, groups):
+    return _lib.negf_plan_set_groups(plan, int(groups))
 
 
 def negf_plan_n_domains(plan):

@@ -2003,6 +2003,17 @@ negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* s
 
 int32_t negf_plan_groups(const negf_plan_t* p) { return p ? p->groups : -1; }
 
+negf_status negf_plan_set_groups(negf_plan_t* p, int32_t groups) {
+  if (!p || groups < 1 || groups > (int)p->side.size() + 1) return NEGF_ERR_ARG;
+  if (groups != p->groups) {
+    if (p->n_domains > 1) return NEGF_ERR_UNSUPPORTED;   // per-group domain streams are fixed
+    p->groups = groups;
+    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+    p->have_key = false;
+  }
+  return NEGF_OK;
+}
+
 negf_status negf_profile_enable(negf_plan_t* p, int32_t on) {
   if (!p) return NEGF_ERR_ARG;
   p->profiling = on != 0;

@@ -462,3 +462,61 @@ def test_band_diag_residual_zero_for_exact_band_and_closed_form_for_a_perturbati
     band[(k, k + w)][0, 0] += delta
     expect = delta * np.linalg.norm(M[(k + w, k)][:, 0]) / np.sqrt(nb)
     assert abs(O.band_diag_residual(M, prob.sizes, w, band) - expect) < 1e-6 * expect
+
+
+def _random_sigma_less(rng, b):
+    # a layer-local lesser self-energy: i * (positive semidefinite)
+    A = rng.normal(size=(b, b)) + 1j * rng.normal(size=(b, b))
+    return 1j * (A @ A.conj().T) / b
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 8])
+def test_recursive_lesser_equals_dense_keldysh_equation(N):
+    rng = np.random.default_rng(100 + N)
+    prob = make_problem(N, b=None, size_range=(2, 6), w=1, n_energies=1, eta=1e-2, seed=100 + N)
+    M = O.system_blocks(prob, prob.energies[0])
+    sl = {0: _random_sigma_less(rng, prob.sizes[0]), N - 1: _random_sigma_less(rng, prob.sizes[-1])}
+    if N > 2:
+        sl[N // 2] = _random_sigma_less(rng, prob.sizes[N // 2])
+    if N == 1:
+        sl = {0: _random_sigma_less(rng, prob.sizes[0])}
+    ref = O.lesser_dense(M, prob.sizes, 1, sl)
+    got, _ = O.rgf_lesser(M, prob.sizes, sl)
+    for k, v in ref.items():
+        assert np.linalg.norm(got[k] - v) <= 1e-12 * max(1.0, np.linalg.norm(v)), k
+
+
+def test_lesser_equilibrium_fluctuation_dissipation():
+    # all reservoirs at one occupation f (leads and the eta broadening):
+    # Sigma^< = i f (Gamma_L + Gamma_R + 2 eta I)  =>  G^< = -f (G^R - G^A)
+    prob = make_problem(7, b=5, w=1, n_energies=1, eta=3e-2, seed=110)
+    E = prob.energies[0]
+    eta = E.imag
+    rng = np.random.default_rng(111)
+    prob.sigma_L = -0.4j * np.eye(5) + 0.1 * (rng.normal(size=(5, 5)) + 1j * rng.normal(size=(5, 5)))
+    prob.sigma_L = 0.5 * (prob.sigma_L + prob.sigma_L.T)            # any Sigma^R with Gamma >= 0 works
+    prob.sigma_R = -0.7j * np.eye(5)
+    f = 0.37
+    M = O.system_blocks(prob, E)
+    gL, gR = O.gamma(prob.sigma_L), O.gamma(prob.sigma_R)
+    sl = {i: 1j * f * 2 * eta * np.eye(5) for i in range(7)}
+    sl[0] = sl[0] + 1j * f * gL
+    sl[6] = sl[6] + 1j * f * gR
+    GL, GR = O.rgf_lesser(M, prob.sizes, sl)
+    for (a, b), v in GL.items():
+        expect = -f * (GR[(a, b)] - GR[(b, a)].conj().T)
+        assert np.linalg.norm(v - expect) < 1e-12 * np.linalg.norm(expect), (a, b)
+
+
+def test_lesser_is_anti_hermitian_and_single_lead_form():
+    # one lead: G^<_ii = i f G^R_{i1} Gamma_L (G^R_{i1})^H (first block column)
+    prob = make_problem(6, b=4, w=1, n_energies=1, eta=1e-2, seed=112)
+    M = O.system_blocks(prob, prob.energies[0])
+    f = 0.8
+    gL = O.gamma(prob.sigma_L)
+    GL, _ = O.rgf_lesser(M, prob.sizes, {0: 1j * f * gL})
+    G = O.dense_inverse(M, prob.sizes)
+    for i in range(6):
+        assert np.linalg.norm(GL[(i, i)] + GL[(i, i)].conj().T) < 1e-13 * np.linalg.norm(GL[(i, i)])
+        c = G[4 * i:4 * i + 4, 0:4]
+        assert np.linalg.norm(GL[(i, i)] - 1j * f * c @ gL @ c.conj().T) < 1e-12 * np.linalg.norm(GL[(i, i)])
