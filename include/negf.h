@@ -82,7 +82,8 @@ enum {
   NEGF_OUT_BAND = 1,          /* bndiag(G) per energy                          */
   NEGF_OUT_G1N = 2,           /* G_{1N} per energy                             */
   NEGF_OUT_TRANSMISSION = 4,  /* T(E)                                          */
-  NEGF_OUT_GRAD = 8           /* allow negf_grad (keeps the first-row chain)   */
+  NEGF_OUT_GRAD = 8,          /* allow negf_grad (keeps the first-row chain)   */
+  NEGF_OUT_LESSER = 16        /* allow negf_lesser (keeps W_i, g^<_i per layer) */
 };
 
 typedef struct {
@@ -205,6 +206,33 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
                       const negf_c128* E, const double* dL_dT, double* T,
                       negf_c128* dH, negf_c128* dSigma_L, negf_c128* dSigma_R,
                       int32_t* info);
+
+/* Selected blocks of the Keldysh equation G^< = G^R Sigma^< G^A (Sec. 1; the
+ * paper leaves its recursive solution to future work, Sec. 5), block
+ * tridiagonal plans (band_n = 3, n_domains = 1) with NEGF_OUT_LESSER.  Runs
+ * the retarded sweep (written to G_band) and a recursion over the
+ * factorisation M = U D L of its upward pass:
+ *   upward   Q_i = Sigma^<_i + H_{i,i+1} g^<_{i+1} H_{i,i+1}^H,
+ *            W_i = Q_i t_i^H, g^<_i = t_i W_i   (right-connected lesser),
+ *   downward G^<_11 = g^<_1, A_i = G^R_{i-1,i} W_i,
+ *            G^<_{i,i-1} = -X_{i,i-1} G^<_{i-1,i-1} - A_i^H,
+ *            G^<_{i-1,i} = -(G^<_{i,i-1})^H,
+ *            G^<_ii = g^<_i - X_{i,i-1} A_i - G^<_{i,i-1} X_{i,i-1}^H,
+ * X_{i,i-1} = t_i M_{i,i-1}.  The layer-local lesser self-energy is
+ *   Sigma^<_1 = sigma_less_L + s_e I,  Sigma^<_N = sigma_less_R + s_e I,
+ *   Sigma^<_i = s_e I otherwise,
+ * with sigma_less_L / _R (b_1^2 / b_N^2 per energy at sless_stride elements,
+ * 0 broadcasts; nullable) and less_diag = n_energies complex scalars s_e
+ * (nullable; e.g. 2 i eta f for the broadening's own reservoir).
+ * G_band: the retarded band (required, as negf_solve writes it); G_less: the
+ * lesser band, same band packing (required).  Lesser products run in FP64 on
+ * every plan (the retarded sweep in the plan's precision).  Errors as
+ * negf_solve; NEGF_ERR_ARG for a plan without NEGF_OUT_LESSER. */
+negf_status negf_lesser(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                        const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                        const negf_c128* sigma_less_L, const negf_c128* sigma_less_R,
+                        int64_t sless_stride, const negf_c128* less_diag, negf_c128* G_band,
+                        negf_c128* G_less, int32_t* info);
 
 /* A-posteriori accuracy of a band from the band alone (no oracle, no
  * off-band block): the diagonal blocks of M G - I,

@@ -37,6 +37,7 @@ NEGF_OUT_BAND = 1
 NEGF_OUT_G1N = 2
 NEGF_OUT_TRANSMISSION = 4
 NEGF_OUT_GRAD = 8
+NEGF_OUT_LESSER = 16
 
 NEGF_MAX_BLOCK = 160
 
@@ -50,7 +51,7 @@ PROF_NAMES = ["zinv_gj_kernel", "zgemm_f64_kernel", "zgemm_tc_kernel", "misc"]
 EXPORTED = [
     "negf_plan", "negf_workspace_bytes", "negf_band_offset", "negf_band_elems", "negf_solve",
     "negf_plan_n_domains", "negf_auto_domains", "negf_band_residual", "negf_autotune", "negf_plan_groups",
-    "negf_plan_set_groups",
+    "negf_plan_set_groups", "negf_lesser",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
 ]
@@ -127,6 +128,8 @@ def _load():
     lib.negf_plan_groups.restype = i32
     lib.negf_plan_set_groups.argtypes = [vp, i32]
     lib.negf_plan_set_groups.restype = st
+    lib.negf_lesser.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.negf_lesser.restype = st
     lib.negf_band_residual.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
     lib.negf_band_residual.restype = st
     lib.negf_plan_n_domains.argtypes = [vp]
@@ -206,6 +209,13 @@ def negf_solve_noalloc(block_sizes, band_n, n_energies, H, sigma_L, sigma_R, sig
 
 def negf_workspace_bytes(plan):
     return int(_lib.negf_workspace_bytes(plan))
+
+
+def negf_lesser(plan, H, sigma_L, sigma_R, sigma_E_stride, E, sigma_less_L, sigma_less_R, sless_stride,
+                less_diag, G_band, G_less, info):
+    return _lib.negf_lesser(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
+                            _ptr(sigma_less_L), _ptr(sigma_less_R), int(sless_stride), _ptr(less_diag),
+                            _ptr(G_band), _ptr(G_less), _ptr(info))
 
 
 def negf_band_residual(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, res):
@@ -442,6 +452,32 @@ class Plan:
         self._check(st, "negf_autotune")
         self.sync()
         return best, {g: t for g, t in zip((1, 2, 4, 8), ms) if t >= 0}
+
+    def lesser(self, H, sigma_L, sigma_R, E, sigma_less_L=None, sigma_less_R=None, less_diag=None,
+               out_band=None, out_less=None, sync=True):
+        """Selected blocks of ``G^< = G^R Sigma^< G^A`` (negf_lesser).  Returns
+        ``(G_band, G_less)``, both ``[n_E, band_elems]``."""
+        torch = self.torch
+        nE = self.n_energies
+        Gb = out_band if out_band is not None else torch.empty(nE, self.band_elems, dtype=torch.complex128,
+                                                               device="cuda")
+        Gl = out_less if out_less is not None else torch.empty(nE, self.band_elems, dtype=torch.complex128,
+                                                               device="cuda")
+        sigma_L, sigma_R, stride = self._sigmas(sigma_L, sigma_R)
+        sls = 0
+        if sigma_less_L is not None or sigma_less_R is not None:
+            b0, bN = self.sizes[0], self.sizes[-1]
+            zl = sigma_less_L if sigma_less_L is not None else torch.zeros(b0, b0, dtype=torch.complex128, device="cuda")
+            zr = sigma_less_R if sigma_less_R is not None else torch.zeros(bN, bN, dtype=torch.complex128, device="cuda")
+            sigma_less_L, sigma_less_R, sls = self._sigmas(zl, zr)
+        self._enter()
+        st = negf_lesser(self.handle, H, sigma_L, sigma_R, stride, E, sigma_less_L, sigma_less_R, sls,
+                         less_diag, Gb, Gl, self.info)
+        self._leave()
+        self._check(st, "negf_lesser")
+        if sync:
+            self.sync()
+        return Gb, Gl
 
     def band_residual(self, H, sigma_L, sigma_R, E, G_band, sync=True):
         """Per-energy ``sqrt(sum_i ||(M G)_ii - I||_F^2 / sum_i b_i)`` of a band

@@ -72,6 +72,8 @@ struct negf_plan_s {
   double2* G1N_ws = nullptr;    // G_1N when the caller does not keep it
   double* Tdummy = nullptr;
   bool full_row = false;        // R_ws holds the whole first row (adjoint without checkpoints)
+  double2* LW_ws = nullptr;     // Keldysh: W_i = Q_ii t_i^H per layer (t_i layout)
+  double2* LG_ws = nullptr;     // Keldysh: right-connected g^<_i per layer
 
   // Checkpointed adjoint (checkpoint_every = k > 0): the sweep quantities
   // t_i, X_{i,i-1}, Y_{i-1,i}, P_i and the last column live in rings of k + 1
@@ -592,6 +594,123 @@ struct Sweep {
     return cudaSuccess;
   }
 
+  // ---- Keldysh equation G^< = G^R Sigma^< G^A (block tridiagonal) --------
+  // Recursion over the factorisation M = U D L of the upward sweep (the
+  // retarded band, t_i and X_{i,i-1} must be in place):
+  //   upward   Q_i = Sigma^<_i + H_{i,i+1} g^<_{i+1} H_{i,i+1}^H,
+  //            W_i = Q_i t_i^H,  g^<_i = t_i W_i;
+  //   downward G^<_11 = g^<_1;  A_i = G^R_{i-1,i} W_i,
+  //            G^<_{i,i-1} = -X_{i,i-1} G^<_{i-1,i-1} - A_i^H,
+  //            G^<_{i-1,i} = -(G^<_{i,i-1})^H,
+  //            G^<_ii = g^<_i - X_{i,i-1} A_i - G^<_{i,i-1} X_{i,i-1}^H.
+  // Sigma^<_i: the leads' blocks on layers 1 and N plus an optional
+  // per-energy scalar times I on every layer.  FP64 products.
+  double2* LWblk(int i) const { return p->LW_ws + p->t_off[i] * p->chunk + (int64_t)wofs * sq(p->b[i]); }
+  double2* LGblk(int i) const { return p->LG_ws + p->t_off[i] * p->chunk + (int64_t)wofs * sq(p->b[i]); }
+  double2* Lb(double2* base, int a, int bb) const {
+    return base + (int64_t)(e0 - gb_e0) * p->band_elems + p->band_off[(bb - a + p->w) * p->N + a];
+  }
+  cudaError_t lesser_up(const double2* slL, const double2* slR, int64_t sls, const double2* ldiag) {
+    const int N = p->N, C = ne;
+    double2* Q = Sslot(0, 0);
+    double2* T1 = Sslot(0, 1);
+    const double2* sLe = slL ? slL + (sls ? (int64_t)e0 * sls : 0) : nullptr;
+    const double2* sRe = slR ? slR + (sls ? (int64_t)e0 * sls : 0) : nullptr;
+    for (int i = N - 1; i >= 0; --i) {
+      const int bi = p->b[i];
+      if (i == N - 1) {
+        NEGF_TRY(misc([&] { return negf::set_eye(Q, sS(), bi, bi, bi, 0, 0, 0, C, st); }));
+      } else {
+        const int bn = p->b[i + 1];
+        ZGemm g;   // T1 = H_{i,i+1} g^<_{i+1}
+        g.m = bi; g.n = bn; g.k = bn;
+        g.A = Hblk(i, i + 1); g.sA = 0; g.lda = bn;
+        g.B = LGblk(i + 1); g.sB = sq(bn); g.ldb = bn;
+        g.C = T1; g.sC = sS(); g.ldc = bn;
+        g.batch = C;
+        NEGF_TRY(gemm64(g));
+        ZGemm h;   // Q = T1 H_{i,i+1}^H
+        h.m = bi; h.n = bi; h.k = bn;
+        h.A = T1; h.sA = sS(); h.lda = bn;
+        h.B = Hblk(i, i + 1); h.sB = 0; h.ldb = bn; h.opB = negf::OP_C;
+        h.C = Q; h.sC = sS(); h.ldc = bi;
+        h.batch = C;
+        NEGF_TRY(gemm64(h));
+      }
+      if (i == 0 && sLe) NEGF_TRY(misc([&] { return negf::copy2d(sLe, sls, bi, Q, sS(), bi, bi, bi, 1.0, 1, C, st); }));
+      if (i == N - 1 && sRe) NEGF_TRY(misc([&] { return negf::copy2d(sRe, sls, bi, Q, sS(), bi, bi, bi, 1.0, 1, C, st); }));
+      if (ldiag) NEGF_TRY(misc([&] { return negf::add_diag(Q, sS(), bi, bi, ldiag + e0, 1, 1.0, C, st); }));
+      ZGemm g;   // W_i = Q t_i^H
+      g.m = bi; g.n = bi; g.k = bi;
+      g.A = Q; g.sA = sS(); g.lda = bi;
+      g.B = Tblk(i); g.sB = sq(bi); g.ldb = bi; g.opB = negf::OP_C;
+      g.C = LWblk(i); g.sC = sq(bi); g.ldc = bi;
+      g.batch = C;
+      NEGF_TRY(gemm64(g));
+      ZGemm h;   // g^<_i = t_i W_i
+      h.m = bi; h.n = bi; h.k = bi;
+      h.A = Tblk(i); h.sA = sq(bi); h.lda = bi;
+      h.B = LWblk(i); h.sB = sq(bi); h.ldb = bi;
+      h.C = LGblk(i); h.sC = sq(bi); h.ldc = bi;
+      h.batch = C;
+      NEGF_TRY(gemm64(h));
+    }
+    return cudaSuccess;
+  }
+  cudaError_t lesser_down(double2* Gl) {
+    const int N = p->N, C = ne;
+    const int64_t sG = p->band_elems;
+    double2* Am = Sslot(0, 1);
+    NEGF_TRY(misc([&] { return negf::copy_blocks(LGblk(0), sq(p->b[0]), Lb(Gl, 0, 0), sG, sq(p->b[0]), C, st); }));
+    for (int i = 1; i < N; ++i) {
+      const int bi = p->b[i], bc = p->b[i - 1];
+      {
+        ZGemm g;   // A_i = G^R_{i-1,i} W_i
+        g.m = bc; g.n = bi; g.k = bi;
+        g.A = Gb(i - 1, i); g.sA = sG; g.lda = bi;
+        g.B = LWblk(i); g.sB = sq(bi); g.ldb = bi;
+        g.C = Am; g.sC = sS(); g.ldc = bi;
+        g.batch = C;
+        NEGF_TRY(gemm64(g));
+      }
+      double2* low = Lb(Gl, i, i - 1);
+      {
+        ZGemm g;   // G^<_{i,i-1} = -X_{i,i-1} G^<_{i-1,i-1} ...
+        g.m = bi; g.n = bc; g.k = bc;
+        g.A = Xblk(i, i - 1); g.sA = (int64_t)bi * bc; g.lda = bc;
+        g.B = Lb(Gl, i - 1, i - 1); g.sB = sG; g.ldb = bc;
+        g.C = low; g.sC = sG; g.ldc = bc; g.alpha = {-1.0, 0.0};
+        g.batch = C;
+        NEGF_TRY(gemm64(g));
+      }
+      // ... - A_i^H; then G^<_{i-1,i} = -(G^<_{i,i-1})^H
+      NEGF_TRY(misc([&] { return negf::copy2d_ct(Am, sS(), bi, low, sG, bc, bi, bc, -1.0, 1, C, st); }));
+      NEGF_TRY(misc([&] { return negf::copy2d_ct(low, sG, bc, Lb(Gl, i - 1, i), sG, bi, bc, bi, -1.0, 0, C, st); }));
+      double2* dia = Lb(Gl, i, i);
+      {
+        ZGemm g;   // G^<_ii = g^<_i - X_{i,i-1} A_i ...
+        g.m = bi; g.n = bi; g.k = bc;
+        g.A = Xblk(i, i - 1); g.sA = (int64_t)bi * bc; g.lda = bc;
+        g.B = Am; g.sB = sS(); g.ldb = bi;
+        g.C = dia; g.sC = sG; g.ldc = bi; g.alpha = {-1.0, 0.0};
+        g.C1 = LGblk(i); g.sC1 = sq(bi); g.ldc1 = bi; g.beta1 = {1.0, 0.0};
+        g.batch = C;
+        NEGF_TRY(gemm64(g));
+      }
+      {
+        ZGemm g;   // ... - G^<_{i,i-1} X_{i,i-1}^H
+        g.m = bi; g.n = bi; g.k = bc;
+        g.A = low; g.sA = sG; g.lda = bc;
+        g.B = Xblk(i, i - 1); g.sB = (int64_t)bi * bc; g.ldb = bc; g.opB = negf::OP_C;
+        g.C = dia; g.sC = sG; g.ldc = bi; g.alpha = {-1.0, 0.0};
+        g.C1 = dia; g.sC1 = sG; g.ldc1 = bi; g.beta1 = {1.0, 0.0};
+        g.batch = C;
+        NEGF_TRY(gemm64(g));
+      }
+    }
+    return cudaSuccess;
+  }
+
   // ---- checkpointed adjoint (block tridiagonal) ----------------------------
   // Rings of k + 1 layers with fixed per-energy strides (bmax^2 for t, X, Y;
   // bmax * b_N for P / U and the last column); X_{i,i-1} and Y_{i-1,i} sit in
@@ -815,7 +934,8 @@ negf_status validate(const negf_desc* d) {
   if (d->n_domains < 0 || (d->n_domains == 0 && d->domain_first_block)) return NEGF_ERR_ARG;
   if (d->precision != NEGF_FP64 && d->precision != NEGF_MIXED) return NEGF_ERR_ARG;
   if (d->refine_steps < 0 || d->refine_steps > 1) return NEGF_ERR_ARG;
-  if (d->outputs & ~(NEGF_OUT_BAND | NEGF_OUT_G1N | NEGF_OUT_TRANSMISSION | NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
+  if (d->outputs & ~(NEGF_OUT_BAND | NEGF_OUT_G1N | NEGF_OUT_TRANSMISSION | NEGF_OUT_GRAD | NEGF_OUT_LESSER))
+    return NEGF_ERR_ARG;
   if (d->checkpoint_every < 0) return NEGF_ERR_ARG;
   if (d->product_bits != 0 && (d->product_bits < 16 || d->product_bits > 56)) return NEGF_ERR_ARG;
   for (int i = 0; i < d->n_blocks; ++i)
@@ -899,6 +1019,8 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   if (d->n_domains > 1 && (d->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_UNSUPPORTED;
   if (d->precision == NEGF_MIXED && !negf::zgemm_tc_available()) return NEGF_ERR_UNSUPPORTED;
   if ((d->outputs & NEGF_OUT_GRAD) && w != 1) return NEGF_ERR_UNSUPPORTED;
+  if ((d->outputs & NEGF_OUT_LESSER) && (w != 1 || d->n_domains > 1 || (d->checkpoint_every > 0 && (d->outputs & NEGF_OUT_GRAD))))
+    return NEGF_ERR_UNSUPPORTED;
   {
     cudaError_t ie = negf::kernels_init();
     if (ie != cudaSuccess) { g_last_cuda = ie; return NEGF_ERR_CUDA; }
@@ -1049,7 +1171,8 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   // Gamma_L, Gamma_R, P, Q, G_1N, and two more b1 x bN temporaries (gradient)
   p->scr_elems = sq(b0) + sq(bN) + 5 * (int64_t)b0 * bN;
 
-  int64_t per_e = te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot * std::max(1, p->n_domains) +
+  const int64_t lesser_e = (d->outputs & NEGF_OUT_LESSER) ? 2 * te : 0;
+  int64_t per_e = lesser_e + te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot * std::max(1, p->n_domains) +
                   (p->full_row ? re : (int64_t)(w + 1) * b0 * bmax) + 2 * p->p_elems + rf_elems + ck_elems +
                   p->scr_elems + dd_e;
   // chunk energies so that the workspace stays within a budget: 45% of the
@@ -1080,6 +1203,10 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   if (p->ck_k > 0) {
     p->CKS = q; q += (int64_t)p->ck_nseg * p->bmax2 * chunk;
     p->CKP = q; q += (int64_t)p->ck_nseg * p->bmaxN * chunk;
+  }
+  if (lesser_e) {
+    p->LW_ws = q; q += te * chunk;
+    p->LG_ws = q; q += te * chunk;
   }
   p->scratch = q; q += p->scr_elems * chunk;
   p->G1N_ws = p->scratch + (sq(b0) + sq(bN) + 2 * (int64_t)b0 * bN) * chunk;
@@ -1904,6 +2031,36 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
 }  // extern "C"
 
 extern "C" {
+
+// Keldysh equation for the selected blocks (see Sweep::lesser_up / down).
+negf_status negf_lesser(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L, const negf_c128* sigma_R,
+                        int64_t sigma_E_stride, const negf_c128* E, const negf_c128* sigma_less_L,
+                        const negf_c128* sigma_less_R, int64_t sless_stride, const negf_c128* less_diag,
+                        negf_c128* G_band, negf_c128* G_less, int32_t* info) {
+  if (!p || !H || !E || !info || !G_band || !G_less || sigma_E_stride < 0 || sless_stride < 0) return NEGF_ERR_ARG;
+  if (!(p->outputs & NEGF_OUT_LESSER)) return NEGF_ERR_ARG;
+  CallKey key{};
+  key.kind = 4;
+  key.stride = sigma_E_stride * 1000003 + sless_stride;
+  const void* ptrs[] = {H, sigma_L, sigma_R, E, sigma_less_L, sigma_less_R, less_diag, G_band, G_less, info};
+  std::memcpy(key.p, ptrs, sizeof(ptrs));
+  return run_captured(p, key, [&]() -> cudaError_t {
+    NEGF_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * p->nE, p->stream));
+    for (int e0 = 0; e0 < p->nE; e0 += p->chunk) {
+      Sweep base{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
+                 sigma_E_stride, (const double2*)E, (double2*)G_band, nullptr, info,
+                 e0, std::min(p->chunk, p->nE - e0)};
+      NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
+        NEGF_TRY(s.upward(true));
+        NEGF_TRY(s.downward());
+        NEGF_TRY(s.lesser_up((const double2*)sigma_less_L, (const double2*)sigma_less_R, sless_stride,
+                             (const double2*)less_diag));
+        return s.lesser_down((double2*)G_less);
+      }));
+    }
+    return cudaSuccess;
+  });
+}
 
 // Diagonal blocks of M G - I from the band alone (the check of a band that
 // needs no off-band block): R_i = sum_{|c - i| <= w} M_{i,c} G_{c,i} - I,

@@ -64,6 +64,11 @@ cudaError_t copy_blocks(const double2* src, int64_t sSrc, double2* dst, int64_t 
 cudaError_t copy2d(const double2* src, int64_t sSrc, int ldSrc, double2* dst, int64_t sDst, int ldDst,
                    int rows, int cols, double scale, int acc, int batch, cudaStream_t st);
 
+// Conjugate-transposed copy / update: dst[e](r, c) = (acc ? dst[e](r, c) : 0)
+// + scale * conj(src[e](c, r)), dst rows x cols, src cols x rows.
+cudaError_t copy2d_ct(const double2* src, int64_t sSrc, int ldSrc, double2* dst, int64_t sDst, int ldDst,
+                      int rows, int cols, double scale, int acc, int batch, cudaStream_t st);
+
 // dst[e] = zeros(rows x cols) with ones at (i, off + i) (cols_mode) or
 // (off + i, i) (rows mode), i = 0 .. nid-1.
 cudaError_t set_eye(double2* dst, int64_t sDst, int ld, int rows, int cols, int off, int nid, int rows_mode,

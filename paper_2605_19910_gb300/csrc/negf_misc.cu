@@ -121,6 +121,24 @@ __global__ void set_identity_kernel(double2* __restrict__ D, int64_t sD, int b) 
   }
 }
 
+// dst(r, c) = (acc ? dst(r, c) : 0) + scale * conj(src(c, r))
+__global__ void copy2d_ct_kernel(const double2* __restrict__ src, int64_t sSrc, int ldSrc, double2* __restrict__ dst,
+                                 int64_t sDst, int ldDst, int rows, int cols, double scale, int acc) {
+  const int e = blockIdx.y;
+  const double2* sp = src + (int64_t)e * sSrc;
+  double2* dp = dst + (int64_t)e * sDst;
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / cols), c = (int)(idx - (int64_t)r * cols);
+    const double2 v = sp[(int64_t)c * ldSrc + r];
+    double2 o = acc ? dp[(int64_t)r * ldDst + c] : make_double2(0.0, 0.0);
+    o.x = fma(scale, v.x, o.x);
+    o.y = fma(-scale, v.y, o.y);
+    dp[(int64_t)r * ldDst + c] = o;
+  }
+}
+
 __global__ void copy2d_kernel(const double2* __restrict__ src, int64_t sSrc, int ldSrc, double2* __restrict__ dst,
                               int64_t sDst, int ldDst, int rows, int cols, double scale, int acc) {
   const int e = blockIdx.y;
@@ -213,6 +231,14 @@ cudaError_t copy2d(const double2* src, int64_t sSrc, int ldSrc, double2* dst, in
   if (batch <= 0 || rows <= 0 || cols <= 0) return cudaSuccess;
   dim3 grid(grid_x_for((int64_t)rows * cols, 256), batch);
   copy2d_kernel<<<grid, 256, 0, st>>>(src, sSrc, ldSrc, dst, sDst, ldDst, rows, cols, scale, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t copy2d_ct(const double2* src, int64_t sSrc, int ldSrc, double2* dst, int64_t sDst, int ldDst,
+                   int rows, int cols, double scale, int acc, int batch, cudaStream_t st) {
+  if (batch <= 0 || rows <= 0 || cols <= 0) return cudaSuccess;
+  dim3 grid(grid_x_for((int64_t)rows * cols, 256), batch);
+  copy2d_ct_kernel<<<grid, 256, 0, st>>>(src, sSrc, ldSrc, dst, sDst, ldDst, rows, cols, scale, acc);
   return cudaGetLastError();
 }
 
