@@ -74,6 +74,8 @@ def _args():
                          "(default: 48 for the 1024-layer nanowire, 32 otherwise)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plan's default energy-group count instead of negf_autotune's choice")
+    ap.add_argument("--no-lesser-side", action="store_true",
+                    help="skip the side measurement of the Keldysh (G^<) path")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -403,6 +405,44 @@ def run_ours(a, rank, world, local_rank):
         fp64_side = {"ms_per_step": fms, "value": world * nE * N / (fms * 1e-3), "steps": k3,
                      "mixed_speedup": fms / ms}
 
+    # side measurement: the Keldysh path (negf_lesser: retarded sweep + the
+    # lesser recursion, FP64 lesser products) with the left lead occupied and
+    # the right one empty, when a second band output fits comfortably
+    lesser_side = None
+    band_bytes = Gb.numel() * Gb.element_size()
+    if not a.no_lesser_side and prob.w == 1 and band_bytes < 16e9:
+        lplan = P.Plan(prob.sizes, 3, nE, precision=a.precision, outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_LESSER,
+                       product_bits=bits)
+        GL = torch.empty_like(Gb)
+        gamL = 1j * (sL - sL.conj().transpose(-1, -2))
+        slL = 1j * gamL
+        slR = torch.zeros_like(sR)
+        lplan.lesser(H, sL, sR, E, slL, slR, out_band=Gb, out_less=GL, sync=False)
+        lplan.sync()
+        k3 = max(1, min(a.steps, 3))
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for _ in range(k3):
+            lplan.lesser(H, sL, sR, E, slL, slR, out_band=Gb, out_less=GL, sync=False)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        lplan.sync()
+        lplan.close()
+        lms = l0.elapsed_time(l1) / k3
+        lrel = None
+        if rank == 0:
+            from oracle import rgf as O
+            e = nE // 2
+            ref, _ = O.rgf_lesser(O.system_blocks(prob, prob.energies[e]), prob.sizes,
+                                  {0: 1j * O.gamma(prob.sigma_L), N - 1: np.zeros_like(prob.sigma_R)})
+            got = P.unpack_band(GL[e].cpu().numpy(), prob.sizes, 1)
+            num = sum(np.linalg.norm(got[k] - v) ** 2 for k, v in ref.items())
+            den = sum(np.linalg.norm(v) ** 2 for v in ref.values())
+            lrel = float(np.sqrt(num / den))
+        del GL
+        lesser_side = {"ms_per_step": lms, "value": world * nE * N / (lms * 1e-3), "steps": k3,
+                       "outputs": "retarded band + lesser band per energy", "rel_err_vs_oracle_sampled": lrel}
+
     cpu = None
     if pool is not None:
         cpu, _ = oracle_sample(a.workload, a.cpu_energies, pool, cores)
@@ -430,6 +470,7 @@ def run_ours(a, rank, world, local_rank):
             "roofline": roof,
             "composite_roofline": composite,
             "fp64_path": fp64_side,
+            "lesser_path": lesser_side,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
