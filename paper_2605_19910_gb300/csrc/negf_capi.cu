@@ -604,7 +604,8 @@ struct Sweep {
   //            G^<_{i-1,i} = -(G^<_{i,i-1})^H,
   //            G^<_ii = g^<_i - X_{i,i-1} A_i - G^<_{i,i-1} X_{i,i-1}^H.
   // Sigma^<_i: the leads' blocks on layers 1 and N plus an optional
-  // per-energy scalar times I on every layer.  FP64 products.
+  // per-energy scalar times I on every layer.  Products in the plan's
+  // precision (the tensor-core kernel takes B^H operands).
   double2* LWblk(int i) const { return p->LW_ws + p->t_off[i] * p->chunk + (int64_t)wofs * sq(p->b[i]); }
   double2* LGblk(int i) const { return p->LG_ws + p->t_off[i] * p->chunk + (int64_t)wofs * sq(p->b[i]); }
   double2* Lb(double2* base, int a, int bb) const {
@@ -628,14 +629,14 @@ struct Sweep {
         g.B = LGblk(i + 1); g.sB = sq(bn); g.ldb = bn;
         g.C = T1; g.sC = sS(); g.ldc = bn;
         g.batch = C;
-        NEGF_TRY(gemm64(g));
+        NEGF_TRY(gemm(g));
         ZGemm h;   // Q = T1 H_{i,i+1}^H
         h.m = bi; h.n = bi; h.k = bn;
         h.A = T1; h.sA = sS(); h.lda = bn;
         h.B = Hblk(i, i + 1); h.sB = 0; h.ldb = bn; h.opB = negf::OP_C;
         h.C = Q; h.sC = sS(); h.ldc = bi;
         h.batch = C;
-        NEGF_TRY(gemm64(h));
+        NEGF_TRY(gemm(h));
       }
       if (i == 0 && sLe) NEGF_TRY(misc([&] { return negf::copy2d(sLe, sls, bi, Q, sS(), bi, bi, bi, 1.0, 1, C, st); }));
       if (i == N - 1 && sRe) NEGF_TRY(misc([&] { return negf::copy2d(sRe, sls, bi, Q, sS(), bi, bi, bi, 1.0, 1, C, st); }));
@@ -646,14 +647,14 @@ struct Sweep {
       g.B = Tblk(i); g.sB = sq(bi); g.ldb = bi; g.opB = negf::OP_C;
       g.C = LWblk(i); g.sC = sq(bi); g.ldc = bi;
       g.batch = C;
-      NEGF_TRY(gemm64(g));
+      NEGF_TRY(gemm(g));
       ZGemm h;   // g^<_i = t_i W_i
       h.m = bi; h.n = bi; h.k = bi;
       h.A = Tblk(i); h.sA = sq(bi); h.lda = bi;
       h.B = LWblk(i); h.sB = sq(bi); h.ldb = bi;
       h.C = LGblk(i); h.sC = sq(bi); h.ldc = bi;
       h.batch = C;
-      NEGF_TRY(gemm64(h));
+      NEGF_TRY(gemm(h));
     }
     return cudaSuccess;
   }
@@ -671,7 +672,7 @@ struct Sweep {
         g.B = LWblk(i); g.sB = sq(bi); g.ldb = bi;
         g.C = Am; g.sC = sS(); g.ldc = bi;
         g.batch = C;
-        NEGF_TRY(gemm64(g));
+        NEGF_TRY(gemm(g));
       }
       double2* low = Lb(Gl, i, i - 1);
       {
@@ -681,7 +682,7 @@ struct Sweep {
         g.B = Lb(Gl, i - 1, i - 1); g.sB = sG; g.ldb = bc;
         g.C = low; g.sC = sG; g.ldc = bc; g.alpha = {-1.0, 0.0};
         g.batch = C;
-        NEGF_TRY(gemm64(g));
+        NEGF_TRY(gemm(g));
       }
       // ... - A_i^H; then G^<_{i-1,i} = -(G^<_{i,i-1})^H
       NEGF_TRY(misc([&] { return negf::copy2d_ct(Am, sS(), bi, low, sG, bc, bi, bc, -1.0, 1, C, st); }));
@@ -695,7 +696,7 @@ struct Sweep {
         g.C = dia; g.sC = sG; g.ldc = bi; g.alpha = {-1.0, 0.0};
         g.C1 = LGblk(i); g.sC1 = sq(bi); g.ldc1 = bi; g.beta1 = {1.0, 0.0};
         g.batch = C;
-        NEGF_TRY(gemm64(g));
+        NEGF_TRY(gemm(g));
       }
       {
         ZGemm g;   // ... - G^<_{i,i-1} X_{i,i-1}^H
@@ -705,7 +706,7 @@ struct Sweep {
         g.C = dia; g.sC = sG; g.ldc = bi; g.alpha = {-1.0, 0.0};
         g.C1 = dia; g.sC1 = sG; g.ldc1 = bi; g.beta1 = {1.0, 0.0};
         g.batch = C;
-        NEGF_TRY(gemm64(g));
+        NEGF_TRY(gemm(g));
       }
     }
     return cudaSuccess;

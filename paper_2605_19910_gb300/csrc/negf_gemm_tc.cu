@@ -191,6 +191,12 @@ __device__ __forceinline__ ulonglong2 ld_bits(const double2* p) {
   return *reinterpret_cast<const ulonglong2*>(p);
 }
 
+// element offset of op(B)(k, c): B[k][c], or B[c][k] (to be conjugated) for B^H
+template <bool BC>
+__device__ __forceinline__ int64_t opb_off(const ZGemm& g, int k, int c) {
+  return BC ? (int64_t)c * g.ldb + k : (int64_t)k * g.ldb + c;
+}
+
 // tcgen05 shared-memory matrix descriptor: start, LBO (K), SBO (M/N), version 1, no swizzle.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   uint64_t d = 0;
@@ -231,6 +237,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -249,8 +262,8 @@ __device__ __forceinline__ long long acc_int(uint32_t bits) {
 }
 
 // WIDE: products longer than 64-bit level combination allows.  The default
-// build is held to 64 registers so that four CTAs fit an SM.
-template <bool WIDE>
+// build is held to 64 registers so that four CTAs fit an SM.  BC: op(B) = B^H.
+template <bool WIDE, bool BC>
 __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
@@ -301,7 +314,9 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGem
   } else {
     for (int idx = tid - 128; idx < g.k * nt; idx += TC_THREADS - 128) {   // coalesced over columns
       const int k = idx / nt, c = idx - k * nt;
-      const ulonglong2 v = ld_bits(B + (int64_t)k * g.ldb + n0 + c);
+      // op(B)(k, c) at B + k sbk + c sbc (op(B) = B^H: the strides swap; the
+      // sign of the imaginary part does not matter here)
+      const ulonglong2 v = ld_bits(B + opb_off<BC>(g, k, n0 + c));
       atomicMax(&e_col[c], max(exp_bound(v.x), exp_bound(v.y)));
     }
   }
@@ -377,7 +392,10 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGem
       for (int j = 0; j < 8; ++j) {
         const int gk = k0 + kg * 8 + j;
         ulonglong2 v = make_ulonglong2(0ull, 0ull);
-        if (gk < g.k && c < nt) v = ld_bits(B + (int64_t)gk * g.ldb + n0 + c);
+        if (gk < g.k && c < nt) {   // op(B) = B^H: conj by the imaginary sign bit
+          v = ld_bits(B + opb_off<BC>(g, gk, n0 + c));
+          if (BC) v.y ^= 0x8000000000000000ull;
+        }
         fre[j] = fixed_abs(v.x, ec, frac);
         fim[j] = fixed_abs(v.y, ec, frac);
         sre |= (uint32_t)(v.x >> 63) << j;
@@ -447,21 +465,24 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGem
     for (int p0 = 0; p0 < n_mma; p0 += EP) {
       // Epilogue 1: combine the levels of this lane's real row for 16 columns
       const int c0 = p0 + 16 * half;
-      if (!WIDE && c0 < n_mma) {                 // levels combine within 64 bits
-        long long T[16];
+      if (!WIDE && c0 < n_mma) {                 // levels combine within 64 bits, 8 columns at a time
+#pragma unroll 1
+        for (int h8 = 0; h8 < 16; h8 += 8) {
+          long long T[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) T[i] = 0;
-        for (int d = 0; d < L; ++d) {
-          uint32_t v[16];
-          tmem_ld16(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * n_mma + c0), v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          const int sh = s * (L - 1 - d);
+          for (int i = 0; i < 8; ++i) T[i] = 0;
+          for (int d = 0; d < L; ++d) {
+            uint32_t v[8];
+            tmem_ld8(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * n_mma + c0 + h8), v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int sh = s * (L - 1 - d);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) T[i] += acc_int(v[i]) << sh;
+            for (int i = 0; i < 8; ++i) T[i] += acc_int(v[i]) << sh;
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            stage[R * lds + 16 * half + h8 + i] = i64_scaled_bits(T[i], er + e_col[c0 + h8 + i] - s * (L + 1));
         }
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          stage[R * lds + 16 * half + i] = i64_scaled_bits(T[i], er + e_col[c0 + i] - s * (L + 1));
       } else if (WIDE && c0 < n_mma) {           // long products: 128-bit combination
         __int128 T[16];
 #pragma unroll
@@ -558,7 +579,7 @@ bool zgemm_tc_available() { return true; }
 cudaError_t zgemm_tc(const ZGemm& g, cudaStream_t st) {
   if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.k <= 0) return zgemm_f64(g, st);
-  if (g.opA != OP_N || g.opB != OP_N || g.reduce || g.k > 512 || g.bits > 56 || !is_pm1(g.alpha) ||
+  if (g.opA != OP_N || g.reduce || g.k > 512 || g.bits > 56 || !is_pm1(g.alpha) ||
       (g.C1 && !is_pm1_or_0(g.beta1)) || (g.C2 && !is_pm1_or_0(g.beta2)) ||
       (g.dshift && !is_pm1_or_0(g.gamma)))
     return cudaErrorNotSupported;
@@ -569,8 +590,11 @@ cudaError_t zgemm_tc(const ZGemm& g, cudaStream_t st) {
   if ((int)sm > g_tc_smem_optin) return cudaErrorInvalidValue;
   dim3 grid(tiles_m * tiles_n, g.batch);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  if (cfg.s * (cfg.L - 1) <= 36) zgemm_tc_kernel<false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
-  else zgemm_tc_kernel<true><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  const bool wide = cfg.s * (cfg.L - 1) > 36, bc = g.opB == OP_C;
+  if (!wide && !bc) zgemm_tc_kernel<false, false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  else if (!wide) zgemm_tc_kernel<false, true><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  else if (!bc) zgemm_tc_kernel<true, false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  else zgemm_tc_kernel<true, true><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
   return cudaGetLastError();
 }
 
@@ -583,22 +607,22 @@ cudaError_t kernels_init() {
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, zgemm_tc_kernel<true>);
+  e = cudaFuncGetAttributes(&fa, zgemm_tc_kernel<true, true>);
   if (e != cudaSuccess) return e;
-  int dyn = optin - (int)fa.sharedSizeBytes - 1024;
-  e = cudaFuncSetAttribute(zgemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(zgemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-  if (e != cudaSuccess) return e;
+  const int dyn = optin - (int)fa.sharedSizeBytes - 1024;
   // all of the SM's unified L1 as shared memory: four 51 KB CTAs per SM (the
-  // 64-register build), and the same split the inversion kernel needs, so
+  // 64-register builds), and the same split the inversion kernel needs, so
   // the two co-reside without reconfiguring the SM
-  e = cudaFuncSetAttribute(zgemm_tc_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           (int)cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(zgemm_tc_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           (int)cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
+  auto setup = [&](auto kern) -> cudaError_t {
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (r != cudaSuccess) return r;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+  };
+  if ((e = setup(zgemm_tc_kernel<false, false>)) != cudaSuccess) return e;
+  if ((e = setup(zgemm_tc_kernel<false, true>)) != cudaSuccess) return e;
+  if ((e = setup(zgemm_tc_kernel<true, false>)) != cudaSuccess) return e;
+  if ((e = setup(zgemm_tc_kernel<true, true>)) != cudaSuccess) return e;
   g_tc_smem_optin = dyn;
   return cudaSuccess;
 }
