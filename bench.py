@@ -77,7 +77,7 @@ def _args():
                     help="keep the plan's default energy-group count instead of negf_autotune's choice")
     ap.add_argument("--no-lesser-side", action="store_true",
                     help="skip the side measurement of the Keldysh (G^<) path")
-    ap.add_argument("--copy-streams", type=int, default=4,
+    ap.add_argument("--copy-streams", type=int, default=1,
                     help="streams the end-to-end leg splits the device-to-host copy over")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -47,13 +47,19 @@ namespace {
 
 constexpr int TC_THREADS = 256;             // two warpgroups
 constexpr int MC = 64;                       // complex rows per CTA (M = 128 real)
-constexpr int KC = 16;                       // complex K per chunk
-constexpr int KG = KC / 8;                   // 8-element K groups per chunk and part
-constexpr int KR = 2 * KC;                   // real K per chunk (BF16 elements per row)
 constexpr int CORE = 128;                    // 8 rows x 16 bytes
 constexpr int LBO = CORE;                    // bytes between 16-byte K groups
-constexpr int SBO = (KR / 8) * CORE;         // bytes between 8-row groups
-constexpr int A_SLICE_BYTES = 128 * KR * 2;  // one slice of the A chunk
+
+// K-chunk geometry: KC complex K per chunk (16, or 8 for the long products
+// whose L slices would otherwise fill the shared memory)
+template <int KC_>
+struct Chunk {
+  static constexpr int KC = KC_;
+  static constexpr int KG = KC / 8;                  // 8-element K groups per chunk and part
+  static constexpr int KR = 2 * KC;                  // real K per chunk (BF16 elements per row)
+  static constexpr int SBO = (KR / 8) * CORE;        // bytes between 8-row groups
+  static constexpr int A_SLICE_BYTES = 128 * KR * 2; // one slice of the A chunk
+};
 constexpr long long WAIT_LIMIT = 1ll << 26;  // bounded mbarrier wait
 constexpr int ZERO_EXP = 0;                  // scale exponent of an all-zero row / column
 
@@ -66,8 +72,9 @@ struct TcCfg {
 
 __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+template <class CK>
 __device__ __forceinline__ uint32_t kmaj_off(int row, int kcol) {   // BF16 element
-  return (uint32_t)((row >> 3) * SBO + (kcol >> 3) * LBO + (row & 7) * 16 + (kcol & 7) * 2);
+  return (uint32_t)((row >> 3) * CK::SBO + (kcol >> 3) * LBO + (row & 7) * 16 + (kcol & 7) * 2);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -198,11 +205,12 @@ __device__ __forceinline__ int64_t opb_off(const ZGemm& g, int k, int c) {
 }
 
 // tcgen05 shared-memory matrix descriptor: start, LBO (K), SBO (M/N), version 1, no swizzle.
+template <class CK>
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((SBO >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)((CK::SBO >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
@@ -261,10 +269,12 @@ __device__ __forceinline__ long long acc_int(uint32_t bits) {
   return (long long)__float2int_rn(__uint_as_float(bits));
 }
 
-// WIDE: products longer than 64-bit level combination allows.  The default
-// build is held to 64 registers so that four CTAs fit an SM.  BC: op(B) = B^H.
+// WIDE: products longer than 64-bit level combination allows.  Every build
+// is held to 64 registers so that four CTAs fit an SM.  BC: op(B) = B^H.
 template <bool WIDE, bool BC>
-__global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
+__global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
+  using CK = Chunk<WIDE ? 8 : 16>;
+  constexpr int KC = CK::KC, KG = CK::KG, KR = CK::KR, A_SLICE_BYTES = CK::A_SLICE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base_s;
@@ -377,10 +387,10 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGem
         const uint4 vr = make_uint4(pr[0], pr[1], pr[2], pr[3]);
         const uint4 vi = make_uint4(pi[0], pi[1], pi[2], pi[3]);
         const uint4 vn = make_uint4(pn[0], pn[1], pn[2], pn[3]);
-        *reinterpret_cast<uint4*>(base + kmaj_off(r, kg * 8)) = vr;
-        *reinterpret_cast<uint4*>(base + kmaj_off(r, KC + kg * 8)) = vn;
-        *reinterpret_cast<uint4*>(base + kmaj_off(MC + r, kg * 8)) = vi;
-        *reinterpret_cast<uint4*>(base + kmaj_off(MC + r, KC + kg * 8)) = vr;
+        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(r, kg * 8)) = vr;
+        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(r, KC + kg * 8)) = vn;
+        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(MC + r, kg * 8)) = vi;
+        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(MC + r, KC + kg * 8)) = vr;
       }
     } else for (int item = tid - half_t; item < n_mma * KG; item += half_t) {
       // B^T (K-major): row c holds [Re B(:, c) | Im B(:, c)].
@@ -414,8 +424,8 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGem
           pi[h] = (i0 | (((sim >> (2 * h)) & 1u) << 15)) | ((i1 | (((sim >> (2 * h + 1)) & 1u) << 15)) << 16);
         }
         unsigned char* base = sB + (size_t)l * b_slice_bytes;
-        *reinterpret_cast<uint4*>(base + kmaj_off(c, kg * 8)) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
-        *reinterpret_cast<uint4*>(base + kmaj_off(c, KC + kg * 8)) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(c, kg * 8)) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(c, KC + kg * 8)) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -433,8 +443,8 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGem
           for (int l = 0; l <= d; ++l) {
             const int m = d - l;
             const uint32_t acc = (ch > 0 || st > 0 || l > 0) ? 1u : 0u;
-            mma_bf16(tm, make_desc(a0 + (uint32_t)l * A_SLICE_BYTES + koff),
-                     make_desc(b0 + (uint32_t)m * b_slice_bytes + koff), idesc, acc);
+            mma_bf16(tm, make_desc<CK>(a0 + (uint32_t)l * A_SLICE_BYTES + koff),
+                     make_desc<CK>(b0 + (uint32_t)m * b_slice_bytes + koff), idesc, acc);
           }
         }
       }
@@ -483,21 +493,24 @@ __global__ void __launch_bounds__(TC_THREADS, WIDE ? 1 : 4) zgemm_tc_kernel(ZGem
           for (int i = 0; i < 8; ++i)
             stage[R * lds + 16 * half + h8 + i] = i64_scaled_bits(T[i], er + e_col[c0 + h8 + i] - s * (L + 1));
         }
-      } else if (WIDE && c0 < n_mma) {           // long products: 128-bit combination
-        __int128 T[16];
+      } else if (WIDE && c0 < n_mma) {           // long products: 128-bit combination, 8 columns at a time
+#pragma unroll 1
+        for (int h8 = 0; h8 < 16; h8 += 8) {
+          __int128 T[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) T[i] = 0;
-        for (int d = 0; d < L; ++d) {
-          uint32_t v[16];
-          tmem_ld16(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * n_mma + c0), v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          const int sh = s * (L - 1 - d);
+          for (int i = 0; i < 8; ++i) T[i] = 0;
+          for (int d = 0; d < L; ++d) {
+            uint32_t v[8];
+            tmem_ld8(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * n_mma + c0 + h8), v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int sh = s * (L - 1 - d);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) T[i] += (__int128)acc_int(v[i]) << sh;
+            for (int i = 0; i < 8; ++i) T[i] += (__int128)acc_int(v[i]) << sh;
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            stage[R * lds + 16 * half + h8 + i] = i128_scaled_bits(T[i], er + e_col[c0 + h8 + i] - s * (L + 1));
         }
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          stage[R * lds + 16 * half + i] = i128_scaled_bits(T[i], er + e_col[c0 + i] - s * (L + 1));
       }
       __syncthreads();
       // Epilogue 2: alpha = +-1, + beta1 C1 + beta2 C2 + gamma dshift I (all +-1), FP64 store.
@@ -566,8 +579,11 @@ TcCfg tc_config(int n, int k, int bits) {
   return c;
 }
 
+bool tc_wide(const TcCfg& c) { return c.s * (c.L - 1) > 36; }
+
 size_t tc_smem_bytes(const TcCfg& c) {
-  size_t op = (size_t)c.L * A_SLICE_BYTES + (size_t)c.L * c.n_mma * KR * 2;
+  const int kr = tc_wide(c) ? Chunk<8>::KR : Chunk<16>::KR;
+  size_t op = (size_t)c.L * 128 * kr * 2 + (size_t)c.L * c.n_mma * kr * 2;
   size_t st = (size_t)128 * (32 + 1) * 8;
   return op > st ? op : st;
 }
@@ -590,7 +606,7 @@ cudaError_t zgemm_tc(const ZGemm& g, cudaStream_t st) {
   if ((int)sm > g_tc_smem_optin) return cudaErrorInvalidValue;
   dim3 grid(tiles_m * tiles_n, g.batch);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  const bool wide = cfg.s * (cfg.L - 1) > 36, bc = g.opB == OP_C;
+  const bool wide = tc_wide(cfg), bc = g.opB == OP_C;
   if (!wide && !bc) zgemm_tc_kernel<false, false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
   else if (!wide) zgemm_tc_kernel<false, true><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
   else if (!bc) zgemm_tc_kernel<true, false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
