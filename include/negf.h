@@ -225,9 +225,9 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
  * 0 broadcasts; nullable) and less_diag = n_energies complex scalars s_e
  * (nullable; e.g. 2 i eta f for the broadening's own reservoir).
  * G_band: the retarded band (required, as negf_solve writes it); G_less: the
- * lesser band, same band packing (required).  Lesser products run in FP64 on
- * every plan (the retarded sweep in the plan's precision).  Errors as
- * negf_solve; NEGF_ERR_ARG for a plan without NEGF_OUT_LESSER. */
+ * lesser band, same band packing (required).  All products in the plan's
+ * precision.  Errors as negf_solve; NEGF_ERR_ARG for a plan without
+ * NEGF_OUT_LESSER. */
 negf_status negf_lesser(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
                         const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                         const negf_c128* sigma_less_L, const negf_c128* sigma_less_R,

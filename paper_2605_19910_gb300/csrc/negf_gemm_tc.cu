@@ -50,8 +50,9 @@ constexpr int MC = 64;                       // complex rows per CTA (M = 128 re
 constexpr int CORE = 128;                    // 8 rows x 16 bytes
 constexpr int LBO = CORE;                    // bytes between 16-byte K groups
 
-// K-chunk geometry: KC complex K per chunk (16, or 8 for the long products
-// whose L slices would otherwise fill the shared memory)
+// K-chunk geometry: KC complex K per chunk.  (Half-size chunks for the long
+// products, to fit more CTAs per SM, measured 3-10 % slower: the extra chunk
+// iterations cost more than the occupancy gained.)
 template <int KC_>
 struct Chunk {
   static constexpr int KC = KC_;
@@ -273,7 +274,7 @@ __device__ __forceinline__ long long acc_int(uint32_t bits) {
 // is held to 64 registers so that four CTAs fit an SM.  BC: op(B) = B^H.
 template <bool WIDE, bool BC>
 __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
-  using CK = Chunk<WIDE ? 8 : 16>;
+  using CK = Chunk<16>;
   constexpr int KC = CK::KC, KG = CK::KG, KR = CK::KR, A_SLICE_BYTES = CK::A_SLICE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
@@ -582,7 +583,7 @@ TcCfg tc_config(int n, int k, int bits) {
 bool tc_wide(const TcCfg& c) { return c.s * (c.L - 1) > 36; }
 
 size_t tc_smem_bytes(const TcCfg& c) {
-  const int kr = tc_wide(c) ? Chunk<8>::KR : Chunk<16>::KR;
+  const int kr = Chunk<16>::KR;
   size_t op = (size_t)c.L * 128 * kr * 2 + (size_t)c.L * c.n_mma * kr * 2;
   size_t st = (size_t)128 * (32 + 1) * 8;
   return op > st ? op : st;
