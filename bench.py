@@ -181,6 +181,30 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# multi-rank host logic (replicas over energies; no collective on the data path)
+# ---------------------------------------------------------------------------
+def rank_energies(energies, rank, world):
+    """Each rank of an N-GPU run solves its own energy grid (weak scaling):
+    rank r shifts the workload's grid by r * 1e-3."""
+    return energies + 1e-3 * rank if world > 1 and rank > 0 else energies
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: the job ends when the last replica does."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_energies, n_blocks, ms):
+    """Whole-job energy-blocks per second over all ranks."""
+    return world * n_energies * n_blocks / (ms * 1e-3)
+
+
 def _overrides(a):
     over = {}
     if a.n_blocks:
@@ -210,8 +234,7 @@ def run_ours(a, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     prob = workload(a.workload, **_overrides(a))
-    if world > 1 and rank > 0:
-        prob.energies = prob.energies + 1e-3 * rank      # each rank its own energy grid
+    prob.energies = rank_energies(prob.energies, rank, world)
     N, nE = prob.n_blocks, len(prob.energies)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
@@ -276,12 +299,8 @@ def run_ours(a, rank, world, local_rank):
         dist.barrier()
     st = plan.sync  # raises on any device-reported error
     st()
-    ms = t_start.elapsed_time(t_end) / a.steps
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * nE * N / (ms * 1e-3)
+    ms = max_over_ranks(t_start.elapsed_time(t_end) / a.steps, dist, dev)
+    value = job_throughput(world, nE, N, ms)
 
     # sampled parity against the oracle (two energies) for the rel-err report
     rel = None
@@ -336,14 +355,10 @@ def run_ours(a, rank, world, local_rank):
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms2 = e0.elapsed_time(e1) / k2
-        if dist:
-            tt = torch.tensor([ms2], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms2 = float(tt.item())
+        ms2 = max_over_ranks(e0.elapsed_time(e1) / k2, dist, dev)
         h2d = sum(x.numel() * x.element_size() for x in (Hh, sLh, sRh, Eh))
         d2h = Gb_h.numel() * Gb_h.element_size() + G1_h.numel() * G1_h.element_size()
-        e2e = {"value": world * nE * N / (ms2 * 1e-3), "unit": UNIT, "ms_per_step": ms2,
+        e2e = {"value": job_throughput(world, nE, N, ms2), "unit": UNIT, "ms_per_step": ms2,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "d2h_copy_streams": ncs}
 
     # roofline of the dominant kernel (from the profiled step)
@@ -426,7 +441,7 @@ def run_ours(a, rank, world, local_rank):
         fplan.sync()
         fplan.close()
         fms = f0.elapsed_time(f1) / k3
-        fp64_side = {"ms_per_step": fms, "value": world * nE * N / (fms * 1e-3), "steps": k3,
+        fp64_side = {"ms_per_step": fms, "value": job_throughput(world, nE, N, fms), "steps": k3,
                      "mixed_speedup": fms / ms}
 
     # side measurement: the Keldysh path (negf_lesser: retarded sweep + the
@@ -464,7 +479,7 @@ def run_ours(a, rank, world, local_rank):
             den = sum(np.linalg.norm(v) ** 2 for v in ref.values())
             lrel = float(np.sqrt(num / den))
         del GL
-        lesser_side = {"ms_per_step": lms, "value": world * nE * N / (lms * 1e-3), "steps": k3,
+        lesser_side = {"ms_per_step": lms, "value": job_throughput(world, nE, N, lms), "steps": k3,
                        "outputs": "retarded band + lesser band per energy", "rel_err_vs_oracle_sampled": lrel}
 
     cpu = None
