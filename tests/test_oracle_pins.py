@@ -520,3 +520,25 @@ def test_lesser_is_anti_hermitian_and_single_lead_form():
         assert np.linalg.norm(GL[(i, i)] + GL[(i, i)].conj().T) < 1e-13 * np.linalg.norm(GL[(i, i)])
         c = G[4 * i:4 * i + 4, 0:4]
         assert np.linalg.norm(GL[(i, i)] - 1j * f * c @ gL @ c.conj().T) < 1e-12 * np.linalg.norm(GL[(i, i)])
+
+
+def _golden_counts():
+    import os
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_op_counts.txt")
+    rows = []
+    for line in open(p):
+        if line.strip() and not line.startswith("#"):
+            rows.append(tuple(int(x) for x in line.split()))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_counts())
+def test_op_counts_at_the_papers_experiment_sizes(row):
+    # the oracle's counters (incremented by the LU / GETRS / GEMM calls it
+    # makes) against the counts the paper prints, at its experiment sizes
+    ell, w, lu, getrs, gemm = row
+    sizes = [1] * ell
+    M = random_band_matrix(sizes, w, seed=2, diag_shift=3.0)
+    ops = O.OpCount()
+    O.rgf_selected(M, sizes, w, ops=ops)
+    assert (ops.lu, ops.getrs, ops.gemm) == (lu, getrs, gemm)
