@@ -137,7 +137,11 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to NEGF_CLOCKS_DIR (default: the system temp dir);
+        # the JSON line carries their summary
+        import tempfile
+        out_dir = os.environ.get("NEGF_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"negf_clocks_rank{index}_{os.getpid()}.csv")
 
     def start(self):
         try:
