@@ -77,6 +77,8 @@ def _args():
                          "(default: 48 for the 1024-layer nanowire, 32 otherwise)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plan's default energy-group count instead of negf_autotune's choice")
+    ap.add_argument("--no-grad-side", action="store_true",
+                    help="skip the side measurement of the adjoint (gradient) path")
     ap.add_argument("--no-lesser-side", action="store_true",
                     help="skip the side measurement of the Keldysh (G^<) path")
     ap.add_argument("--copy-streams", type=int, default=1,
@@ -486,6 +488,31 @@ def run_ours(a, rank, world, local_rank):
         lesser_side = {"ms_per_step": lms, "value": job_throughput(world, nE, N, lms), "steps": k3,
                        "outputs": "retarded band + lesser band per energy", "rel_err_vs_oracle_sampled": lrel}
 
+    # side measurement: the adjoint (negf_grad: T(E) and dT-weighted gradients
+    # with respect to the band of H and to Sigma_L / Sigma_R), full and
+    # checkpointed every ~sqrt(N) layers
+    grad_side = None
+    if not a.no_grad_side and prob.w == 1:
+        grad_side = {}
+        wts = torch.linspace(-1.0, 1.0, nE, dtype=torch.float64, device=dev)
+        for ck in (0, max(1, int(round(N ** 0.5)))):
+            gplan = P.Plan(prob.sizes, 3, nE, precision=a.precision, product_bits=bits,
+                           outputs=P.NEGF_OUT_TRANSMISSION | P.NEGF_OUT_GRAD, checkpoint_every=ck)
+            gplan.grad(H, sL, sR, E, wts)
+            k3 = max(1, min(a.steps, 3))
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(k3):
+                gplan.grad(H, sL, sR, E, wts, sync=False)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            gplan.sync()
+            gws = P.negf_workspace_bytes(gplan.handle) / 1e9
+            gplan.close()
+            gms = g0.elapsed_time(g1) / k3
+            grad_side["checkpoint_every_%d" % ck] = {"ms_per_step": gms, "value": job_throughput(world, nE, N, gms),
+                                                     "workspace_gb": gws, "steps": k3}
+
     cpu = None
     if pool is not None:
         cpu, _ = oracle_sample(a.workload, a.cpu_energies, pool, cores)
@@ -514,6 +541,7 @@ def run_ours(a, rank, world, local_rank):
             "composite_roofline": composite,
             "fp64_path": fp64_side,
             "lesser_path": lesser_side,
+            "grad_path": grad_side,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

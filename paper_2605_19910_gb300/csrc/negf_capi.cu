@@ -72,6 +72,7 @@ struct negf_plan_s {
   double2* G1N_ws = nullptr;    // G_1N when the caller does not keep it
   double* Tdummy = nullptr;
   bool full_row = false;        // R_ws holds the whole first row (adjoint without checkpoints)
+  double2* DH_ws = nullptr;     // adjoint: per-energy products of one band pair (bmax^2 per energy)
   double2* LW_ws = nullptr;     // Keldysh: W_i = Q_ii t_i^H per layer (t_i layout)
   double2* LG_ws = nullptr;     // Keldysh: right-connected g^<_i per layer
 
@@ -1173,7 +1174,8 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   p->scr_elems = sq(b0) + sq(bN) + 5 * (int64_t)b0 * bN;
 
   const int64_t lesser_e = (d->outputs & NEGF_OUT_LESSER) ? 2 * te : 0;
-  int64_t per_e = lesser_e + te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot * std::max(1, p->n_domains) +
+  const int64_t dh_e = grad ? p->bmax2 : 0;
+  int64_t per_e = dh_e + lesser_e + te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot * std::max(1, p->n_domains) +
                   (p->full_row ? re : (int64_t)(w + 1) * b0 * bmax) + 2 * p->p_elems + rf_elems + ck_elems +
                   p->scr_elems + dd_e;
   // chunk energies so that the workspace stays within a budget: 45% of the
@@ -1204,6 +1206,9 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   if (p->ck_k > 0) {
     p->CKS = q; q += (int64_t)p->ck_nseg * p->bmax2 * chunk;
     p->CKP = q; q += (int64_t)p->ck_nseg * p->bmaxN * chunk;
+  }
+  if (dh_e) {
+    p->DH_ws = q; q += dh_e * chunk;
   }
   if (lesser_e) {
     p->LW_ws = q; q += te * chunk;
@@ -1893,18 +1898,23 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
                  sigma_E_stride, (const double2*)E, nullptr, nullptr, info, e0, ne};
       Sweep s = base;   // wofs = 0: the whole chunk, for the energy-reduced products
 
-      // dH_ab (+)= 2 sum_e w_e (G_{b,N} U_a)^H = 2 sum_e w_e U_a^H G_{b,N}^H
+      // dH_ab (+)= 2 sum_e w_e (G_{b,N} U_a)^H: the per-energy products
+      // P_e = G_{b,N} U_a batched over the chunk (plan precision), then their
+      // weighted, conjugate-transposed sum over energies
       auto dh_pair = [&](int a, int bb, const double2* Ua, int64_t sUa, const double2* Lb, int64_t sLb) {
         const int ba = p->b[a], bbs = p->b[bb];
         double2* out = (double2*)dH + p->band_off[(size_t)(bb - a + p->w) * N + a];
         ZGemm g;
-        g.m = ba; g.n = bbs; g.k = bN;
-        g.A = Ua; g.sA = sUa; g.lda = ba; g.opA = negf::OP_C;
-        g.B = Lb; g.sB = sLb; g.ldb = bN; g.opB = negf::OP_C;
-        g.C = out; g.ldc = bbs; g.alpha = {2.0, 0.0};
-        if (!first) { g.C1 = out; g.ldc1 = bbs; g.beta1 = {1.0, 0.0}; }
-        g.weight = dL_dT + e0; g.reduce = 1; g.batch = ne;
-        return s.gemm64(g);
+        g.m = bbs; g.n = ba; g.k = bN;
+        g.A = Lb; g.sA = sLb; g.lda = bN;
+        g.B = Ua; g.sB = sUa; g.ldb = ba;
+        g.C = p->DH_ws; g.sC = p->bmax2; g.ldc = ba;
+        g.batch = ne;
+        NEGF_TRY(s.gemm(g));
+        return s.misc([&] {
+          return negf::reduce_energies(p->DH_ws, p->bmax2, ba, ne, dL_dT + e0, out, bbs, ba, bbs, {2.0, 0.0},
+                                       first ? 0 : 1, 1, p->stream);
+        });
       };
       // per-energy Sigma: the M-path part 2 w_e (G_{i,N} U_i)^H of layer 0 / N-1
       auto sigma_mpath = [&](int side, const double2* Ui, int64_t sUi, const double2* Li, int64_t sLi) {
@@ -1995,18 +2005,22 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
           g.A = s.scr(4); g.sA = s1; g.lda = bN; g.opA = negf::OP_C;
           g.B = V; g.sB = s1; g.ldb = bN;
         }
-        g.alpha = {0.0, -2.0};
-        g.weight = dL_dT + e0;
         g.batch = ne;
-        if (sigma_E_stride == 0) {
-          g.C = (double2*)dS; g.ldc = bs; g.reduce = 1;
-          if (!first) { g.C1 = (double2*)dS; g.ldc1 = bs; g.beta1 = {1.0, 0.0}; }
+        if (sigma_E_stride == 0) {   // per-energy products, then their weighted sum times -2i
+          g.C = p->DH_ws; g.sC = p->bmax2; g.ldc = bs;
+          NEGF_TRY(s.gemm64(g));
+          NEGF_TRY(s.misc([&] {
+            return negf::reduce_energies(p->DH_ws, p->bmax2, bs, ne, dL_dT + e0, (double2*)dS, bs, bs, bs,
+                                         {0.0, -2.0}, first ? 0 : 1, 0, p->stream);
+          }));
         } else {   // per energy, onto the M-path part written above
           double2* out = (double2*)dS + (int64_t)e0 * sigma_E_stride;
+          g.alpha = {0.0, -2.0};
+          g.weight = dL_dT + e0;
           g.C = out; g.sC = sigma_E_stride; g.ldc = bs;
           g.C1 = out; g.sC1 = sigma_E_stride; g.ldc1 = bs; g.beta1 = {1.0, 0.0};
+          NEGF_TRY(s.gemm64(g));
         }
-        NEGF_TRY(s.gemm64(g));
       }
     }
     if (sigma_E_stride == 0) {   // add the M-path parts dH_00 / dH_NN once, after all chunks

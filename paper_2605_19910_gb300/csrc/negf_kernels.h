@@ -93,6 +93,11 @@ cudaError_t gamma_from_sigma(const double2* sig, int64_t sSig, double2* gam, int
 cudaError_t trace_prod(const double2* P, int64_t sP, const double2* Q, int64_t sQ, int rows, int cols,
                        double* T, int batch, double scale, int accumulate, cudaStream_t st);
 
+// dst(r, c) = (acc ? dst(r, c) : 0) + scale * sum_e w[e] S_e(r, c) over nE
+// energies, S_e = src[e] (ct = 0) or src[e]^H (ct = 1); w nullable (= 1).
+cudaError_t reduce_energies(const double2* src, int64_t sSrc, int ldSrc, int nE, const double* w, double2* dst,
+                            int ldDst, int rows, int cols, double2 scale, int acc, int ct, cudaStream_t st);
+
 // out[e] (+)= sum |A[e]_k|^2 over n contiguous elements.
 cudaError_t frob2(const double2* A, int64_t sA, int64_t n, double* out, int batch, int accumulate, cudaStream_t st);
 

@@ -1,6 +1,8 @@
 // Small element-wise kernels of the sweep: assembling the diagonal blocks of
 // M = E I - H - Sigma (Sec. 2), strided block copies, Gamma = i(Sigma -
 // Sigma^H) and the trace reduction of the transmission.
+#include <algorithm>
+
 #include "negf_common.cuh"
 #include "negf_kernels.h"
 
@@ -79,6 +81,33 @@ __global__ void trace_prod_kernel(const double2* __restrict__ P, int64_t sP, con
     acc = lane < nw ? red[lane] : 0.0;
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if (lane == 0) T[e] = (accumulate ? T[e] : 0.0) + scale * acc;
+  }
+}
+
+// dst(r, c) = (acc ? dst(r, c) : 0) + scale * sum_e w[e] * S_e(r, c), with
+// S_e = src[e] (ct = 0) or src[e]^H (ct = 1: element (c, r), conjugated).
+// Threads run along the output's contiguous index; each sums its element
+// over the energies (reads coalesced per energy).
+__global__ void reduce_energies_kernel(const double2* __restrict__ src, int64_t sSrc, int ldSrc, int nE,
+                                       const double* __restrict__ w, double2* __restrict__ dst, int ldDst,
+                                       int rows, int cols, double2 scale, int acc, int ct) {
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / cols), c = (int)(idx - (int64_t)r * cols);
+    const int64_t o = ct ? (int64_t)c * ldSrc + r : (int64_t)r * ldSrc + c;
+    double sx = 0.0, sy = 0.0;
+    for (int e = 0; e < nE; ++e) {
+      const double we = w ? w[e] : 1.0;
+      if (we == 0.0) continue;
+      const double2 v = src[(int64_t)e * sSrc + o];
+      sx = fma(we, v.x, sx);
+      sy = fma(we, ct ? -v.y : v.y, sy);
+    }
+    double2 out = acc ? dst[(int64_t)r * ldDst + c] : make_double2(0.0, 0.0);
+    out.x += scale.x * sx - scale.y * sy;
+    out.y += scale.x * sy + scale.y * sx;
+    dst[(int64_t)r * ldDst + c] = out;
   }
 }
 
@@ -285,6 +314,15 @@ cudaError_t trace_prod(const double2* P, int64_t sP, const double2* Q, int64_t s
                        double* T, int batch, double scale, int accumulate, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   trace_prod_kernel<<<batch, 256, 0, st>>>(P, sP, Q, sQ, rows, cols, T, scale, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_energies(const double2* src, int64_t sSrc, int ldSrc, int nE, const double* w, double2* dst,
+                            int ldDst, int rows, int cols, double2 scale, int acc, int ct, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const int64_t n = (int64_t)rows * cols;
+  reduce_energies_kernel<<<(int)std::min<int64_t>((n + 127) / 128, 4096), 128, 0, st>>>(
+      src, sSrc, ldSrc, nE, w, dst, ldDst, rows, cols, scale, acc, ct);
   return cudaGetLastError();
 }
 
