@@ -186,7 +186,7 @@ struct Sweep {
     return e;
   }
   static double gemm_flops(const ZGemm& g) {
-    return 8.0 * g.m * (double)g.n * g.k * (g.reduce ? g.batch : g.batch);
+    return 8.0 * g.m * (double)g.n * g.k * g.batch;
   }
   cudaError_t gemm(ZGemm g) {
     g.errword = p->d_err;
