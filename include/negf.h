@@ -207,6 +207,20 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
                       negf_c128* dH, negf_c128* dSigma_L, negf_c128* dSigma_R,
                       int32_t* info);
 
+/* negf_solve with the caller's buffers in HOST memory (same arguments and
+ * layouts as negf_solve, every pointer a host pointer): the inputs are
+ * copied to device buffers the plan owns (allocated at the first call, kept
+ * for later ones: band_elems + the self-energies + n_energies x (band_elems
+ * + b_1 b_N) elements), the solve runs as negf_solve, and G_band / G_1N /
+ * info are copied back, all on the plan's stream.  Synchronous: returns when
+ * the outputs are in host memory, with negf_sync's status.  Page-locked host
+ * memory (cudaHostAlloc, torch pin_memory) lets the copies run at the link's
+ * rate; pageable memory works, more slowly.  NEGF_ERR_NOMEM if the device
+ * buffers cannot be allocated. */
+negf_status negf_solve_host(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                            const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                            negf_c128* G_band, negf_c128* G_1N, int32_t* info);
+
 /* Selected blocks of the Keldysh equation G^< = G^R Sigma^< G^A (Sec. 1; the
  * paper leaves its recursive solution to future work, Sec. 5), block
  * tridiagonal plans (band_n = 3, n_domains = 1) with NEGF_OUT_LESSER.  Runs

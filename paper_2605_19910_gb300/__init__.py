@@ -51,7 +51,7 @@ PROF_NAMES = ["zinv_gj_kernel", "zgemm_f64_kernel", "zgemm_tc_kernel", "misc"]
 EXPORTED = [
     "negf_plan", "negf_workspace_bytes", "negf_band_offset", "negf_band_elems", "negf_solve",
     "negf_plan_n_domains", "negf_auto_domains", "negf_band_residual", "negf_autotune", "negf_plan_groups",
-    "negf_plan_set_groups", "negf_lesser",
+    "negf_plan_set_groups", "negf_lesser", "negf_solve_host",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
 ]
@@ -128,6 +128,8 @@ def _load():
     lib.negf_plan_groups.restype = i32
     lib.negf_plan_set_groups.argtypes = [vp, i32]
     lib.negf_plan_set_groups.restype = st
+    lib.negf_solve_host.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.negf_solve_host.restype = st
     lib.negf_lesser.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp]
     lib.negf_lesser.restype = st
     lib.negf_band_residual.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
@@ -209,6 +211,11 @@ def negf_solve_noalloc(block_sizes, band_n, n_energies, H, sigma_L, sigma_R, sig
 
 def negf_workspace_bytes(plan):
     return int(_lib.negf_workspace_bytes(plan))
+
+
+def negf_solve_host(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info):
+    return _lib.negf_solve_host(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
+                                _ptr(G_band), _ptr(G_1N), _ptr(info))
 
 
 def negf_lesser(plan, H, sigma_L, sigma_R, sigma_E_stride, E, sigma_less_L, sigma_less_R, sless_stride,
@@ -434,6 +441,16 @@ class Plan:
         if sync:
             self.sync()
         return Gb, G1
+
+    def solve_host(self, H, sigma_L, sigma_R, E, out_band, out_g1n=None, info=None):
+        """negf_solve_host: every tensor in host memory (page-locked for full
+        speed); returns the device status after the outputs have landed."""
+        if sigma_L.dim() == 3 or sigma_R.dim() == 3:
+            raise ValueError("solve_host takes one Sigma_L / Sigma_R for all energies")
+        info = info if info is not None else self.torch.zeros(self.n_energies, dtype=self.torch.int32).pin_memory()
+        st = negf_solve_host(self.handle, H, sigma_L, sigma_R, 0, E, out_band, out_g1n, info)
+        self._check(st, "negf_solve_host")
+        return info
 
     def autotune(self, H, sigma_L, sigma_R, E, out_band=None, out_g1n=None, reps=2):
         """Times the solve schedule with 1, 2, 4, 8 energy groups on these

@@ -73,6 +73,10 @@ struct negf_plan_s {
   double* Tdummy = nullptr;
   bool full_row = false;        // R_ws holds the whole first row (adjoint without checkpoints)
   double2* DH_ws = nullptr;     // adjoint: per-energy products of one band pair (bmax^2 per energy)
+  // negf_solve_host: device copies of the caller's host inputs / outputs
+  // (allocated at the first call, sized for the sigma stride of that call)
+  char* host_io = nullptr;
+  size_t host_io_bytes = 0;
   double2* LW_ws = nullptr;     // Keldysh: W_i = Q_ii t_i^H per layer (t_i layout)
   double2* LG_ws = nullptr;     // Keldysh: right-connected g^<_i per layer
 
@@ -1315,6 +1319,7 @@ void negf_destroy(negf_plan_t* p) {
   for (auto e5 : p->djoin) cudaEventDestroy(e5);
   cudaFree(p->ws);
   cudaFree(p->d_err);
+  if (p->host_io) cudaFree(p->host_io);
   delete p;
 }
 
@@ -2046,6 +2051,53 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
 }  // extern "C"
 
 extern "C" {
+
+// negf_solve from host memory to host memory: inputs copied to device
+// buffers the plan owns, the captured solve, outputs copied back, all on the
+// plan's stream; returns after the outputs are in host memory (with
+// negf_sync's status).
+negf_status negf_solve_host(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                            const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                            negf_c128* G_band, negf_c128* G_1N, int32_t* info) {
+  if (!p || !H || !E || !info || sigma_E_stride < 0 || (!G_band && !G_1N)) return NEGF_ERR_ARG;
+  const int64_t nE = p->nE, b0 = p->b[0], bN = p->b[p->N - 1];
+  const int64_t nsig_L = sigma_E_stride ? (nE - 1) * sigma_E_stride + b0 * b0 : b0 * b0;
+  const int64_t nsig_R = sigma_E_stride ? (nE - 1) * sigma_E_stride + bN * bN : bN * bN;
+  auto al = [](int64_t elems) { return (size_t)((elems * (int64_t)sizeof(double2) + 255) / 256 * 256); };
+  const size_t oH = 0, oL = oH + al(p->band_elems), oR = oL + al(nsig_L), oE = oR + al(nsig_R),
+               oG = oE + al(nE), o1 = oG + al(nE * p->band_elems), oI = o1 + al(nE * b0 * bN),
+               need = oI + al(nE);
+  if (!p->host_io || p->host_io_bytes < need) {
+    if (p->host_io) cudaFree(p->host_io);
+    p->host_io = nullptr;
+    p->host_io_bytes = 0;
+    cudaError_t e = cudaMalloc((void**)&p->host_io, need);
+    if (e != cudaSuccess) { g_last_cuda = e; cudaGetLastError(); return NEGF_ERR_NOMEM; }
+    p->host_io_bytes = need;
+  }
+  char* d = p->host_io;
+  negf_c128* dH = (negf_c128*)(d + oH);
+  negf_c128* dL = sigma_L ? (negf_c128*)(d + oL) : nullptr;
+  negf_c128* dR = sigma_R ? (negf_c128*)(d + oR) : nullptr;
+  negf_c128* dE = (negf_c128*)(d + oE);
+  negf_c128* dG = G_band ? (negf_c128*)(d + oG) : nullptr;
+  negf_c128* d1 = G_1N ? (negf_c128*)(d + o1) : nullptr;
+  int32_t* dI = (int32_t*)(d + oI);
+  const size_t z = sizeof(negf_c128);
+  cudaStream_t st = p->stream;
+  cudaError_t e = cudaMemcpyAsync(dH, H, (size_t)p->band_elems * z, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && dL) e = cudaMemcpyAsync(dL, sigma_L, (size_t)nsig_L * z, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && dR) e = cudaMemcpyAsync(dR, sigma_R, (size_t)nsig_R * z, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dE, E, (size_t)nE * z, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  negf_status s = negf_solve(p, dH, dL, dR, sigma_E_stride, dE, dG, d1, dI);
+  if (s != NEGF_OK) return s;
+  if (G_band) e = cudaMemcpyAsync(G_band, dG, (size_t)(nE * p->band_elems) * z, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && G_1N) e = cudaMemcpyAsync(G_1N, d1, (size_t)(nE * b0 * bN) * z, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(info, dI, (size_t)nE * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  return negf_sync(p);
+}
 
 // Keldysh equation for the selected blocks (see Sweep::lesser_up / down).
 negf_status negf_lesser(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L, const negf_c128* sigma_R,

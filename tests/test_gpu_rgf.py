@@ -207,3 +207,24 @@ def test_large_blocks_cluster_inversion(P, torch, b):
 def test_nanowire_block_sizes_96_to_160(P, torch):
     prob = make_problem(6, b=None, size_range=(96, 160), w=1, n_energies=2, eta=1e-3, seed=61)
     run_and_compare(P, torch, prob)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_solve_host_matches_device_solve(P, torch, pinned):
+    # negf_solve_host (host buffers in and out) gives the device call's results
+    prob = make_problem(7, b=9, w=1, n_energies=5, eta=1e-3, seed=140)
+    Hp, sL, sR, E = to_dev(prob, torch)
+    plan = P.Plan(prob.sizes, 3, 5)
+    Gb, G1 = plan.solve(Hp, sL, sR, E)
+    host = lambda t: t.cpu().pin_memory() if pinned else t.cpu()
+    Gb_h = host(torch.zeros_like(Gb))
+    G1_h = host(torch.zeros_like(G1))
+    info = plan.solve_host(host(Hp), host(sL), host(sR), host(E), Gb_h, G1_h)
+    assert not info.numpy().any()
+    assert torch.equal(Gb_h, Gb.cpu()) and torch.equal(G1_h, G1.cpu())
+    # a second call reuses the plan's device copies and the captured graph
+    E2 = E.clone() + 0.1
+    plan.solve_host(host(Hp), host(sL), host(sR), host(E2), Gb_h, G1_h)
+    Gb2, _ = plan.solve(Hp, sL, sR, E2)
+    plan.close()
+    assert torch.equal(Gb_h, Gb2.cpu())
