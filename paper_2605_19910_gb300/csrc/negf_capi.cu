@@ -1310,7 +1310,10 @@ int64_t negf_band_elems(const negf_plan_t* p) { return p ? p->band_elems : -1; }
 
 void negf_destroy(negf_plan_t* p) {
   if (!p) return;
-  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->gexec) {
+    cudaStreamSynchronize(p->stream);
+    cudaGraphExecDestroy(p->gexec);
+  }
   for (auto s2 : p->side) cudaStreamDestroy(s2);
   for (auto e2 : p->ev) cudaEventDestroy(e2);
   for (auto e3 : p->stagger) cudaEventDestroy(e3);
@@ -1755,6 +1758,17 @@ cudaError_t for_groups(negf_plan_s* p, Sweep base, F f, bool stagger = true) {
   return cudaSuccess;
 }
 
+// Drop the plan's executable graph.  Its last launch may still be running
+// on the plan's stream, so the stream is drained first.
+void drop_graph(negf_plan_s* p) {
+  if (p->gexec) {
+    cudaStreamSynchronize(p->stream);
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  p->have_key = false;
+}
+
 // Enqueue (or replay) the schedule of one call.  `body` enqueues the work of
 // every energy chunk on p->stream.
 template <class F>
@@ -1777,7 +1791,7 @@ negf_status run_captured(negf_plan_s* p, const CallKey& key, F body) {
     cudaGetLastError();
     return NEGF_ERR_CUDA;
   }
-  if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+  drop_graph(p);
   e = cudaGraphInstantiate(&p->gexec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) { p->gexec = nullptr; p->have_key = false; return NEGF_ERR_CUDA; }
@@ -2201,8 +2215,7 @@ negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* s
     const int G = cand[k];
     if (G > gmax) continue;
     p->groups = G;
-    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
-    p->have_key = false;
+    drop_graph(p);
     st = negf_solve(p, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info);   // capture + warm-up
     if (st != NEGF_OK) break;
     if (cudaEventRecord(a, p->stream) != cudaSuccess) { st = NEGF_ERR_CUDA; break; }
@@ -2219,8 +2232,7 @@ negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* s
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   p->groups = st == NEGF_OK ? best : g0;
-  if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
-  p->have_key = false;
+  drop_graph(p);
   if (best_groups) *best_groups = p->groups;
   return st;
 }
@@ -2232,8 +2244,7 @@ negf_status negf_plan_set_groups(negf_plan_t* p, int32_t groups) {
   if (groups != p->groups) {
     if (p->n_domains > 1) return NEGF_ERR_UNSUPPORTED;   // per-group domain streams are fixed
     p->groups = groups;
-    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
-    p->have_key = false;
+    drop_graph(p);
   }
   return NEGF_OK;
 }
