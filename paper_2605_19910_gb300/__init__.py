@@ -339,6 +339,95 @@ def unpack_band(vec, sizes, w):
     return {(i, j): vec[o:o + sizes[i] * sizes[j]].reshape(sizes[i], sizes[j]) for (i, j), o in off.items()}
 
 
+def fused_sizes(sizes, w):
+    """Super-block sizes of the block tridiagonal form of a block n-diagonal
+    chain (Sec. 2.3, block fusing): super-layer J holds layers
+    [J w, (J + 1) w) (the last one may hold fewer)."""
+    return [int(sum(sizes[j:j + w])) for j in range(0, len(sizes), w)]
+
+
+def _fuse_maps(sizes, w):
+    off, _ = band_layout(sizes, w)
+    fs = fused_sizes(sizes, w)
+    foff, fn = band_layout(fs, 1)
+    start = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
+    fstart = np.concatenate([[0], np.cumsum(fs)]).astype(int)
+    maps = []   # (src offset, rows, cols, fused offset, fused rows, fused cols, row0, col0)
+    for (a, b), o in off.items():
+        J, K = a // w, b // w
+        maps.append((o, sizes[a], sizes[b], foff[(J, K)], fs[J], fs[K],
+                     int(start[a] - fstart[J]), int(start[b] - fstart[K])))
+    return fs, fn, maps
+
+
+def fuse_band(band, sizes, w):
+    """Band-packed blocks of an n-diagonal chain (``band``: [..., band_elems]
+    torch tensor) re-laid out as the band of its fused block tridiagonal
+    form (block copies; zero where the fused form has no original block).
+    Returns ``(fused band [..., fused_elems], fused sizes)``."""
+    torch = __import__("torch")
+    fs, fn, maps = _fuse_maps(sizes, w)
+    lead = band.shape[:-1]
+    out = torch.zeros(*lead, fn, dtype=band.dtype, device=band.device)
+    for o, r, c, fo, fr, fc, r0, c0 in maps:
+        fblk = out[..., fo:fo + fr * fc].view(*lead, fr, fc)
+        fblk[..., r0:r0 + r, c0:c0 + c] = band[..., o:o + r * c].view(*lead, r, c)
+    return out, fs
+
+
+def unfuse_band(fband, sizes, w):
+    """Inverse of :func:`fuse_band` restricted to the original band: the
+    blocks ``(a, b)``, ``|a - b| <= w``, cut out of the fused band."""
+    torch = __import__("torch")
+    fs, fn, maps = _fuse_maps(sizes, w)
+    _, n = band_layout(sizes, w)
+    lead = fband.shape[:-1]
+    out = torch.empty(*lead, n, dtype=fband.dtype, device=fband.device)
+    for o, r, c, fo, fr, fc, r0, c0 in maps:
+        fblk = fband[..., fo:fo + fr * fc].view(*lead, fr, fc)
+        out[..., o:o + r * c].view(*lead, r, c).copy_(fblk[..., r0:r0 + r, c0:c0 + c])
+    return out
+
+
+def lesser_ndiag(sizes, band_n, H, sigma_L, sigma_R, E, sigma_less_L=None, sigma_less_R=None, less_diag=None,
+                 precision="fp64", product_bits=0):
+    """Keldysh ``G^<`` (and ``G^R``) bands of a block n-diagonal chain through
+    its fused block tridiagonal form: the band of ``H`` is re-laid out on
+    super-blocks of w layers, the lead terms are placed in the first and last
+    super-blocks, :meth:`Plan.lesser` runs on the fused chain, and the
+    original band is cut out of both results.  ``H``: band-packed torch CUDA
+    tensor; ``sigma_*``: one matrix each (shared by all energies).  Returns
+    ``(G_band, G_less)`` in the original band packing."""
+    torch = __import__("torch")
+    w = (band_n - 1) // 2
+    if w == 1:
+        plan = Plan(sizes, 3, len(E), precision=precision, outputs=NEGF_OUT_BAND | NEGF_OUT_LESSER,
+                    product_bits=product_bits)
+        try:
+            return plan.lesser(H, sigma_L, sigma_R, E, sigma_less_L, sigma_less_R, less_diag)
+        finally:
+            plan.close()
+    Hf, fs = fuse_band(H, sizes, w)
+    N, Nf = len(sizes), len(fs)
+    rl = sum(sizes[(Nf - 1) * w:N - 1])      # offset of layer N inside the last super-block
+
+    def pad(m, size, at):
+        if m is None:
+            return None
+        out = torch.zeros(size, size, dtype=m.dtype, device=m.device)
+        out[at:at + m.shape[0], at:at + m.shape[1]] = m
+        return out
+    sLf, sRf = pad(sigma_L, fs[0], 0), pad(sigma_R, fs[-1], rl)
+    slLf, slRf = pad(sigma_less_L, fs[0], 0), pad(sigma_less_R, fs[-1], rl)
+    plan = Plan(fs, 3, len(E), precision=precision, outputs=NEGF_OUT_BAND | NEGF_OUT_LESSER,
+                product_bits=product_bits)
+    try:
+        Gbf, Glf = plan.lesser(Hf, sLf, sRf, E, slLf, slRf, less_diag)
+    finally:
+        plan.close()
+    return unfuse_band(Gbf, sizes, w), unfuse_band(Glf, sizes, w)
+
+
 # ---------------------------------------------------------------------------
 # Plan bound to torch tensors
 # ---------------------------------------------------------------------------

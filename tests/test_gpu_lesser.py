@@ -100,7 +100,7 @@ def test_lesser_equilibrium_from_gpu_retarded_band(P):
 
 
 def test_lesser_on_mixed_plan(P):
-    # retarded sweep on the tensor cores, lesser products in FP64
+    # retarded sweep and lesser products on the tensor cores
     rng = np.random.default_rng(127)
     prob = make_problem(10, b=32, w=1, n_energies=3, eta=1e-3, seed=128)
     slL, slR = _sless(rng, 32), _sless(rng, 32)
@@ -133,3 +133,24 @@ def test_lesser_plan_requirements(P):
     with pytest.raises(P.NegfError) as ei:
         P.Plan([4] * 6, 5, 1, outputs=P.NEGF_OUT_LESSER)
     assert ei.value.status == P.NEGF_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("N", [6, 9])
+def test_lesser_pentadiagonal_through_the_fused_chain(P, N):
+    """n = 5: G^R and G^< bands through the fused block tridiagonal chain
+    (lesser_ndiag) against the oracle's dense Keldysh equation."""
+    import torch
+    rng = np.random.default_rng(130 + N)
+    prob = make_problem(N, b=None, size_range=(3, 9), w=2, n_energies=3, eta=1e-3, seed=131 + N)
+    b0, bN = prob.sizes[0], prob.sizes[-1]
+    slL, slR = _sless(rng, b0), _sless(rng, bN)
+    Hp, sL, sR, E = to_dev(prob, torch)
+    Gb, Gl = P.lesser_ndiag(prob.sizes, 5, Hp, sL, sR, E, torch.tensor(slL, device="cuda"),
+                            torch.tensor(slR, device="cuda"))
+    Gb, Gl = Gb.cpu().numpy(), Gl.cpu().numpy()
+    for e in range(3):
+        M = O.system_blocks(prob, prob.energies[e])
+        ref = O.lesser_dense(M, prob.sizes, 2, {0: slL, N - 1: slR})
+        assert band_rel_err(Gl[e], ref, prob.sizes, 2) < FP64_TOL, e
+        refR = O.dense_selected(M, prob.sizes, 2)["band"]
+        assert band_rel_err(Gb[e], refR, prob.sizes, 2) < FP64_TOL, e
