@@ -319,6 +319,11 @@ def run_ours(a, rank, world, local_rank):
             errs.append(float(np.sqrt(num / den)))
         rel = max(errs)
 
+    # a-posteriori check of every energy's band from the band alone:
+    # sqrt(sum_i ||(M G)_ii - I||_F^2 / sum_i b_i) (negf_band_residual)
+    res = plan.band_residual(H, sL, sR, E, Gb).cpu().numpy()
+    band_residual = {"median": float(np.median(res)), "max": float(res.max()), "energies": int(nE)}
+
     # end to end through the public API: pinned host inputs -> device, solve,
     # selected blocks and G_1N back to pinned host memory, every step
     e2e = None
@@ -520,6 +525,7 @@ def run_ours(a, rank, world, local_rank):
             "autotune": tune,
             "effective_tflops_paper_count": flops_step / (ms * 1e-3) / 1e12 * world,
             "rel_err_vs_oracle_sampled": rel,
+            "band_residual": band_residual,
             "roofline": roof,
             "composite_roofline": composite,
             "fp64_path": fp64_side,
