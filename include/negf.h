@@ -130,6 +130,7 @@ typedef struct {
 
 #define NEGF_MAX_BLOCK 160
 #define NEGF_MAX_GROUPS 8   /* energy groups (concurrent streams) per plan */
+#define NEGF_AUTOTUNE_CANDIDATES 6   /* group counts negf_autotune times: 1 2 3 4 6 8 */
 
 typedef struct negf_plan_s negf_plan_t;   /* opaque plan handle */
 
@@ -265,11 +266,11 @@ negf_status negf_band_residual(negf_plan_t* p, const negf_c128* H, const negf_c1
  * groups that run concurrently on forked streams (graph branches), so that
  * one group's tensor-core products overlap another's inversions.  This call
  * replays the plan's negf_solve schedule on the caller's buffers (same
- * arguments as negf_solve) with 1, 2, 4 and 8 groups (at most
+ * arguments as negf_solve) with 1, 2, 3, 4, 6 and 8 groups (at most
  * NEGF_MAX_GROUPS, at most one group per energy of a chunk), `reps` timed
  * repetitions each after one warm-up, and keeps the fastest count for the
- * plan's later calls.  ms (nullable): 4 doubles, the time per solve for each
- * candidate or -1 where skipped.  best_groups (nullable): the kept count.
+ * plan's later calls.  ms (nullable): NEGF_AUTOTUNE_CANDIDATES doubles, the
+ * time per solve for each candidate in that order, or -1 where skipped.  best_groups (nullable): the kept count.
  * Synchronises the plan's stream.  NEGF_ERR_UNSUPPORTED for DDRGF and
  * checkpointed plans (fixed stream sets). */
 negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,

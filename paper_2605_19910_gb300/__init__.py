@@ -57,6 +57,7 @@ EXPORTED = [
 ]
 
 NEGF_NOALLOC_SCRATCH_BYTES = 32 << 20
+AUTOTUNE_GROUPS = (1, 2, 3, 4, 6, 8)   # the candidates of negf_autotune, in its order
 
 
 class NegfError(RuntimeError):
@@ -231,9 +232,9 @@ def negf_band_residual(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, res
 
 
 def negf_autotune(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info, reps=2):
-    """Returns ``(status, best_groups, [ms for 1, 2, 4, 8 groups])``."""
+    """Returns ``(status, best_groups, [ms per candidate of AUTOTUNE_GROUPS])``."""
     best = ctypes.c_int32(0)
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * len(AUTOTUNE_GROUPS))()
     st = _lib.negf_autotune(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
                             _ptr(G_band), _ptr(G_1N), _ptr(info), int(reps), ctypes.byref(best), ms)
     return st, int(best.value), list(ms)
@@ -542,7 +543,7 @@ class Plan:
         return info
 
     def autotune(self, H, sigma_L, sigma_R, E, out_band=None, out_g1n=None, reps=2):
-        """Times the solve schedule with 1, 2, 4, 8 energy groups on these
+        """Times the solve schedule with 1, 2, 3, 4, 6, 8 energy groups on these
         inputs and keeps the fastest (negf_autotune).  Returns
         ``(best_groups, {groups: ms})``."""
         torch = self.torch
@@ -557,7 +558,7 @@ class Plan:
         self._leave()
         self._check(st, "negf_autotune")
         self.sync()
-        return best, {g: t for g, t in zip((1, 2, 4, 8), ms) if t >= 0}
+        return best, {g: t for g, t in zip(AUTOTUNE_GROUPS, ms) if t >= 0}
 
     def lesser(self, H, sigma_L, sigma_R, E, sigma_less_L=None, sigma_less_R=None, less_diag=None,
                out_band=None, out_less=None, sync=True):

@@ -2194,15 +2194,15 @@ negf_status negf_band_residual(negf_plan_t* p, const negf_c128* H, const negf_c1
   return NEGF_OK;
 }
 
-// Energy-group autotuner: replays the plan's solve schedule with 1, 2, 4, 8
-// groups (those the plan's streams allow), times each with CUDA events on
-// the plan's stream, and keeps the fastest.
+// Energy-group autotuner: replays the plan's solve schedule with 1, 2, 3, 4,
+// 6, 8 groups (those the plan's streams allow), times each with CUDA events
+// on the plan's stream, and keeps the fastest.
 negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L, const negf_c128* sigma_R,
                           int64_t sigma_E_stride, const negf_c128* E, negf_c128* G_band, negf_c128* G_1N,
                           int32_t* info, int32_t reps, int32_t* best_groups, double* ms) {
   if (!p || reps < 1) return NEGF_ERR_ARG;
   if (p->n_domains > 1 || p->ck_k > 0) return NEGF_ERR_UNSUPPORTED;
-  const int cand[4] = {1, 2, 4, 8};
+  const int cand[NEGF_AUTOTUNE_CANDIDATES] = {1, 2, 3, 4, 6, 8};
   const int gmax = (int)p->side.size() + 1;
   cudaEvent_t a = nullptr, b = nullptr;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return NEGF_ERR_CUDA;
@@ -2210,7 +2210,7 @@ negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* s
   int best = g0;
   double best_ms = 1e300;
   negf_status st = NEGF_OK;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NEGF_AUTOTUNE_CANDIDATES; ++k) {
     if (ms) ms[k] = -1.0;
     const int G = cand[k];
     if (G > gmax) continue;

@@ -24,7 +24,7 @@ def test_autotune_keeps_a_timed_candidate_and_results_hold(P, precision, tol):
     Hp, sL, sR, E = to_dev(prob, torch)
     plan = P.Plan(prob.sizes, 3, len(prob.energies), precision=precision)
     best, ms = plan.autotune(Hp, sL, sR, E)
-    assert set(ms) == {1, 2, 4, 8} and all(t > 0 for t in ms.values())
+    assert set(ms) == set(P.AUTOTUNE_GROUPS) and all(t > 0 for t in ms.values())
     assert best in ms and ms[best] == min(ms.values())
     assert P.negf_plan_groups(plan.handle) == best
     Gb, _ = plan.solve(Hp, sL, sR, E)
@@ -41,7 +41,7 @@ def test_autotune_skips_counts_above_the_energies(P):
     Hp, sL, sR, E = to_dev(prob, torch)
     plan = P.Plan(prob.sizes, 3, 3)
     best, ms = plan.autotune(Hp, sL, sR, E)
-    assert set(ms) == {1, 2} and best in (1, 2)
+    assert set(ms) == {1, 2, 3} and best in (1, 2, 3)
     plan.close()
 
 
