@@ -1,0 +1,144 @@
+// Plan state of libnegf.so (one TU: included by negf_capi.cu only): the
+// graph key of a call, the plan with its workspace layout, streams, events
+// and profiling records, and the error helpers of the schedule code.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/negf.h"
+#include "negf_common.cuh"
+#include "negf_kernels.h"
+
+using negf::ZGemm;
+
+namespace {
+
+struct CallKey {
+  const void* p[12];
+  int64_t stride;
+  int kind;
+  bool operator==(const CallKey& o) const {
+    return kind == o.kind && stride == o.stride && std::memcmp(p, o.p, sizeof(p)) == 0;
+  }
+};
+
+}  // namespace
+
+struct negf_plan_s {
+  int N = 0, w = 1, nE = 0, n_domains = 1, precision = 0, refine = 0, outputs = 0, ckpt = 0, bits = 0;
+  std::vector<int> b;
+  std::vector<int64_t> band_off;   // (d + w) * N + i -> element offset or -1
+  int64_t band_elems = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int chunk = 0;                   // energies per chunk
+
+  // workspace (one allocation)
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int* d_err = nullptr;
+
+  // per-energy element offsets inside one chunk slab of each region
+  std::vector<int64_t> t_off, x_off, y_off;   // x_off/y_off indexed [i * w + (i - c - 1)]
+  int64_t t_elems = 0, x_elems = 0, y_elems = 0;
+  double2 *T_ws = nullptr, *X_ws = nullptr, *Y_ws = nullptr;
+  double2* S_ws = nullptr;      // (w+1)^2 slots of bmax^2 per energy
+  int64_t s_slot = 0;           // bmax^2
+  double2* R_ws = nullptr;      // first-row chain: full row (grad) or a ring of w+1
+  std::vector<int64_t> r_off;   // per layer offset (per energy) in R_ws
+  int64_t r_elems = 0;
+  double2* P_ws = nullptr;      // grad: suffix products P_i (b_i x b_N)
+  double2* LC_ws = nullptr;     // grad: last column g_i (b_i x b_N)
+  std::vector<int64_t> p_off;
+  int64_t p_elems = 0;
+  double2* RF_ws = nullptr;     // refinement: correction blocks (b_i x b_N)
+  double2* scratch = nullptr;   // transmission: Gamma_L, Gamma_R, P, Q per energy
+  int64_t scr_elems = 0;
+  double2* G1N_ws = nullptr;    // G_1N when the caller does not keep it
+  double* Tdummy = nullptr;
+  bool full_row = false;        // R_ws holds the whole first row (adjoint without checkpoints)
+  double2* DH_ws = nullptr;     // adjoint: per-energy products of one band pair (bmax^2 per energy)
+  // negf_solve_host: device copies of the caller's host inputs / outputs
+  // (allocated at the first call, sized for the sigma stride of that call)
+  char* host_io = nullptr;
+  size_t host_io_bytes = 0;
+  double2* LW_ws = nullptr;     // Keldysh: W_i = Q_ii t_i^H per layer (t_i layout)
+  double2* LG_ws = nullptr;     // Keldysh: right-connected g^<_i per layer
+
+  // Checkpointed adjoint (checkpoint_every = k > 0): the sweep quantities
+  // t_i, X_{i,i-1}, Y_{i-1,i}, P_i and the last column live in rings of k + 1
+  // layers (fixed per-energy strides bmax^2 and bmax * b_N); the Schur
+  // complement S_hi and P_hi at the top layer of every segment of k layers are
+  // kept and the segment is recomputed from them in the reverse pass.
+  int ck_k = 0, ck_nseg = 0;
+  double2* CKS = nullptr;       // ck_nseg slots of bmax^2 per energy
+  double2* CKP = nullptr;       // ck_nseg slots of bmax * b_N per energy
+  int64_t bmax2 = 0, bmaxN = 0;
+
+  // DDRGF (Alg. 2): n_domains (D2, D1) pairs; D2_j = [dom_f[j], dom_l[j]], its
+  // right separator D1_j = [dom_l[j] + 1, dom_l[j] + w].
+  std::vector<int> dom_f, dom_l, Fsz, Lsz, Psz;
+  std::vector<int> dom_of;                       // layer -> domain (-1: separator)
+  std::vector<int> sep_of;                       // layer -> separator (-1: domain)
+  std::vector<int> off_in;                       // layer offset inside F / Lw / separator super-block
+  std::vector<int64_t> fc_off, lc_off, wp_off, wq_off;   // per layer (D2 layers), per energy
+  std::vector<int64_t> tsd_off, tsu_off, tsl_off, rs_off, ts_x_off;  // per separator
+  std::vector<int64_t> mfp_off, mpf_off, mlq_off, mql_off;  // per domain, energy independent
+  int64_t fc_e = 0, lc_e = 0, wp_e = 0, wq_e = 0, tsd_e = 0, tsu_e = 0, rs_e = 0, ts_x_e = 0, msup_e = 0;
+  int Pmax = 0;
+  double2 *FC = nullptr, *FR = nullptr, *LCd = nullptr, *LR = nullptr, *VT = nullptr;
+  double2 *Wp = nullptr, *Wq = nullptr, *Vp = nullptr, *Vq = nullptr, *Zp = nullptr, *Zq = nullptr;
+  double2 *TSd = nullptr, *TSu = nullptr, *TSl = nullptr, *GSd = nullptr, *GSu = nullptr, *GSl = nullptr;
+  double2 *tS = nullptr, *XS = nullptr, *YS = nullptr, *SS = nullptr, *RS = nullptr, *Msup = nullptr;
+  double2* band_ws = nullptr;   // band of one chunk when the caller keeps no band output
+
+  // independent energy groups run on forked streams (graph branches)
+  int groups = 1;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;   // [0] fork, [1..] joins
+  std::vector<cudaEvent_t> stagger;   // group g -> g + 1 start dependency
+  // DDRGF: the sub-domains of one energy group run concurrently, domain j of
+  // group g on dstream[g * n_domains + j] (j = 0 on the group's own stream)
+  std::vector<cudaStream_t> dstream;
+  std::vector<cudaEvent_t> dfork, djoin;
+
+  // optional per-launch timing (negf_profile_enable)
+  bool profiling = false;
+  struct Rec { int kind; double flops; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  double prof_ms[NEGF_PROF_KINDS] = {0};
+  double prof_flops[NEGF_PROF_KINDS] = {0};
+  int64_t prof_launches[NEGF_PROF_KINDS] = {0};
+
+  // CUDA graph of the last call
+  cudaGraphExec_t gexec = nullptr;
+  bool have_key = false;
+  CallKey key{};
+};
+
+namespace {
+
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+inline negf_status cuda_status(cudaError_t e) {
+  if (e != cudaSuccess) g_last_cuda = e;
+  return e == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
+}
+
+#define NEGF_TRY(x)                                          \
+  do {                                                       \
+    cudaError_t _e = (x);                                    \
+    if (_e != cudaSuccess) return _e;                        \
+  } while (0)
+
+#define NEGF_TRY_STATUS(x)                                   \
+  do {                                                       \
+    cudaError_t _e = (x);                                    \
+    if (_e != cudaSuccess) return cuda_status(_e);           \
+  } while (0)
+
+int64_t sq(int x) { return (int64_t)x * x; }
+
+}  // namespace
