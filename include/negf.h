@@ -173,7 +173,8 @@ int64_t negf_band_elems(const negf_plan_t* p);
  *   H:       band-packed H (energy independent), negf_band_elems() elements.
  *   sigma_L: b_1 x b_1 per energy, energy e at sigma_L + e * sigma_E_stride
  *            (stride 0 broadcasts one matrix to all energies); same for sigma_R
- *            (b_N x b_N).  sigma_E_stride is in elements.
+ *            (b_N x b_N).  sigma_E_stride is in elements: 0, or at least
+ *            max(b_1^2, b_N^2) (smaller strides are NEGF_ERR_ARG).
  *   E:       n_energies complex energies (E_r + i eta).
  *   G_band:  n_energies x negf_band_elems() elements (energy-major); may be
  *            NULL if NEGF_OUT_BAND is not requested.

@@ -28,6 +28,15 @@ using negf::ZGemm;
 
 namespace {
 
+// A per-energy self-energy stride must keep the energies' lead blocks apart
+// (0 broadcasts one block to every energy).
+bool bad_sigma_stride(const negf_plan_s* p, int64_t stride) {
+  if (stride < 0) return true;
+  if (stride == 0) return false;
+  const int64_t need = std::max(sq(p->b[0]), sq(p->b[p->N - 1]));
+  return stride < need;
+}
+
 // ---------------------------------------------------------------------------
 // Plan construction
 // ---------------------------------------------------------------------------
@@ -528,7 +537,7 @@ extern "C" {
 negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
                        const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                        negf_c128* G_band, negf_c128* G_1N, int32_t* info) {
-  if (!p || !H || !E || !info || sigma_E_stride < 0) return NEGF_ERR_ARG;
+  if (!p || !H || !E || !info || bad_sigma_stride(p, sigma_E_stride)) return NEGF_ERR_ARG;
   if (!G_band && !G_1N) return NEGF_ERR_ARG;
   // a checkpointed adjoint plan keeps rings of k + 1 layers, not the whole
   // factorisation the band needs
@@ -575,7 +584,7 @@ negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigm
 negf_status negf_transmission(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
                               const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                               double* T, int32_t* info) {
-  if (!p || !H || !E || !info || !T || !sigma_L || !sigma_R || sigma_E_stride < 0) return NEGF_ERR_ARG;
+  if (!p || !H || !E || !info || !T || !sigma_L || !sigma_R || bad_sigma_stride(p, sigma_E_stride)) return NEGF_ERR_ARG;
   CallKey key{};
   key.kind = CALL_TRANS;
   key.stride = sigma_E_stride;
@@ -619,7 +628,8 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
                       const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                       const double* dL_dT, double* T, negf_c128* dH, negf_c128* dSigma_L,
                       negf_c128* dSigma_R, int32_t* info) {
-  if (!p || !H || !E || !info || !dL_dT || !dH || !sigma_L || !sigma_R || sigma_E_stride < 0) return NEGF_ERR_ARG;
+  if (!p || !H || !E || !info || !dL_dT || !dH || !sigma_L || !sigma_R || bad_sigma_stride(p, sigma_E_stride))
+    return NEGF_ERR_ARG;
   if (!(p->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
   CallKey key{};
   key.kind = CALL_GRAD;
@@ -794,7 +804,7 @@ extern "C" {
 negf_status negf_solve_host(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
                             const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                             negf_c128* G_band, negf_c128* G_1N, int32_t* info) {
-  if (!p || !H || !E || !info || sigma_E_stride < 0 || (!G_band && !G_1N)) return NEGF_ERR_ARG;
+  if (!p || !H || !E || !info || bad_sigma_stride(p, sigma_E_stride) || (!G_band && !G_1N)) return NEGF_ERR_ARG;
   const int64_t nE = p->nE, b0 = p->b[0], bN = p->b[p->N - 1];
   const int64_t nsig_L = sigma_E_stride ? (nE - 1) * sigma_E_stride + b0 * b0 : b0 * b0;
   const int64_t nsig_R = sigma_E_stride ? (nE - 1) * sigma_E_stride + bN * bN : bN * bN;
@@ -839,7 +849,9 @@ negf_status negf_lesser(negf_plan_t* p, const negf_c128* H, const negf_c128* sig
                         int64_t sigma_E_stride, const negf_c128* E, const negf_c128* sigma_less_L,
                         const negf_c128* sigma_less_R, int64_t sless_stride, const negf_c128* less_diag,
                         negf_c128* G_band, negf_c128* G_less, int32_t* info) {
-  if (!p || !H || !E || !info || !G_band || !G_less || sigma_E_stride < 0 || sless_stride < 0) return NEGF_ERR_ARG;
+  if (!p || !H || !E || !info || !G_band || !G_less || bad_sigma_stride(p, sigma_E_stride) ||
+      bad_sigma_stride(p, sless_stride))
+    return NEGF_ERR_ARG;
   if (!(p->outputs & NEGF_OUT_LESSER)) return NEGF_ERR_ARG;
   CallKey key{};
   key.kind = 4;
@@ -870,7 +882,7 @@ negf_status negf_lesser(negf_plan_t* p, const negf_c128* H, const negf_c128* sig
 negf_status negf_band_residual(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
                                const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                                const negf_c128* G_band, double* res) {
-  if (!p || !H || !E || !G_band || !res || sigma_E_stride < 0) return NEGF_ERR_ARG;
+  if (!p || !H || !E || !G_band || !res || bad_sigma_stride(p, sigma_E_stride)) return NEGF_ERR_ARG;
   const int N = p->N, w = p->w;
   int64_t sumb = 0;
   for (int i = 0; i < N; ++i) sumb += p->b[i];

@@ -177,6 +177,16 @@ def test_argument_errors(P, torch):
     assert P.negf_solve(plan.handle, None, None, None, 0, None, None, None, None) == P.NEGF_ERR_ARG
     assert P.negf_transmission(plan.handle, None, None, None, 0, None, None, None) == P.NEGF_ERR_ARG
     plan.close()
+    # a per-energy Sigma stride shorter than a lead block is rejected before any launch
+    prob = make_problem(3, b=5, w=1, n_energies=2, eta=1e-2, seed=141)
+    Hp, sL, sR, E = to_dev(prob, torch, per_energy_sigma=True)
+    plan = P.Plan(prob.sizes, 3, 2)
+    out = torch.empty(2, plan.band_elems, dtype=torch.complex128, device="cuda")
+    for bad in (-1, 24):
+        assert P.negf_solve(plan.handle, Hp, sL, sR, bad, E, out, None, plan.info) == P.NEGF_ERR_ARG
+    assert P.negf_solve(plan.handle, Hp, sL, sR, 25, E, out, None, plan.info) == P.NEGF_OK
+    assert P.negf_sync(plan.handle) == P.NEGF_OK
+    plan.close()
 
 
 def test_variable_sizes_many_energies_concurrent_groups(P, torch):
