@@ -141,7 +141,11 @@ typedef struct negf_plan_s negf_plan_t;   /* opaque plan handle */
  * build does not implement.  On success *out owns the workspace. */
 negf_status negf_plan(negf_plan_t** out, const negf_desc* d, void* cuda_stream);
 
-/* Bytes of device workspace the plan holds. */
+/* Bytes of device workspace the plan holds.  negf_plan sizes it to
+ * max(24 GiB, 45 % of the device memory free at plan time) and runs the
+ * energies in chunks that fit; the environment variable NEGF_WORKSPACE_GB
+ * (a positive number, read by negf_plan) caps it instead (at least one
+ * energy per chunk). */
 size_t negf_workspace_bytes(const negf_plan_t* p);
 
 /* The plan's number of DDRGF (D2, D1) pairs (1 = plain RGF); -1 for NULL. */

@@ -297,7 +297,11 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   // need the rest)
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 0; }
-  const double budget_bytes = std::max(24.0 * (1ull << 30), 0.45 * (double)free_b);
+  double budget_bytes = std::max(24.0 * (1ull << 30), 0.45 * (double)free_b);
+  if (const char* cap = getenv("NEGF_WORKSPACE_GB")) {   // caller's cap (energies are chunked to fit)
+    const double gb = atof(cap);
+    if (gb > 0.0) budget_bytes = gb * (double)(1ull << 30);
+  }
   const int64_t budget_elems = (int64_t)(budget_bytes / (double)sizeof(double2));
   int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(p->nE, budget_elems / std::max<int64_t>(per_e, 1)));
   p->chunk = chunk;
