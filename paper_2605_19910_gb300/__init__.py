@@ -61,6 +61,8 @@ AUTOTUNE_GROUPS = (1, 2, 3, 4, 6, 8)   # the candidates of negf_autotune, in its
 
 
 class NegfError(RuntimeError):
+    """A negf_status other than NEGF_OK, with the CUDA error text for NEGF_ERR_CUDA."""
+
     def __init__(self, status, where=""):
         self.status = int(status)
         extra = ""
@@ -70,6 +72,8 @@ class NegfError(RuntimeError):
 
 
 class negf_desc(ctypes.Structure):
+    """The plan descriptor of include/negf.h (same fields, same order)."""
+
     _fields_ = [
         ("n_blocks", ctypes.c_int32),
         ("block_sizes", ctypes.POINTER(ctypes.c_int32)),
@@ -146,6 +150,7 @@ _lib = _load()
 
 
 def lib():
+    """The loaded libnegf.so (ctypes handle)."""
     return _lib
 
 
@@ -153,6 +158,7 @@ def lib():
 # C-ABI mirror (argument marshalling only)
 # ---------------------------------------------------------------------------
 def negf_status_string(status):
+    """``negf_status_string`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_status_string(int(status)).decode()
 
 
@@ -211,22 +217,26 @@ def negf_solve_noalloc(block_sizes, band_n, n_energies, H, sigma_L, sigma_R, sig
 
 
 def negf_workspace_bytes(plan):
+    """``negf_workspace_bytes`` of include/negf.h (argument marshalling only)."""
     return int(_lib.negf_workspace_bytes(plan))
 
 
 def negf_solve_host(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info):
+    """``negf_solve_host`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_solve_host(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
                                 _ptr(G_band), _ptr(G_1N), _ptr(info))
 
 
 def negf_lesser(plan, H, sigma_L, sigma_R, sigma_E_stride, E, sigma_less_L, sigma_less_R, sless_stride,
                 less_diag, G_band, G_less, info):
+    """``negf_lesser`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_lesser(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
                             _ptr(sigma_less_L), _ptr(sigma_less_R), int(sless_stride), _ptr(less_diag),
                             _ptr(G_band), _ptr(G_less), _ptr(info))
 
 
 def negf_band_residual(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, res):
+    """``negf_band_residual`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_band_residual(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
                                    _ptr(G_band), _ptr(res))
 
@@ -241,54 +251,66 @@ def negf_autotune(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, in
 
 
 def negf_plan_groups(plan):
+    """``negf_plan_groups`` of include/negf.h (argument marshalling only)."""
     return int(_lib.negf_plan_groups(plan))
 
 
 def negf_plan_set_groups(plan, groups):
+    """``negf_plan_set_groups`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_plan_set_groups(plan, int(groups))
 
 
 def negf_plan_n_domains(plan):
+    """``negf_plan_n_domains`` of include/negf.h (argument marshalling only)."""
     return int(_lib.negf_plan_n_domains(plan))
 
 
 def negf_auto_domains(block_sizes, band_n, n_energies, sm_count):
+    """``negf_auto_domains`` of include/negf.h (argument marshalling only)."""
     sizes = (ctypes.c_int32 * len(block_sizes))(*[int(b) for b in block_sizes])
     return int(_lib.negf_auto_domains(len(block_sizes), sizes, int(band_n), int(n_energies), int(sm_count)))
 
 
 def negf_band_offset(plan, d, i):
+    """``negf_band_offset`` of include/negf.h (argument marshalling only)."""
     return int(_lib.negf_band_offset(plan, d, i))
 
 
 def negf_band_elems(plan):
+    """``negf_band_elems`` of include/negf.h (argument marshalling only)."""
     return int(_lib.negf_band_elems(plan))
 
 
 def negf_solve(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info):
+    """``negf_solve`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_solve(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
                            _ptr(G_band), _ptr(G_1N), _ptr(info))
 
 
 def negf_transmission(plan, H, sigma_L, sigma_R, sigma_E_stride, E, T, info):
+    """``negf_transmission`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_transmission(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride),
                                   _ptr(E), _ptr(T), _ptr(info))
 
 
 def negf_grad(plan, H, sigma_L, sigma_R, sigma_E_stride, E, dL_dT, T, dH, dSigma_L, dSigma_R, info):
+    """``negf_grad`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_grad(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
                           _ptr(dL_dT), _ptr(T), _ptr(dH), _ptr(dSigma_L), _ptr(dSigma_R), _ptr(info))
 
 
 def negf_sync(plan):
+    """``negf_sync`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_sync(plan)
 
 
 def negf_destroy(plan):
+    """``negf_destroy`` of include/negf.h (argument marshalling only)."""
     _lib.negf_destroy(plan)
 
 
 def negf_profile_enable(plan, on):
+    """``negf_profile_enable`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_profile_enable(plan, int(bool(on)))
 
 
@@ -461,6 +483,7 @@ class Plan:
         self.info = torch.zeros(self.n_energies, dtype=torch.int32, device="cuda")
 
     def close(self):
+        """Destroy the plan (negf_destroy); idempotent."""
         if getattr(self, "handle", None):
             negf_destroy(self.handle)
             self.handle = None
@@ -482,6 +505,7 @@ class Plan:
         self.torch.cuda.current_stream().wait_stream(self.stream)
 
     def sync(self):
+        """Wait for the plan's stream and raise on a device-reported error (negf_sync)."""
         s = negf_sync(self.handle)
         if s != NEGF_OK:
             raise NegfError(s, "negf_sync")
@@ -601,6 +625,7 @@ class Plan:
         return res
 
     def transmission(self, H, sigma_L, sigma_R, E, out=None, sync=True):
+        """``T(E)`` per energy (negf_transmission); returns a float64 tensor ``[n_E]``."""
         torch = self.torch
         T = out if out is not None else torch.empty(self.n_energies, dtype=torch.float64, device="cuda")
         sigma_L, sigma_R, stride = self._sigmas(sigma_L, sigma_R)
@@ -647,12 +672,14 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, plan, H, sigma_L, sigma_R, E):
+            """T(E) for the given inputs; saves them for the adjoint."""
             ctx.plan = plan
             ctx.save_for_backward(H, sigma_L, sigma_R, E)
             return plan.transmission(H, sigma_L, sigma_R, E)
 
         @staticmethod
         def backward(ctx, gT):
+            """The library's adjoint (negf_grad) with the incoming dL/dT as energy weights."""
             H, sL, sR, E = ctx.saved_tensors
             _, dH, dSL, dSR = ctx.plan.grad(H, sL, sR, E, gT.to(torch.float64))
             return None, dH, dSL, dSR, None
