@@ -2,16 +2,18 @@
 """Benchmark: selected-G^R energies x blocks per second on one GB300.
 
 A step is one full selected inversion (upward Schur sweep, per-block
-inversions, downward pass, G_1N chain) of the synthetic nanowire workload
+inversions, downward pass; on the mixed path G_1N from the last block column
+after one step of iterative refinement) of the synthetic nanowire workload
 "batched64x64": 64 blocks of b = 64, block tridiagonal, 512 energies in
 [-2, 2] with eta = 1e-6, all energies in one call.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
   python bench.py --impl reference    # the CPU oracle on the host cores
 
-Under torchrun (N > 1) every rank runs the full workload on its own GPU with
-its own energy grid (weak scaling, no collective on the data path); rank 0
-prints the line with the max time over ranks.
+Under torchrun (N > 1) the job is one energy list of N x 512 energies in
+[-2, 2]; rank r solves its contiguous share of it on its own GPU (weak
+scaling: fixed work per GPU, every energy solved once, no collective on the
+data path); rank 0 prints the line with the max time over ranks.
 """
 from __future__ import annotations
 
@@ -40,8 +42,8 @@ UNIT = "energy-blocks/s"
 PRODUCT_BITS = {"wire1024": 42, "penta256x32": 42, "trans128x48": 42}
 
 # DRAM traffic per unit (one block inversion) of the dominant kernel from an
-# ncu capture, valid only while the kernel source is the one captured; the
-# summary and its command are in profiles/zinv_gj_kernel_b64_512E_full.md
+# ncu capture of one 512-block launch, valid only while the kernel source is
+# the one captured (the summary and its command are under profiles/)
 NCU_TRAFFIC = {
     ("zinv_gj_kernel", 64): {
         "bytes_per_unit": (33.590272e6 + 0.707584e6) / 512,
@@ -50,10 +52,9 @@ NCU_TRAFFIC = {
     },
 }
 
-# FP64 peaks (TFLOP/s): the GJ inversion is plain DFMA arithmetic (bound
-# "alu"), rated at the GB300's nominal FP64 rate at the 2070 MHz maximum SM
-# clock; the DMMA block product is a contraction, rated at the measured BF16
-# sustained peak times the nominal FP64:BF16 ratio
+# Nominal GB300 FP64 rate at the 2070 MHz maximum SM clock (context only: the
+# roofline of the FP64 kernels is taken against the rates negf_fp64_peak
+# measures in this run, DFMA for the inversion, DMMA for the FP64 product)
 FP64_NOMINAL_TFLOPS = 1.25
 
 
@@ -81,6 +82,8 @@ def _args():
                     help="skip the side measurement of the adjoint (gradient) path")
     ap.add_argument("--no-lesser-side", action="store_true",
                     help="skip the side measurement of the Keldysh (G^<) path")
+    ap.add_argument("--refine-steps", type=int, default=1,
+                    help="refinement steps of the mixed plan's G_1N (the benchmark configuration has one)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -188,10 +191,24 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # multi-rank host logic (replicas over energies; no collective on the data path)
 # ---------------------------------------------------------------------------
+def job_energies(prob_energies, world):
+    """The job's energy list for an N-rank run: N times the workload's count
+    of energies over the same interval with the same eta (one problem whose
+    energies are split over the ranks; N = 1 gives the workload's list)."""
+    import numpy as np
+    if world <= 1:
+        return prob_energies
+    n = len(prob_energies) * world
+    re = prob_energies.real
+    return (np.linspace(re.min(), re.max(), n) + 1j * prob_energies.imag[0]).astype(np.complex128)
+
+
 def rank_energies(energies, rank, world):
-    """Each rank of an N-GPU run solves its own energy grid (weak scaling):
-    rank r shifts the workload's grid by r * 1e-3."""
-    return energies + 1e-3 * rank if world > 1 and rank > 0 else energies
+    """Rank r's contiguous share of the job's energy list (energy_shard of the
+    binding: the shares of all ranks concatenate to the list)."""
+    import paper_2605_19910_gb300 as P
+    lo, hi = P.energy_shard(len(energies), rank, world)
+    return energies[lo:hi]
 
 
 def max_over_ranks(ms, dist, device):
@@ -205,8 +222,33 @@ def max_over_ranks(ms, dist, device):
 
 
 def job_throughput(world, n_energies, n_blocks, ms):
-    """Whole-job energy-blocks per second over all ranks."""
+    """Whole-job energy-blocks per second over all ranks: ``n_energies`` is
+    one rank's share, each of the ``world`` ranks solves a disjoint share of
+    the job's energy list, so every energy counts once."""
     return world * n_energies * n_blocks / (ms * 1e-3)
+
+
+def measure_fp64_peaks(P, local_rank, stream):
+    """FP64 FMA and FP64 MMA rates of this GPU (negf_fp64_peak: one kernel of
+    independent dependency chains per kind, CUDA-event timed), each run for
+    about 0.3 s after a short calibration, with the SM clock sampled during
+    the runs; plus both kinds side by side (whether they share one unit)."""
+    out = {}
+    clocks = Clocks(local_rank)
+    clocks.start()
+    for key, kind in (("dfma_tflops", P.NEGF_PEAK_DFMA), ("dmma_tflops", P.NEGF_PEAK_DMMA),
+                      ("dfma_plus_dmma_tflops", P.NEGF_PEAK_BOTH)):
+        _, ms0 = P.negf_fp64_peak(kind, 2000, stream.cuda_stream)
+        iters = max(2000, int(2000 * 300.0 / max(ms0, 1e-3)))
+        best = 0.0
+        for _ in range(3):
+            tf, _ = P.negf_fp64_peak(kind, iters, stream.cuda_stream)
+            best = max(best, tf)
+        out[key] = best
+    out["clocks"] = clocks.stop()
+    out["how"] = ("negf_fp64_peak: 4 x 256-thread CTAs per SM, 8 independent chains per thread (DFMA) or "
+                  "warp (DMMA m8n8k4), ~0.3 s per run, best of 3")
+    return out
 
 
 def _overrides(a):
@@ -238,7 +280,7 @@ def run_ours(a, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     prob = workload(a.workload, **_overrides(a))
-    prob.energies = rank_energies(prob.energies, rank, world)
+    prob.energies = rank_energies(job_energies(prob.energies, world), rank, world)
     N, nE = prob.n_blocks, len(prob.energies)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
@@ -250,7 +292,9 @@ def run_ours(a, rank, world, local_rank):
     outputs = P.NEGF_OUT_BAND | P.NEGF_OUT_G1N | P.NEGF_OUT_TRANSMISSION
     bits = a.product_bits if a.product_bits is not None else PRODUCT_BITS.get(a.workload, 0)
     bits = bits if a.precision == "mixed" else 0
-    plan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision=a.precision, outputs=outputs, product_bits=bits)
+    refine = a.refine_steps if a.precision == "mixed" else 0
+    plan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision=a.precision, outputs=outputs, product_bits=bits,
+                  refine_steps=refine)
     Gb = torch.empty(nE, plan.band_elems, dtype=torch.complex128, device=dev)
     G1 = torch.empty(nE, prob.sizes[0], prob.sizes[-1], dtype=torch.complex128, device=dev)
 
@@ -306,18 +350,24 @@ def run_ours(a, rank, world, local_rank):
     ms = max_over_ranks(t_start.elapsed_time(t_end) / a.steps, dist, dev)
     value = job_throughput(world, nE, N, ms)
 
-    # sampled parity against the oracle (two energies) for the rel-err report
+    fp64 = measure_fp64_peaks(P, local_rank, stream)
+
+    # sampled parity against the oracle (two energies) for the rel-err report:
+    # the band and G_1N (from the refined last column when refine_steps = 1)
     rel = None
     if rank == 0:
         from oracle import rgf as O
-        errs = []
+        errs, errs1 = [], []
         for e in (0, nE // 2):
             ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, prob.w, first_row=True)
             got = P.unpack_band(Gb[e].cpu().numpy(), prob.sizes, prob.w)
             num = sum(np.linalg.norm(got[k] - v) ** 2 for k, v in ref["band"].items())
             den = sum(np.linalg.norm(v) ** 2 for v in ref["band"].values())
             errs.append(float(np.sqrt(num / den)))
-        rel = max(errs)
+            g1 = G1[e].cpu().numpy()
+            errs1.append(float(np.linalg.norm(g1 - ref["G1N"]) / np.linalg.norm(ref["G1N"])))
+        rel = {"band": max(errs), "G1N": max(errs1), "energies": [0, nE // 2],
+               "G1N_refined": bool(refine)}
 
     # a-posteriori check of every energy's band from the band alone:
     # sqrt(sum_i ||(M G)_ii - I||_F^2 / sum_i b_i) (negf_band_residual)
@@ -363,13 +413,13 @@ def run_ours(a, rank, world, local_rank):
         pass
     src = "MEASURED_PEAKS" if "bf16_tflops_sustained" in peaks else "fallback"
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-    dmma_peak = bf16 * (1.25 / 2250.0)          # FP64 nominal : bf16 nominal
+    dfma_peak, dmma_peak = fp64["dfma_tflops"], fp64["dmma_tflops"]
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     name, (dms, dfl, dln) = dom
     achieved = dfl / (dms * 1e-3) / 1e12 if dms > 0 else 0.0
     if name == "zgemm_f64_kernel":
         bound, peak = "tensor", dmma_peak
-        psrc = f"of measured: {src} bf16 sustained x nominal FP64:bf16 (1.25:2250)"
+        psrc = "of measured: FP64 MMA (mma.sync m8n8k4) loop of negf_fp64_peak in this run"
     elif name == "zgemm_tc_kernel":
         # useful complex-product flops against the BF16 tensor peak: the exact
         # slicing issues several BF16 products per useful one and the kernel
@@ -377,8 +427,8 @@ def run_ours(a, rank, world, local_rank):
         bound, peak = "tensor", bf16
         psrc = f"of measured: {src} bf16 sustained (useful flops of exact-slice emulated products)"
     else:
-        bound, peak = "alu", FP64_NOMINAL_TFLOPS
-        psrc = "nominal GB300 FP64 at the 2070 MHz maximum SM clock (DFMA pipe)"
+        bound, peak = "alu", dfma_peak
+        psrc = "of measured: FP64 FMA loop of negf_fp64_peak in this run (DFMA pipe)"
     issued = None
     if name == "zgemm_f64_kernel":   # the 3M form issues 6 m n k of the 8 m n k counted
         issued = {"achieved": achieved * 0.75, "frac": achieved * 0.75 / peak}
@@ -395,7 +445,7 @@ def run_ours(a, rank, world, local_rank):
             "traffic": traffic, "peak_source": psrc,
             "flop_count": "the method's 8 m n k per complex product / 8 b^3 per inversion",
             "kernel_share": dms / sum(v[0] for v in prof.values()),
-            "launches_per_step": int(dln)}
+            "launches_per_step": int(dln), "nominal_fp64_tflops": FP64_NOMINAL_TFLOPS}
     if issued:
         roof["issued_dmma"] = issued
 
@@ -406,11 +456,12 @@ def run_ours(a, rank, world, local_rank):
         f64 = prof["zinv_gj_kernel"][1]
         fdm = prof["zgemm_f64_kernel"][1]
         flow = prof["zgemm_tc_kernel"][1]
-        t_roof = f64 / (FP64_NOMINAL_TFLOPS * 1e12) + fdm / (dmma_peak * 1e12) + flow / (bf16 * 1e12)
+        t_roof = f64 / (dfma_peak * 1e12) + fdm / (dmma_peak * 1e12) + flow / (bf16 * 1e12)
         composite = {"t_roof_ms": t_roof * 1e3, "t_measured_ms": ms, "frac": t_roof * 1e3 / ms,
                      "fp64_inverse_flops": f64, "fp64_product_flops": fdm, "tensor_product_flops": flow,
-                     "peaks": {"fp64_alu_tflops": FP64_NOMINAL_TFLOPS, "fp64_dmma_tflops": dmma_peak,
-                               "bf16_tflops": bf16}}
+                     "peaks": {"fp64_alu_tflops": dfma_peak, "fp64_dmma_tflops": dmma_peak,
+                               "bf16_tflops": bf16, "source": "FP64: negf_fp64_peak in this run; "
+                                                             "bf16: MEASURED_PEAKS sustained"}}
 
     from oracle.rgf import rgf_flops_paper
     flops_step = rgf_flops_paper(prob.sizes, prob.w) * nE
@@ -517,7 +568,9 @@ def run_ours(a, rank, world, local_rank):
             "config": {"workload": a.workload, "n_blocks": N, "block_size": prob.sizes[0], "band_n": 2 * prob.w + 1,
                        "n_energies": nE, "eta": 1e-6, "precision": a.precision,
                        "product_bits": plan_bits if a.precision == "mixed" else None,
-                       "outputs": "band + G_1N per energy",
+                       "refine_steps": refine,
+                       "outputs": "band + G_1N per energy" + (" (G_1N from the refined last block column)"
+                                                              if refine else ""),
                        "l2": "no flush: each step writes %.1f GB of selected blocks and %.1f GB of sweep "
                              "workspace, both far above the 129 MB L2" % (Gb.numel() * 16 / 1e9, ws_gb),
                        "parallelism": f"replicas x{world} (energies)",
@@ -528,6 +581,7 @@ def run_ours(a, rank, world, local_rank):
             "band_residual": band_residual,
             "roofline": roof,
             "composite_roofline": composite,
+            "fp64_peaks_measured": fp64,
             "fp64_path": fp64_side,
             "lesser_path": lesser_side,
             "grad_path": grad_side,

@@ -325,15 +325,21 @@ int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* la
  * GPU that loads the library holds until the process exits.
  *
  * Arguments are those of negf_plan plus negf_solve, with the descriptor in
- * place of a plan: FP64 only, n_domains == 1, no NEGF_OUT_GRAD (otherwise
- * NEGF_ERR_UNSUPPORTED).  The caller passes device inputs and outputs as for
- * negf_solve.  If the scratch this descriptor needs,
+ * place of a plan: FP64 only, n_domains == 1, and outputs a subset of
+ * NEGF_OUT_BAND | NEGF_OUT_G1N (anything else: NEGF_ERR_UNSUPPORTED; a
+ * requested output with a NULL buffer: NEGF_ERR_ARG).  The caller passes
+ * device inputs and outputs as for negf_solve, with the same rule on
+ * sigma_E_stride (0, or at least max(b_1^2, b_N^2); else NEGF_ERR_ARG).  The
+ * band is written when G_band is not NULL, G_1N when G_1N is not NULL.  If
+ * the scratch this descriptor needs,
  *   256 + 16 * n_energies * (sum_i b_i^2 + 2 * sum_{|i-j|=1..w, i>j} b_i b_j
  *                            + (w+1)^2 * bmax^2 + (w+1) * b_1 * bmax)  bytes,
  * exceeds NEGF_NOALLOC_SCRATCH_BYTES, the call returns NEGF_ERR_ARG before
  * launching anything.  Work is enqueued on cuda_stream without a CUDA graph.
  * Numerical failures are reported only through info[] (there is no plan to
- * negf_sync).
+ * negf_sync): info[e] = k > 0 names the first layer (1-based) whose pivot
+ * was zero OR non-finite; the two cases are not told apart here (a NaN or
+ * Inf in H or Sigma shows as non-finite values in that energy's outputs).
  *
  * The first call on each device sets that device up (it looks up the device
  * address of the scratch array and sets kernel attributes); make that first
@@ -345,6 +351,22 @@ int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* la
 negf_status negf_solve_noalloc(const negf_desc* d, const negf_c128* H, const negf_c128* sigma_L,
                                const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                                negf_c128* G_band, negf_c128* G_1N, int32_t* info, void* cuda_stream);
+
+/* FP64 peak probe (instrumentation; no counterpart in the paper).  Runs one
+ * kernel that keeps every SM's FP64 units busy with one instruction kind on
+ * independent dependency chains, and returns the issued rate in TFLOP/s:
+ *   NEGF_PEAK_DFMA: scalar FP64 fused multiply-add (2 flops each), the
+ *                   arithmetic of the per-block inversion;
+ *   NEGF_PEAK_DMMA: FP64 MMA m8n8k4 (512 flops per warp instruction), the
+ *                   arithmetic of the FP64 block product;
+ *   NEGF_PEAK_BOTH: half of the warps each (whether the two kinds share one
+ *                   FP64 unit: the sum of both rates if they do not).
+ * iters: loop trips per thread (8 instructions each; ~1e5 gives about
+ * 0.1 s).  tflops: required; ms (nullable): the kernel's CUDA-event time.
+ * Synchronous on cuda_stream (NULL = legacy default stream); allocates
+ * nothing.  NEGF_ERR_ARG for an unknown kind or iters < 1. */
+enum { NEGF_PEAK_DFMA = 0, NEGF_PEAK_DMMA = 1, NEGF_PEAK_BOTH = 2 };
+negf_status negf_fp64_peak(int32_t kind, int32_t iters, double* tflops, double* ms, void* cuda_stream);
 
 /* Text of the last CUDA runtime error this thread's calls met (for
  * NEGF_ERR_CUDA diagnostics); "no error" if none. */

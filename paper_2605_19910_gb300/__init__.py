@@ -54,9 +54,13 @@ EXPORTED = [
     "negf_plan_set_groups", "negf_lesser", "negf_solve_host",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
+    "negf_fp64_peak",
 ]
 
 NEGF_NOALLOC_SCRATCH_BYTES = 32 << 20
+NEGF_PEAK_DFMA = 0
+NEGF_PEAK_DMMA = 1
+NEGF_PEAK_BOTH = 2
 AUTOTUNE_GROUPS = (1, 2, 3, 4, 6, 8)   # the candidates of negf_autotune, in its order
 
 
@@ -143,6 +147,8 @@ def _load():
     lib.negf_plan_n_domains.restype = i32
     lib.negf_auto_domains.argtypes = [i32, ctypes.POINTER(i32), i32, i32, i32]
     lib.negf_auto_domains.restype = i32
+    lib.negf_fp64_peak.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+    lib.negf_fp64_peak.restype = st
     return lib
 
 
@@ -214,6 +220,26 @@ def negf_solve_noalloc(block_sizes, band_n, n_energies, H, sigma_L, sigma_R, sig
     d.product_bits = 0
     return _lib.negf_solve_noalloc(ctypes.byref(d), _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride),
                                    _ptr(E), _ptr(G_band), _ptr(G_1N), _ptr(info), stream)
+
+
+def negf_fp64_peak(kind, iters, stream=None):
+    """``negf_fp64_peak`` of include/negf.h: returns ``(TFLOP/s, ms)``; raises NegfError."""
+    tf = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    s = _lib.negf_fp64_peak(int(kind), int(iters), ctypes.byref(tf), ctypes.byref(ms), stream)
+    if s != NEGF_OK:
+        raise NegfError(s, "negf_fp64_peak")
+    return tf.value, ms.value
+
+
+def energy_shard(n_energies, rank, world):
+    """Contiguous share ``[lo, hi)`` of an energy list of ``n_energies`` for
+    rank ``rank`` of ``world`` (energies are independent problems, so ranks
+    need no exchange); the shares of ranks 0..world-1 concatenate to the whole
+    list, their sizes differing by at most one."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("rank outside [0, world)")
+    return (int(n_energies) * rank) // world, (int(n_energies) * (rank + 1)) // world
 
 
 def negf_workspace_bytes(plan):

@@ -29,12 +29,15 @@ using negf::ZGemm;
 namespace {
 
 // A per-energy self-energy stride must keep the energies' lead blocks apart
-// (0 broadcasts one block to every energy).
-bool bad_sigma_stride(const negf_plan_s* p, int64_t stride) {
+// (0 broadcasts one block to every energy): 0, or at least the larger lead
+// block b_1^2, b_N^2.
+bool bad_sigma_stride_sizes(int b_first, int b_last, int64_t stride) {
   if (stride < 0) return true;
   if (stride == 0) return false;
-  const int64_t need = std::max(sq(p->b[0]), sq(p->b[p->N - 1]));
-  return stride < need;
+  return stride < std::max(sq(b_first), sq(b_last));
+}
+bool bad_sigma_stride(const negf_plan_s* p, int64_t stride) {
+  return bad_sigma_stride_sizes(p->b[0], p->b[p->N - 1], stride);
 }
 
 // ---------------------------------------------------------------------------
@@ -1039,8 +1042,13 @@ extern "C" negf_status negf_solve_noalloc(const negf_desc* d, const negf_c128* H
                                           negf_c128* G_band, negf_c128* G_1N, int32_t* info, void* cuda_stream) {
   negf_status v = validate(d);
   if (v != NEGF_OK) return v;
-  if (!H || !E || !info || sigma_E_stride < 0 || (!G_band && !G_1N)) return NEGF_ERR_ARG;
-  if (d->n_domains != 1 || d->precision != NEGF_FP64 || (d->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_UNSUPPORTED;
+  if (!H || !E || !info || (!G_band && !G_1N)) return NEGF_ERR_ARG;
+  if (bad_sigma_stride_sizes(d->block_sizes[0], d->block_sizes[d->n_blocks - 1], sigma_E_stride))
+    return NEGF_ERR_ARG;
+  if (d->n_domains != 1 || d->precision != NEGF_FP64 || (d->outputs & ~(NEGF_OUT_BAND | NEGF_OUT_G1N)))
+    return NEGF_ERR_UNSUPPORTED;
+  // every requested output needs its buffer
+  if (((d->outputs & NEGF_OUT_BAND) && !G_band) || ((d->outputs & NEGF_OUT_G1N) && !G_1N)) return NEGF_ERR_ARG;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) { g_last_cuda = e; return NEGF_ERR_CUDA; }
