@@ -101,7 +101,7 @@ typedef struct {
                                          layer of each (D2, D1) pair; pair j is
                                          D2_j then a separator D1_j of w layers;
                                          entry 0 must be 0, every pair must have
-                                         at least 2w layers.  NULL balances the
+                                         at least 3w layers.  NULL balances the
                                          pairs by sum of b_i^3 (Sec. 3).        */
   int32_t precision;                  /* negf_precision                        */
   int32_t refine_steps;               /* 0 or 1 (NEGF_MIXED only)              */

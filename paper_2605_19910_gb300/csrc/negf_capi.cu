@@ -194,56 +194,21 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
         while (i < N && cum[i] < target - 1e-9 * cum[N]) ++i;
         first[j] = j == 0 ? 0 : i;
       }
+      // every pair keeps at least 3w layers (a sub-domain of 2w, a separator of w)
+      for (int j = 1; j < nd; ++j) first[j] = std::max(first[j], first[j - 1] + 3 * w);
+      for (int j = nd - 1; j >= 1; --j) first[j] = std::min(first[j], (j + 1 < nd ? first[j + 1] : N) - 3 * w);
     }
     p->dom_f.resize(nd); p->dom_l.resize(nd);
     for (int j = 0; j < nd; ++j) {
       const int lo = first[j], hi = (j + 1 < nd) ? first[j + 1] : N;   // pair = [lo, hi)
-      if ((j == 0 && lo != 0) || hi - lo < 2 * w || hi - lo - w < 1) { delete p; return NEGF_ERR_ARG; }
+      // a pair holds its sub-domain (at least 2w layers: disjoint first and
+      // last w layers) and its separator of w layers
+      if ((j == 0 && lo != 0) || hi - lo < 3 * w) { delete p; return NEGF_ERR_ARG; }
       p->dom_f[j] = lo;
       p->dom_l[j] = hi - w - 1;
     }
-    p->dom_of.assign(N, -1); p->sep_of.assign(N, -1); p->off_in.assign(N, 0);
-    p->Fsz.assign(nd, 0); p->Lsz.assign(nd, 0); p->Psz.assign(nd, 0);
-    for (int j = 0; j < nd; ++j) {
-      for (int a = p->dom_f[j]; a <= p->dom_l[j]; ++a) p->dom_of[a] = j;
-      for (int r = 0; r < w; ++r) {
-        p->Fsz[j] += p->b[p->dom_f[j] + r];
-        p->Lsz[j] += p->b[p->dom_l[j] - w + 1 + r];
-        const int sl = p->dom_l[j] + 1 + r;
-        p->sep_of[sl] = j;
-        p->off_in[sl] = p->Psz[j];
-        p->Psz[j] += p->b[sl];
-      }
-      p->Pmax = std::max(p->Pmax, p->Psz[j]);
-    }
-    p->fc_off.assign(N, 0); p->lc_off.assign(N, 0); p->wp_off.assign(N, 0); p->wq_off.assign(N, 0);
-    for (int a = 0; a < N; ++a) {
-      const int j = p->dom_of[a];
-      if (j < 0) continue;
-      const int Pp = j > 0 ? p->Psz[j - 1] : 0;
-      p->fc_off[a] = p->fc_e; p->fc_e += (int64_t)p->b[a] * p->Fsz[j];
-      p->lc_off[a] = p->lc_e; p->lc_e += (int64_t)p->b[a] * p->Lsz[j];
-      p->wp_off[a] = p->wp_e; p->wp_e += (int64_t)p->b[a] * Pp;
-      p->wq_off[a] = p->wq_e; p->wq_e += (int64_t)p->b[a] * p->Psz[j];
-    }
-    p->tsd_off.assign(nd, 0); p->tsu_off.assign(nd, 0); p->rs_off.assign(nd, 0); p->ts_x_off.assign(nd, 0);
-    for (int k = 0; k < nd; ++k) {
-      p->tsd_off[k] = p->tsd_e; p->tsd_e += sq(p->Psz[k]);
-      p->rs_off[k] = p->rs_e; p->rs_e += (int64_t)p->Psz[0] * p->Psz[k];
-      if (k + 1 < nd) { p->tsu_off[k] = p->tsu_e; p->tsu_e += (int64_t)p->Psz[k] * p->Psz[k + 1]; }
-      if (k >= 1) { p->ts_x_off[k] = p->ts_x_e; p->ts_x_e += (int64_t)p->Psz[k] * p->Psz[k - 1]; }
-    }
-    p->mfp_off.assign(nd, 0); p->mpf_off.assign(nd, 0); p->mlq_off.assign(nd, 0); p->mql_off.assign(nd, 0);
-    for (int j = 0; j < nd; ++j) {
-      const int Pp = j > 0 ? p->Psz[j - 1] : 0;
-      p->mfp_off[j] = p->msup_e; p->msup_e += (int64_t)p->Fsz[j] * Pp;
-      p->mpf_off[j] = p->msup_e; p->msup_e += (int64_t)Pp * p->Fsz[j];
-      p->mlq_off[j] = p->msup_e; p->msup_e += (int64_t)p->Lsz[j] * p->Psz[j];
-      p->mql_off[j] = p->msup_e; p->msup_e += (int64_t)p->Psz[j] * p->Lsz[j];
-    }
-    if (p->Pmax > negf::zinv_max_block()) { delete p; return NEGF_ERR_UNSUPPORTED; }
-    dd_e = 2 * p->fc_e + 3 * p->lc_e + 3 * p->wp_e + 3 * p->wq_e + 3 * p->tsd_e + 4 * p->tsu_e +
-           2 * p->ts_x_e + sq(p->Pmax) + p->rs_e + p->band_elems;
+    if (!dd_layout(p, negf::zinv_max_block())) { delete p; return NEGF_ERR_UNSUPPORTED; }
+    dd_e = p->dd_e + p->band_elems;
   }
 
   // per-energy workspace layout
@@ -281,7 +246,6 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   const bool refine = d->refine_steps > 0 && d->precision == NEGF_MIXED && d->n_domains == 1 && p->ck_k == 0;
   p->refine = refine ? 1 : 0;
   p->p_elems = (grad || refine) ? pe : 0;
-  int64_t rf_elems = refine ? pe : 0;
   int64_t ck_elems = 0;
   if (p->ck_k > 0) {
     p->p_elems = (int64_t)(p->ck_k + 1) * p->bmaxN;
@@ -293,7 +257,7 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   const int64_t lesser_e = (d->outputs & NEGF_OUT_LESSER) ? 2 * te : 0;
   const int64_t dh_e = grad ? p->bmax2 : 0;
   int64_t per_e = dh_e + lesser_e + te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot * std::max(1, p->n_domains) +
-                  (p->full_row ? re : (int64_t)(w + 1) * b0 * bmax) + 2 * p->p_elems + rf_elems + ck_elems +
+                  (p->full_row ? re : (int64_t)(w + 1) * b0 * bmax) + 2 * p->p_elems + ck_elems +
                   p->scr_elems + dd_e;
   // chunk energies so that the workspace stays within a budget: 45% of the
   // device memory free at plan time, at least 24 GiB (the caller's outputs
@@ -308,7 +272,7 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   const int64_t budget_elems = (int64_t)(budget_bytes / (double)sizeof(double2));
   int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(p->nE, budget_elems / std::max<int64_t>(per_e, 1)));
   p->chunk = chunk;
-  p->ws_bytes = (size_t)(per_e * chunk + p->msup_e) * sizeof(double2) + 256;
+  p->ws_bytes = (size_t)(per_e * chunk + p->hf_e) * sizeof(double2) + 256;
   cudaError_t err = cudaMalloc((void**)&p->ws, p->ws_bytes);
   if (err != cudaSuccess) { g_last_cuda = err; cudaGetLastError(); delete p; return NEGF_ERR_NOMEM; }
   err = cudaMalloc((void**)&p->d_err, sizeof(int) + sizeof(double) * (size_t)p->nE);
@@ -323,7 +287,6 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   p->R_ws = q; q += (p->full_row ? re : (int64_t)(w + 1) * b0 * bmax) * chunk;
   p->P_ws = q; q += p->p_elems * chunk;
   p->LC_ws = q; q += p->p_elems * chunk;
-  p->RF_ws = q; q += rf_elems * chunk;
   if (p->ck_k > 0) {
     p->CKS = q; q += (int64_t)p->ck_nseg * p->bmax2 * chunk;
     p->CKP = q; q += (int64_t)p->ck_nseg * p->bmaxN * chunk;
@@ -338,30 +301,9 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   p->scratch = q; q += p->scr_elems * chunk;
   p->G1N_ws = p->scratch + (sq(b0) + sq(bN) + 2 * (int64_t)b0 * bN) * chunk;
   if (p->n_domains > 1) {
-    p->FC = q; q += p->fc_e * chunk;
-    p->FR = q; q += p->fc_e * chunk;
-    p->LCd = q; q += p->lc_e * chunk;
-    p->LR = q; q += p->lc_e * chunk;
-    p->VT = q; q += p->lc_e * chunk;
-    p->Wp = q; q += p->wp_e * chunk;
-    p->Vp = q; q += p->wp_e * chunk;
-    p->Zp = q; q += p->wp_e * chunk;
-    p->Wq = q; q += p->wq_e * chunk;
-    p->Vq = q; q += p->wq_e * chunk;
-    p->Zq = q; q += p->wq_e * chunk;
-    p->TSd = q; q += p->tsd_e * chunk;
-    p->GSd = q; q += p->tsd_e * chunk;
-    p->tS = q; q += p->tsd_e * chunk;
-    p->TSu = q; q += p->tsu_e * chunk;
-    p->TSl = q; q += p->tsu_e * chunk;
-    p->GSu = q; q += p->tsu_e * chunk;
-    p->GSl = q; q += p->tsu_e * chunk;
-    p->XS = q; q += p->ts_x_e * chunk;
-    p->YS = q; q += p->ts_x_e * chunk;
-    p->SS = q; q += sq(p->Pmax) * chunk;
-    p->RS = q; q += p->rs_e * chunk;
+    p->DDW = q; q += p->dd_e * chunk;
     p->band_ws = q; q += p->band_elems * chunk;
-    p->Msup = q; q += p->msup_e;
+    p->Hf = q; q += p->hf_e;
   }
   // one-time kernel attributes (kept out of graph capture)
   {
@@ -563,7 +505,7 @@ negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigm
       const int64_t s1 = (int64_t)p->b[0] * p->b[p->N - 1];
       if (p->n_domains > 1) {
         if (!G_band) { base.Gband = p->band_ws; base.gb_e0 = e0; }
-        if (e0 == 0) NEGF_TRY(DD(p, base).assemble_msup());
+        if (e0 == 0) NEGF_TRY(DD(p, base).assemble_static());
         NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
           return DD(p, s).run(true, G_1N ? (double2*)G_1N + (int64_t)s.e0 * s1 : nullptr, s1);
         }));
@@ -573,12 +515,9 @@ negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigm
         if (p->ck_k > 0) return s.ck_forward((double2*)G_1N + (int64_t)s.e0 * s1, s1);
         NEGF_TRY(s.upward(G_band != nullptr || (G_1N && p->refine)));
         if (G_band) NEGF_TRY(s.downward());
-        if (G_1N && p->refine) {   // G_1N = first block of the refined last column
+        if (G_1N && p->refine) {   // G_1N = first block of the last column, refined
           NEGF_TRY(s.last_column());
-          NEGF_TRY(s.refine_last_column());
-          return s.misc([&] {
-            return negf::copy_blocks(s.LCblk(0), s1, (double2*)G_1N + (int64_t)s.e0 * s1, s1, s1, s.ne, s.st);
-          });
+          return s.refine_g1n((double2*)G_1N + (int64_t)s.e0 * s1, s1);
         }
         if (G_1N) NEGF_TRY(s.first_row((double2*)G_1N + (int64_t)s.e0 * s1, s1));
         return cudaSuccess;
@@ -607,7 +546,7 @@ negf_status negf_transmission(negf_plan_t* p, const negf_c128* H, const negf_c12
       if (p->n_domains > 1) {
         base.Gband = p->band_ws;
         base.gb_e0 = e0;
-        if (e0 == 0) NEGF_TRY(DD(p, base).assemble_msup());
+        if (e0 == 0) NEGF_TRY(DD(p, base).assemble_static());
       }
       NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
         double2* g1n = p->G1N_ws + (int64_t)s.wofs * s1;
@@ -618,8 +557,7 @@ negf_status negf_transmission(negf_plan_t* p, const negf_c128* H, const negf_c12
         } else if (p->refine) {
           NEGF_TRY(s.upward(true));
           NEGF_TRY(s.last_column());
-          NEGF_TRY(s.refine_last_column());
-          NEGF_TRY(s.misc([&] { return negf::copy_blocks(s.LCblk(0), s1, g1n, s1, s1, s.ne, s.st); }));
+          NEGF_TRY(s.refine_g1n(g1n, s1));
         } else {
           NEGF_TRY(s.upward(false));
           NEGF_TRY(s.first_row(g1n, s1));

@@ -1,5 +1,5 @@
 // DDRGF (Sec. 3, Alg. 2) schedule of one energy range (one TU: included by
-// negf_capi.cu only).
+// negf_capi.cu only), with the plan's DDRGF workspace layout.
 #pragma once
 
 #include "negf_sweep.cuh"
@@ -7,10 +7,148 @@
 namespace {
 
 // ---------------------------------------------------------------------------
-// DDRGF (Sec. 3, Alg. 2) for one energy range: per-domain extended RGF,
-// the interface Schur complement T_S in FP64, its block tridiagonal RGF
-// (Prop. 4) in FP64, and the stitching of the four parts of
-// Eq. 2x2_explicit_inverse_parallel_DDRGF restricted to the band.
+// Layout.  The chain is cut into n_domains (D2, D1) pairs (Fig.
+// parallel_RGF_domains): D2_j = [dom_f[j], dom_l[j]] followed by its
+// separator D1_j of w layers.  F_j / L_j are the first / last w layers of
+// D2_j, P_j the separator's layers as one super-block.
+//
+// Step 1 works on each closed sub-domain cut into w-layer groups (a block
+// tridiagonal chain of super-blocks, Sec. 2.3 block fusing): anchored at the
+// first layer for the right-connected sweep (the last group may be shorter)
+// and at the last layer for the left-connected sweep (the first group may be
+// shorter).  Eliminating whole w-layer groups pivots across the group, which
+// keeps the closed sub-domains' corners accurate near their resonances.
+// ---------------------------------------------------------------------------
+
+// Fills the DDRGF part of the plan (domain layout already in dom_f / dom_l)
+// and returns false if a super-block exceeds the inversion kernel's limit.
+inline bool dd_layout(negf_plan_s* p, int max_block) {
+  const int N = p->N, w = p->w, nd = p->n_domains;
+  p->dom_of.assign(N, -1); p->sep_of.assign(N, -1); p->off_in.assign(N, 0);
+  p->Fsz.assign(nd, 0); p->Lsz.assign(nd, 0); p->Psz.assign(nd, 0);
+  for (int j = 0; j < nd; ++j) {
+    for (int a = p->dom_f[j]; a <= p->dom_l[j]; ++a) p->dom_of[a] = j;
+    for (int r = 0; r < w; ++r) {
+      p->off_in[p->dom_f[j] + r] = p->Fsz[j];
+      p->Fsz[j] += p->b[p->dom_f[j] + r];
+      p->Lsz[j] += p->b[p->dom_l[j] - w + 1 + r];
+      const int sl = p->dom_l[j] + 1 + r;
+      p->sep_of[sl] = j;
+      p->off_in[sl] = p->Psz[j];
+      p->Psz[j] += p->b[sl];
+    }
+    p->Pmax = std::max(p->Pmax, p->Psz[j]);
+    p->FLmax = std::max(p->FLmax, std::max(p->Fsz[j], p->Lsz[j]));
+  }
+  p->dd_e = 0;
+  p->hf_e = 0;
+  auto reg = [&](int64_t size) { negf_plan_s::Reg r{p->dd_e, size}; p->dd_e += size; return r; };
+  auto hreg = [&](int64_t size) { const int64_t o = p->hf_e; p->hf_e += size; return o; };
+  p->grR.assign(nd, DDGroups());
+  p->grL.assign(nd, DDGroups());
+  p->Bmax = 0;
+  for (int j = 0; j < nd; ++j) {
+    const int f = p->dom_f[j], l = p->dom_l[j];
+    for (int side = 0; side < 2; ++side) {
+      DDGroups& g = side == 0 ? p->grR[j] : p->grL[j];
+      std::vector<std::pair<int, int>> ranges;   // [lo, hi] layers of each group, in chain order
+      if (side == 0)
+        for (int lo = f; lo <= l; lo += w) ranges.push_back({lo, std::min(l, lo + w - 1)});
+      else {
+        for (int hi = l; hi >= f; hi -= w) ranges.push_back({std::max(f, hi - w + 1), hi});
+        std::reverse(ranges.begin(), ranges.end());
+      }
+      for (auto& rg : ranges) {
+        int sz = 0;
+        for (int a = rg.first; a <= rg.second; ++a) sz += p->b[a];
+        g.first.push_back(rg.first);
+        g.nl.push_back(rg.second - rg.first + 1);
+        g.sz.push_back(sz);
+        p->Bmax = std::max(p->Bmax, sz);
+      }
+      const int K = (int)g.sz.size();
+      for (int I = 0; I < K; ++I) {
+        g.hd.push_back(hreg(sq(g.sz[I])));
+        g.hu.push_back(I + 1 < K ? hreg((int64_t)g.sz[I] * g.sz[I + 1]) : -1);
+        g.hl.push_back(I + 1 < K ? hreg((int64_t)g.sz[I + 1] * g.sz[I]) : -1);
+        if (side == 0) {
+          g.t.push_back(reg(sq(g.sz[I])));
+          g.x.push_back(I > 0 ? reg((int64_t)g.sz[I] * g.sz[I - 1]) : negf_plan_s::Reg{});
+          g.y.push_back(I > 0 ? reg((int64_t)g.sz[I - 1] * g.sz[I]) : negf_plan_s::Reg{});
+        }
+      }
+    }
+  }
+  if (p->Bmax > max_block || p->Pmax > max_block || p->FLmax > max_block) return false;
+  const int64_t B2 = sq(p->Bmax);
+  p->r_xll.resize(nd); p->r_xfl.resize(nd); p->r_xlf.resize(nd);
+  p->r_lsS.resize(nd); p->r_lsG.resize(nd); p->r_lsY.resize(nd); p->r_row.resize(nd); p->r_col.resize(nd);
+  p->r_wr.resize(nd); p->r_vr.resize(nd); p->r_sr.resize(nd); p->r_wl.resize(nd); p->r_vl.resize(nd);
+  p->r_sl.resize(nd); p->r_tmp.resize(nd);
+  for (int j = 0; j < nd; ++j) {
+    const int F = p->Fsz[j], L = p->Lsz[j], P = p->Psz[j], P0 = j > 0 ? p->Psz[j - 1] : 0;
+    p->r_xll[j] = reg(sq(L));
+    p->r_xfl[j] = reg((int64_t)F * L);
+    p->r_xlf[j] = reg((int64_t)L * F);
+    p->r_lsS[j] = reg(B2);
+    p->r_lsG[j] = reg(B2);
+    p->r_lsY[j] = reg(B2);
+    p->r_row[j] = reg(2 * (int64_t)F * p->Bmax);
+    p->r_col[j] = reg(2 * (int64_t)p->Bmax * F);
+    p->r_wr[j] = reg((int64_t)L * P);
+    p->r_vr[j] = reg((int64_t)P * L);
+    p->r_sr[j] = reg(sq(L));
+    p->r_wl[j] = reg((int64_t)F * P0);
+    p->r_vl[j] = reg((int64_t)P0 * F);
+    p->r_sl[j] = reg(sq(F));
+    p->r_tmp[j] = reg((int64_t)p->Pmax * p->FLmax);
+  }
+  p->r_A.resize(nd); p->r_cL.resize(nd); p->r_cR.resize(nd); p->r_base.resize(nd); p->r_LL.resize(nd);
+  p->r_RR.resize(nd); p->r_gLin.resize(nd); p->r_gLs.resize(nd); p->r_gRin.resize(nd); p->r_gRs.resize(nd);
+  p->r_Gpp.resize(nd); p->r_Tu.resize(nd); p->r_Tl.resize(nd);
+  for (int k = 0; k < nd; ++k) {
+    const int64_t P2 = sq(p->Psz[k]), PP = k + 1 < nd ? (int64_t)p->Psz[k] * p->Psz[k + 1] : 0;
+    p->r_A[k] = reg(P2); p->r_cL[k] = reg(P2); p->r_cR[k] = reg(P2); p->r_base[k] = reg(P2);
+    p->r_LL[k] = reg(P2); p->r_RR[k] = reg(P2); p->r_gLin[k] = reg(P2); p->r_gLs[k] = reg(P2);
+    p->r_gRin[k] = reg(P2); p->r_gRs[k] = reg(P2); p->r_Gpp[k] = reg(P2);
+    p->r_Tu[k] = reg(PP); p->r_Tl[k] = reg(PP);
+  }
+  p->r_itL = reg(sq(p->Pmax));
+  p->r_itR = reg(sq(p->Pmax));
+  p->r_g1 = reg(2 * (int64_t)p->b[0] * p->Pmax);
+  p->r_g1t = reg((int64_t)p->b[0] * p->Pmax);
+  // energy-independent M super-blocks between F / L and the separators
+  p->mfp_off.assign(nd, 0); p->mpf_off.assign(nd, 0); p->mlq_off.assign(nd, 0); p->mql_off.assign(nd, 0);
+  for (int j = 0; j < nd; ++j) {
+    const int Pp = j > 0 ? p->Psz[j - 1] : 0;
+    p->mfp_off[j] = hreg((int64_t)p->Fsz[j] * Pp);
+    p->mpf_off[j] = hreg((int64_t)Pp * p->Fsz[j]);
+    p->mlq_off[j] = hreg((int64_t)p->Lsz[j] * p->Psz[j]);
+    p->mql_off[j] = hreg((int64_t)p->Psz[j] * p->Lsz[j]);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// DDRGF for one energy range:
+//   step 1: per sub-domain (concurrently), the corner super-blocks X_FF,
+//           X_FL, X_LF, X_LL of the closed sub-domain's inverse (fused
+//           right- and left-connected sweeps, first super-row / column
+//           chains);
+//   steps 2-3: the interface system T_S = T11 - T12 X T21 (Eq.
+//           Schur_complement_in_parallel_DDRGF; block tridiagonal over the
+//           separators, Prop. 4), FP64: its left- and right-connected sweeps
+//           and the separator diagonals of T_S^{-1}; every matrix that is
+//           inverted is formed from its own parts;
+//   step 4: the four parts of Eq. 2x2_explicit_inverse_parallel_DDRGF on the
+//           band, evaluated as each sub-domain's RGF with the boundary
+//           self-energies Sigma_left = M_{F,p} gL_p M_{p,F} and Sigma_right =
+//           M_{L,q} gR_q M_{q,L} of the rest of the chain (gL_p / gR_q: the
+//           interface's connected Green's functions at the neighbouring
+//           separators without this sub-domain), plus the blocks between the
+//           sub-domain and its separators.  Equal in exact arithmetic to the
+//           stitching G_22 = X + X T21 T_S^{-1} T12 X, without adding the
+//           closed sub-domain's inverse to a term that cancels it.
 // ---------------------------------------------------------------------------
 struct DD {
   negf_plan_s* p;
@@ -21,57 +159,23 @@ struct DD {
   DD(negf_plan_s* pp, Sweep& ss) : p(pp), s(ss), w(pp->w), nd(pp->n_domains), C(ss.ne), sG(pp->band_elems) {}
 
   int b(int i) const { return p->b[i]; }
-  int Pp(int j) const { return j > 0 ? p->Psz[j - 1] : 0; }
-  double2* reg(double2* base, int64_t off, int64_t size) const {
-    return base + off * p->chunk + (int64_t)s.wofs * size;
-  }
-  int offF(int c) const {          // column offset of layer c inside F of its domain
-    const int j = p->dom_of[c];
-    int o = 0;
-    for (int k = p->dom_f[j]; k < c; ++k) o += b(k);
-    return o;
-  }
-  int offL(int c) const {          // column offset of layer c inside Lw of its domain
+  double2* R(const negf_plan_s::Reg& r) const { return p->DDW + r.off * p->chunk + (int64_t)s.wofs * r.sz; }
+  const double2* HF(int64_t off) const { return p->Hf + off; }
+  int offL(int c) const {          // offset of layer c inside L of its domain
     const int j = p->dom_of[c];
     int o = 0;
     for (int k = p->dom_l[j] - w + 1; k < c; ++k) o += b(k);
     return o;
   }
-  bool inF(int c) const { const int j = p->dom_of[c]; return j >= 0 && c < p->dom_f[j] + w; }
-  bool inL(int c) const { const int j = p->dom_of[c]; return j >= 0 && c > p->dom_l[j] - w; }
-  int Fj(int a) const { return p->Fsz[p->dom_of[a]]; }
-  int Lj(int a) const { return p->Lsz[p->dom_of[a]]; }
-  int Pj(int a) const { return p->Psz[p->dom_of[a]]; }
-  int Pm(int a) const { return Pp(p->dom_of[a]); }
+  int offF(int c) const { return p->off_in[c]; }   // offset of layer c inside F of its domain
 
-  double2* FC(int a) const { return reg(p->FC, p->fc_off[a], (int64_t)b(a) * Fj(a)); }
-  double2* FR(int a) const { return reg(p->FR, p->fc_off[a], (int64_t)b(a) * Fj(a)); }
-  double2* LC(int a) const { return reg(p->LCd, p->lc_off[a], (int64_t)b(a) * Lj(a)); }
-  double2* LR(int a) const { return reg(p->LR, p->lc_off[a], (int64_t)b(a) * Lj(a)); }
-  double2* VT(int a) const { return reg(p->VT, p->lc_off[a], (int64_t)b(a) * Lj(a)); }
-  double2* Wp(int a) const { return reg(p->Wp, p->wp_off[a], (int64_t)b(a) * Pm(a)); }
-  double2* Vp(int a) const { return reg(p->Vp, p->wp_off[a], (int64_t)b(a) * Pm(a)); }
-  double2* Zp(int a) const { return reg(p->Zp, p->wp_off[a], (int64_t)b(a) * Pm(a)); }
-  double2* Wq(int a) const { return reg(p->Wq, p->wq_off[a], (int64_t)b(a) * Pj(a)); }
-  double2* Vq(int a) const { return reg(p->Vq, p->wq_off[a], (int64_t)b(a) * Pj(a)); }
-  double2* Zq(int a) const { return reg(p->Zq, p->wq_off[a], (int64_t)b(a) * Pj(a)); }
-  double2* TSd(int k) const { return reg(p->TSd, p->tsd_off[k], sq(p->Psz[k])); }
-  double2* GSd(int k) const { return reg(p->GSd, p->tsd_off[k], sq(p->Psz[k])); }
-  double2* tS(int k) const { return reg(p->tS, p->tsd_off[k], sq(p->Psz[k])); }
-  double2* TSu(int k) const { return reg(p->TSu, p->tsu_off[k], (int64_t)p->Psz[k] * p->Psz[k + 1]); }
-  double2* TSl(int k) const { return reg(p->TSl, p->tsu_off[k], (int64_t)p->Psz[k] * p->Psz[k + 1]); }
-  double2* GSu(int k) const { return reg(p->GSu, p->tsu_off[k], (int64_t)p->Psz[k] * p->Psz[k + 1]); }
-  double2* GSl(int k) const { return reg(p->GSl, p->tsu_off[k], (int64_t)p->Psz[k] * p->Psz[k + 1]); }
-  double2* XS(int k) const { return reg(p->XS, p->ts_x_off[k], (int64_t)p->Psz[k] * p->Psz[k - 1]); }
-  double2* YS(int k) const { return reg(p->YS, p->ts_x_off[k], (int64_t)p->Psz[k] * p->Psz[k - 1]); }
-  double2* RS(int k) const { return reg(p->RS, p->rs_off[k], (int64_t)p->Psz[0] * p->Psz[k]); }
-  double2* SS() const { return reg(p->SS, 0, sq(p->Pmax)); }
-
-  // C (+)= alpha A B with per-energy strides (0 = shared operand);
-  // lowp routes through the plan's precision, otherwise FP64.
-  cudaError_t mm(bool lowp, int m, int n, int k, const double2* A, int64_t sA, int lda, const double2* B,
-                 int64_t sB, int ldb, double2* Cm, int64_t sC, int ldc, double alpha, bool acc,
-                 const double2* C1 = nullptr, int64_t sC1 = 0, int ldc1 = 0) {
+  // C (+)= alpha A B over the range's energies (per-energy strides, 0 =
+  // shared operand).  kind: 0 FP64, 1 plan precision, 2 step-1 precision
+  // (FP64, or 56-bit tensor-core products on mixed plans).
+  cudaError_t mm(int kind, int m, int n, int k, const double2* A, int64_t sA, int lda, const double2* B, int64_t sB,
+                 int ldb, double2* Cm, int64_t sC, int ldc, double alpha, bool acc = false,
+                 const double2* C1 = nullptr, int64_t sC1 = 0, int ldc1 = 0, double beta1 = 1.0,
+                 const double2* dshift = nullptr) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     ZGemm g;
     g.m = m; g.n = n; g.k = k;
@@ -79,33 +183,78 @@ struct DD {
     g.B = B; g.sB = sB; g.ldb = ldb;
     g.C = Cm; g.sC = sC; g.ldc = ldc;
     g.alpha = {alpha, 0.0};
-    if (C1) { g.C1 = C1; g.sC1 = sC1; g.ldc1 = ldc1; g.beta1 = {1.0, 0.0}; }
+    if (C1) { g.C1 = C1; g.sC1 = sC1; g.ldc1 = ldc1; g.beta1 = {beta1, 0.0}; }
     else if (acc) { g.C1 = Cm; g.sC1 = sC; g.ldc1 = ldc; g.beta1 = {1.0, 0.0}; }
+    if (dshift) { g.dshift = dshift; g.sD = 1; g.gamma = {1.0, 0.0}; }
     g.batch = C;
-    return lowp ? s.gemm(g) : s.gemm64(g);
+    if (kind == 1) return s.gemm(g);
+    if (kind == 2 && p->precision == NEGF_MIXED) { g.bits = 56; return s.gemm(g); }
+    return s.gemm64(g);
   }
   cudaError_t cp(const double2* src, int64_t sSrc, int ldSrc, double2* dst, int64_t sDst, int ldDst, int rows,
                  int cols, double scale, int acc, int batch) {
     return s.misc([&] { return negf::copy2d(src, sSrc, ldSrc, dst, sDst, ldDst, rows, cols, scale, acc, batch, s.st); });
   }
-  cudaError_t eye(double2* dst, int64_t sDst, int ld, int rows, int cols, int off, int nid, int rows_mode, int batch) {
-    return s.misc([&] { return negf::set_eye(dst, sDst, ld, rows, cols, off, nid, rows_mode, batch, s.st); });
+  cudaError_t zero(double2* dst, int64_t sDst, int ld, int rows, int cols, int batch) {
+    return s.misc([&] { return negf::set_eye(dst, sDst, ld, rows, cols, 0, 0, 0, batch, s.st); });
+  }
+  cudaError_t comb(const negf_plan_s::Reg& out, int64_t n, const negf_plan_s::Reg* r0, double c0,
+                   const negf_plan_s::Reg* r1, double c1, const negf_plan_s::Reg* r2, double c2,
+                   const negf_plan_s::Reg* r3, double c3) {
+    auto ptr = [&](const negf_plan_s::Reg* r) -> const double2* { return r ? R(*r) : nullptr; };
+    auto str = [&](const negf_plan_s::Reg* r) -> int64_t { return r ? r->sz : 0; };
+    return s.misc([&] {
+      return negf::lincomb(R(out), out.sz, n, C, ptr(r0), str(r0), c0, ptr(r1), str(r1), c1, ptr(r2), str(r2), c2,
+                           ptr(r3), str(r3), c3, s.st);
+    });
+  }
+  // In-place inversion of a separator super-block (info: the separator's first layer).
+  cudaError_t inv_reg(const negf_plan_s::Reg& r, int k) {
+    return s.inv(R(r), r.sz, R(r), r.sz, p->Psz[k], C, p->dom_l[k] + 2);
   }
 
-  // Energy-independent super-blocks of M = -H between a domain's first /
-  // last w layers and its separators.
-  cudaError_t assemble_msup() {
+  // Energy-independent blocks: the fused H super-blocks of step 1 and the M
+  // super-blocks between F / L and the separators.
+  cudaError_t assemble_static() {
+    auto fused = [&](int64_t off, int r0, int nr, int c0, int nc, int rows, int cols) -> cudaError_t {
+      double2* dst = p->Hf + off;
+      NEGF_TRY(zero(dst, 0, cols, rows, cols, 1));
+      int ro = 0;
+      for (int a = r0; a < r0 + nr; ++a) {
+        int co = 0;
+        for (int c = c0; c < c0 + nc; ++c) {
+          if (std::abs(a - c) <= w) NEGF_TRY(cp(s.Hblk(a, c), 0, b(c), dst + (int64_t)ro * cols + co, 0, cols, b(a), b(c),
+                                                1.0, 0, 1));
+          co += b(c);
+        }
+        ro += b(a);
+      }
+      return cudaSuccess;
+    };
+    for (int j = 0; j < nd; ++j)
+      for (int side = 0; side < 2; ++side) {
+        const DDGroups& g = side == 0 ? p->grR[j] : p->grL[j];
+        const int K = (int)g.sz.size();
+        for (int I = 0; I < K; ++I) {
+          NEGF_TRY(fused(g.hd[I], g.first[I], g.nl[I], g.first[I], g.nl[I], g.sz[I], g.sz[I]));
+          if (I + 1 < K) {
+            NEGF_TRY(fused(g.hu[I], g.first[I], g.nl[I], g.first[I + 1], g.nl[I + 1], g.sz[I], g.sz[I + 1]));
+            NEGF_TRY(fused(g.hl[I], g.first[I + 1], g.nl[I + 1], g.first[I], g.nl[I], g.sz[I + 1], g.sz[I]));
+          }
+        }
+      }
     for (int j = 0; j < nd; ++j) {
-      const int f = p->dom_f[j], l = p->dom_l[j], F = p->Fsz[j], L = p->Lsz[j], P = p->Psz[j], P0 = Pp(j);
-      double2* MFp = p->Msup + p->mfp_off[j];
-      double2* MpF = p->Msup + p->mpf_off[j];
-      double2* MLq = p->Msup + p->mlq_off[j];
-      double2* MqL = p->Msup + p->mql_off[j];
-      NEGF_TRY(eye(MLq, 0, P, L, P, 0, 0, 0, 1));
-      NEGF_TRY(eye(MqL, 0, L, P, L, 0, 0, 0, 1));
+      const int f = p->dom_f[j], l = p->dom_l[j], F = p->Fsz[j], L = p->Lsz[j], P = p->Psz[j];
+      const int P0 = j > 0 ? p->Psz[j - 1] : 0;
+      double2* MFp = p->Hf + p->mfp_off[j];
+      double2* MpF = p->Hf + p->mpf_off[j];
+      double2* MLq = p->Hf + p->mlq_off[j];
+      double2* MqL = p->Hf + p->mql_off[j];
+      NEGF_TRY(zero(MLq, 0, P, L, P, 1));
+      NEGF_TRY(zero(MqL, 0, L, P, L, 1));
       if (P0) {
-        NEGF_TRY(eye(MFp, 0, P0, F, P0, 0, 0, 0, 1));
-        NEGF_TRY(eye(MpF, 0, F, P0, F, 0, 0, 0, 1));
+        NEGF_TRY(zero(MFp, 0, P0, F, P0, 1));
+        NEGF_TRY(zero(MpF, 0, F, P0, F, 1));
       }
       for (int r = l - w + 1; r <= l; ++r)
         for (int sl = l + 1; sl <= l + w; ++sl) {
@@ -124,235 +273,285 @@ struct DD {
     return cudaSuccess;
   }
 
-  // Step 1 of Alg. 2 for domain j: X = (M restricted to D2_j)^{-1}, its band
-  // (into the band output) and its first / last w block rows and columns
-  // (the internal halos of Sec. 3, "Data dependencies").
-  cudaError_t domain(int j) {
-    const int f = p->dom_f[j], l = p->dom_l[j], F = p->Fsz[j], L = p->Lsz[j];
-    NEGF_TRY(s.upward(true, f, l));
-    NEGF_TRY(s.downward(f, l));
-    // First w columns: X_{i,c} = -sum_{c'} Xm_{i,c'} X_{c',c}  (i > c), band values elsewhere.
-    for (int i = f; i <= l; ++i) {
-      const int lo = std::max(f, i - w);
-      for (int c = lo; c < i; ++c)
-        NEGF_TRY(mm(true, b(i), F, b(c), s.Xblk(i, c), (int64_t)b(i) * b(c), b(c), FC(c), (int64_t)b(c) * F, F,
-                    FC(i), (int64_t)b(i) * F, F, -1.0, c > lo));
-      for (int c = f; c < f + w; ++c)
-        if (c >= i) NEGF_TRY(cp(s.Gb(i, c), sG, b(c), FC(i) + offF(c), (int64_t)b(i) * F, F, b(i), b(c), 1.0, 0, C));
+  // S_I = E I - H_II (fused), minus Sigma_L on layer 0 when the group holds it.
+  cudaError_t diag_group(const DDGroups& g, int I, double2* S, int64_t sS) {
+    const int B = g.sz[I];
+    NEGF_TRY(mm(0, B, B, 0, S, sS, B, S, sS, B, S, sS, B, 1.0, false, HF(g.hd[I]), 0, B, -1.0, s.E + s.e0));
+    if (g.first[I] == 0 && s.sigL)
+      NEGF_TRY(cp(s.sigmaL(), s.sig_stride, b(0), S, sS, B, b(0), b(0), -1.0, 1, C));
+    return cudaSuccess;
+  }
+
+  // Step 1 for domain j.
+  cudaError_t corners(int j) {
+    const DDGroups& g = p->grR[j];
+    const int K = (int)g.sz.size(), F = p->Fsz[j], L = p->Lsz[j];
+    double2* S = R(p->r_lsS[j]);
+    const int64_t sS = p->r_lsS[j].sz;
+    // right-connected sweep of the closed sub-domain on groups anchored at f
+    NEGF_TRY(diag_group(g, K - 1, S, sS));
+    for (int I = K - 1; I >= 0; --I) {
+      const int B = g.sz[I];
+      NEGF_TRY(s.inv(S, sS, R(g.t[I]), g.t[I].sz, B, C, g.first[I] + 1));
+      if (I == 0) break;
+      const int Bp = g.sz[I - 1];
+      // Y_I = M_{I-1,I} t_I = -H_u t_I ; X_I = t_I M_{I,I-1} = -t_I H_l
+      NEGF_TRY(mm(2, Bp, B, B, HF(g.hu[I - 1]), 0, B, R(g.t[I]), g.t[I].sz, B, R(g.y[I]), g.y[I].sz, B, -1.0));
+      NEGF_TRY(mm(2, B, Bp, B, R(g.t[I]), g.t[I].sz, B, HF(g.hl[I - 1]), 0, Bp, R(g.x[I]), g.x[I].sz, Bp, -1.0));
+      // S_{I-1} = E I - H_{I-1,I-1} + Y_I H_l
+      NEGF_TRY(mm(2, Bp, Bp, B, R(g.y[I]), g.y[I].sz, B, HF(g.hl[I - 1]), 0, Bp, S, sS, Bp, 1.0, false,
+                  HF(g.hd[I - 1]), 0, Bp, -1.0, s.E + s.e0));
+      if (g.first[I - 1] == 0 && s.sigL)
+        NEGF_TRY(cp(s.sigmaL(), s.sig_stride, b(0), S, sS, Bp, b(0), b(0), -1.0, 1, C));
     }
-    // First w rows: X_{c,j'} = -sum_{c'} X_{c,c'} Y_{c',j'}  (j' > c), band values elsewhere.
-    for (int jj = f; jj <= l; ++jj) {
-      const int lo = std::max(f, jj - w);
-      for (int c = lo; c < jj; ++c)
-        NEGF_TRY(mm(true, F, b(jj), b(c), FR(c), (int64_t)b(c) * F, b(c), s.Yblk(c, jj), (int64_t)b(c) * b(jj), b(jj),
-                    FR(jj), (int64_t)b(jj) * F, b(jj), -1.0, c > lo));
-      for (int r = f; r < f + w; ++r)
-        if (r >= jj) NEGF_TRY(cp(s.Gb(r, jj), sG, b(jj), FR(jj) + (int64_t)offF(r) * b(jj), (int64_t)b(jj) * F, b(jj),
-                                b(r), b(jj), 1.0, 0, C));
+    // X_FF = t_0; first super-row X_{F,J} = -X_{F,J-1} Y_J and first
+    // super-column X_{J,F} = -X_J X_{J-1,F} (rings of two), the last w
+    // layers' columns / rows into X_FL / X_LF
+    const int rL = g.sz[K - 1];                 // elements of L in the last group
+    const int rP = L - rL;                      // elements of L in group K-2 (shorter last group)
+    const int64_t srow = p->r_row[j].sz, scol = p->r_col[j].sz;
+    const int64_t slotR = (int64_t)F * p->Bmax, slotC = (int64_t)p->Bmax * F;
+    auto rowp = [&](int J) -> double2* { return J == 0 ? R(g.t[0]) : R(p->r_row[j]) + (J & 1) * slotR; };
+    auto colp = [&](int J) -> double2* { return J == 0 ? R(g.t[0]) : R(p->r_col[j]) + (J & 1) * slotC; };
+    auto rows_s = [&](int J) -> int64_t { return J == 0 ? g.t[0].sz : srow; };
+    auto cols_s = [&](int J) -> int64_t { return J == 0 ? g.t[0].sz : scol; };
+    for (int J = 1; J < K; ++J) {
+      const int B = g.sz[J], Bp = g.sz[J - 1];
+      NEGF_TRY(mm(2, F, B, Bp, rowp(J - 1), rows_s(J - 1), Bp, R(g.y[J]), g.y[J].sz, B, rowp(J), rows_s(J), B, -1.0));
+      NEGF_TRY(mm(2, B, F, Bp, R(g.x[J]), g.x[J].sz, Bp, colp(J - 1), cols_s(J - 1), F, colp(J), cols_s(J), F, -1.0));
     }
-    // Last w columns: with M_D = U D L from the upward pass, X E_L =
-    // L^{-1} D^{-1} U^{-1} E_L: backward v = U^{-1} E_L, then forward.
-    for (int i = l; i >= f; --i) {
-      NEGF_TRY(eye(VT(i), (int64_t)b(i) * L, L, b(i), L, inL(i) ? offL(i) : 0, inL(i) ? b(i) : 0, 0, C));
-      for (int c = i + 1; c <= std::min(l, i + w); ++c)
-        NEGF_TRY(mm(true, b(i), L, b(c), s.Yblk(i, c), (int64_t)b(i) * b(c), b(c), VT(c), (int64_t)b(c) * L, L,
-                    VT(i), (int64_t)b(i) * L, L, -1.0, true));
+    double2* XFL = R(p->r_xfl[j]);
+    double2* XLF = R(p->r_xlf[j]);
+    NEGF_TRY(cp(rowp(K - 1), rows_s(K - 1), rL, XFL + rP, p->r_xfl[j].sz, L, F, rL, 1.0, 0, C));
+    NEGF_TRY(cp(colp(K - 1), cols_s(K - 1), F, XLF + (int64_t)rP * F, p->r_xlf[j].sz, F, rL, F, 1.0, 0, C));
+    if (rP > 0) {
+      const int Bq = g.sz[K - 2];
+      NEGF_TRY(cp(rowp(K - 2) + (Bq - rP), rows_s(K - 2), Bq, XFL, p->r_xfl[j].sz, L, F, rP, 1.0, 0, C));
+      NEGF_TRY(cp(colp(K - 2) + (int64_t)(Bq - rP) * F, cols_s(K - 2), F, XLF, p->r_xlf[j].sz, F, rP, F, 1.0, 0, C));
     }
-    for (int i = f; i <= l; ++i) {
-      NEGF_TRY(mm(true, b(i), L, b(i), s.Tblk(i), sq(b(i)), b(i), VT(i), (int64_t)b(i) * L, L, LC(i),
-                  (int64_t)b(i) * L, L, 1.0, false));
-      for (int c = std::max(f, i - w); c < i; ++c)
-        NEGF_TRY(mm(true, b(i), L, b(c), s.Xblk(i, c), (int64_t)b(i) * b(c), b(c), LC(c), (int64_t)b(c) * L, L,
-                    LC(i), (int64_t)b(i) * L, L, -1.0, true));
-    }
-    // Last w rows: E_L^T L^{-1} D^{-1} U^{-1}: backward u^T, then forward.
-    for (int i = l; i >= f; --i) {
-      NEGF_TRY(eye(VT(i), (int64_t)b(i) * L, b(i), L, b(i), inL(i) ? offL(i) : 0, inL(i) ? b(i) : 0, 1, C));
-      for (int c = i + 1; c <= std::min(l, i + w); ++c)
-        NEGF_TRY(mm(true, L, b(i), b(c), VT(c), (int64_t)b(c) * L, b(c), s.Xblk(c, i), (int64_t)b(c) * b(i), b(i),
-                    VT(i), (int64_t)b(i) * L, b(i), -1.0, true));
-    }
-    for (int i = f; i <= l; ++i) {
-      NEGF_TRY(mm(true, L, b(i), b(i), VT(i), (int64_t)b(i) * L, b(i), s.Tblk(i), sq(b(i)), b(i), LR(i),
-                  (int64_t)b(i) * L, b(i), 1.0, false));
-      for (int c = std::max(f, i - w); c < i; ++c)
-        NEGF_TRY(mm(true, L, b(i), b(c), LR(c), (int64_t)b(c) * L, b(c), s.Yblk(c, i), (int64_t)b(c) * b(i), b(i),
-                    LR(i), (int64_t)b(i) * L, b(i), -1.0, true));
-    }
-    // W_a = [X_{a,F} M_{F,p}, X_{a,L} M_{L,q}],  V_a = [M_{p,F} X_{F,a}; M_{q,L} X_{L,a}]
-    const int P = p->Psz[j], P0 = Pp(j);
-    const double2* MFp = p->Msup + p->mfp_off[j];
-    const double2* MpF = p->Msup + p->mpf_off[j];
-    const double2* MLq = p->Msup + p->mlq_off[j];
-    const double2* MqL = p->Msup + p->mql_off[j];
-    for (int a = f; a <= l; ++a) {
-      NEGF_TRY(mm(true, b(a), P, L, LC(a), (int64_t)b(a) * L, L, MLq, 0, P, Wq(a), (int64_t)b(a) * P, P, 1.0, false));
-      NEGF_TRY(mm(true, P, b(a), L, MqL, 0, L, LR(a), (int64_t)b(a) * L, b(a), Vq(a), (int64_t)b(a) * P, b(a), 1.0, false));
-      if (P0) {
-        NEGF_TRY(mm(true, b(a), P0, F, FC(a), (int64_t)b(a) * F, F, MFp, 0, P0, Wp(a), (int64_t)b(a) * P0, P0, 1.0, false));
-        NEGF_TRY(mm(true, P0, b(a), F, MpF, 0, F, FR(a), (int64_t)b(a) * F, b(a), Vp(a), (int64_t)b(a) * P0, b(a), 1.0, false));
-      }
+    // left-connected sweep on groups anchored at l: X_LL = the last group's inverse
+    const DDGroups& h = p->grL[j];
+    const int KL = (int)h.sz.size();
+    double2* Gm = R(p->r_lsG[j]);
+    double2* Ym = R(p->r_lsY[j]);
+    const int64_t sB = p->r_lsG[j].sz;
+    NEGF_TRY(diag_group(h, 0, S, sS));
+    for (int I = 0; I < KL; ++I) {
+      const int B = h.sz[I];
+      if (I == KL - 1) return s.inv(S, sS, R(p->r_xll[j]), p->r_xll[j].sz, B, C, h.first[I] + 1);
+      NEGF_TRY(s.inv(S, sS, Gm, sB, B, C, h.first[I] + 1));
+      const int Bn = h.sz[I + 1];
+      // Y = M_{I+1,I} g_I = -H_l g_I ; S_{I+1} = E I - H_{I+1,I+1} + Y H_u
+      NEGF_TRY(mm(2, Bn, B, B, HF(h.hl[I]), 0, B, Gm, sB, B, Ym, sB, B, -1.0));
+      NEGF_TRY(mm(2, Bn, Bn, B, Ym, sB, B, HF(h.hu[I]), 0, Bn, S, sS, Bn, 1.0, false, HF(h.hd[I + 1]), 0, Bn, -1.0,
+                  s.E + s.e0));
+      if (h.first[I + 1] == 0 && s.sigL)
+        NEGF_TRY(cp(s.sigmaL(), s.sig_stride, b(0), S, sS, Bn, b(0), b(0), -1.0, 1, C));
     }
     return cudaSuccess;
   }
 
-  // Step 2 (Eq. Schur_complement_in_parallel_DDRGF): T_S = T11 - T12 X T21,
-  // block tridiagonal over the separators (Prop. 4), in FP64.
-  cudaError_t schur() {
+  // Steps 2-3 (FP64): T_S pieces per separator, the left- and right-connected
+  // sweeps over the separators, and the separator diagonals of T_S^{-1}.
+  cudaError_t interface() {
     const int N = p->N;
     for (int k = 0; k < nd; ++k) {
-      const int P = p->Psz[k], s0 = p->dom_l[k] + 1;
-      NEGF_TRY(eye(TSd(k), sq(P), P, P, P, 0, 0, 0, C));
+      const int P = p->Psz[k], s0 = p->dom_l[k] + 1, Lk = p->Lsz[k];
+      double2* A = R(p->r_A[k]);
+      const int64_t sP = p->r_A[k].sz;
+      // A_k = E I - H_PP (- Sigma_R on the last layer)
+      NEGF_TRY(zero(A, sP, P, P, P, C));
       for (int a = s0; a < s0 + w; ++a)
         for (int c = s0; c < s0 + w; ++c)
-          NEGF_TRY(cp(s.Hblk(a, c), 0, b(c), TSd(k) + (int64_t)p->off_in[a] * P + p->off_in[c], sq(P), P, b(a), b(c),
-                      -1.0, 0, C));
-      NEGF_TRY(s.misc([&] { return negf::add_diag(TSd(k), sq(P), P, P, s.E + s.e0, 1, 1.0, C, s.st); }));
-      if (s0 + w - 1 == N - 1 && s.sigR) {
-        const int sl = N - 1;
-        NEGF_TRY(cp(s.sigmaR(), s.sig_stride, b(sl), TSd(k) + (int64_t)p->off_in[sl] * P + p->off_in[sl], sq(P), P,
-                    b(sl), b(sl), -1.0, 1, C));
-      }
-      // - M[p_k, L_k] X^(k)[L_k, L_k] M[L_k, p_k]
-      const int Lk = p->Lsz[k];
-      const double2* MqL = p->Msup + p->mql_off[k];
-      for (int r = p->dom_l[k] - w + 1; r <= p->dom_l[k]; ++r)
-        NEGF_TRY(mm(false, P, P, b(r), MqL + offL(r), 0, Lk, Wq(r), (int64_t)b(r) * P, P, TSd(k), sq(P), P, -1.0, true));
+          NEGF_TRY(cp(s.Hblk(a, c), 0, b(c), A + (int64_t)p->off_in[a] * P + p->off_in[c], sP, P, b(a), b(c), -1.0, 0, C));
+      NEGF_TRY(s.misc([&] { return negf::add_diag(A, sP, P, P, s.E + s.e0, 1, 1.0, C, s.st); }));
+      if (s0 + w - 1 == N - 1 && s.sigR)
+        NEGF_TRY(cp(s.sigmaR(), s.sig_stride, b(N - 1), A + (int64_t)p->off_in[N - 1] * P + p->off_in[N - 1], sP, P,
+                    b(N - 1), b(N - 1), -1.0, 1, C));
+      double2* T = R(p->r_tmp[k]);
+      const int64_t sT = p->r_tmp[k].sz;
+      const double2* MqL = HF(p->mql_off[k]);
+      const double2* MLq = HF(p->mlq_off[k]);
+      // cL_k = M_{P,L} X_LL M_{L,P} (sub-domain k, left of separator k)
+      NEGF_TRY(mm(0, P, Lk, Lk, MqL, 0, Lk, R(p->r_xll[k]), p->r_xll[k].sz, Lk, T, sT, Lk, 1.0));
+      NEGF_TRY(mm(0, P, P, Lk, T, sT, Lk, MLq, 0, P, R(p->r_cL[k]), sP, P, 1.0));
       if (k + 1 < nd) {
         const int j = k + 1, F = p->Fsz[j], L = p->Lsz[j], P1 = p->Psz[j];
-        const double2* MpF = p->Msup + p->mpf_off[j];
-        const double2* MqL1 = p->Msup + p->mql_off[j];
-        bool first_u = true, first_l = true;
-        for (int r = p->dom_f[j]; r < p->dom_f[j] + w; ++r) {
-          // - M[p_k, F] X[F, F] M[F, p_k]  and  T_S[p_k, p_{k+1}] = - M[p_k, F] X[F, L] M[L, p_{k+1}]
-          NEGF_TRY(mm(false, P, P, b(r), MpF + offF(r), 0, F, Wp(r), (int64_t)b(r) * P, P, TSd(k), sq(P), P, -1.0, true));
-          NEGF_TRY(mm(false, P, P1, b(r), MpF + offF(r), 0, F, Wq(r), (int64_t)b(r) * P1, P1, TSu(k),
-                      (int64_t)P * P1, P1, -1.0, !first_u));
-          first_u = false;
-        }
-        for (int r = p->dom_l[j] - w + 1; r <= p->dom_l[j]; ++r) {
-          // T_S[p_{k+1}, p_k] = - M[p_{k+1}, L] X[L, F] M[F, p_k]
-          NEGF_TRY(mm(false, P1, P, b(r), MqL1 + offL(r), 0, L, Wp(r), (int64_t)b(r) * P, P, TSl(k), (int64_t)P * P1, P,
-                      -1.0, !first_l));
-          first_l = false;
-        }
+        const double2* MpF = HF(p->mpf_off[j]);
+        const double2* MFp = HF(p->mfp_off[j]);
+        // cR_k = M_{P,F} X_FF M_{F,P} (sub-domain k + 1, right of separator k)
+        NEGF_TRY(mm(0, P, F, F, MpF, 0, F, R(p->grR[j].t[0]), p->grR[j].t[0].sz, F, T, sT, F, 1.0));
+        NEGF_TRY(mm(0, P, P, F, T, sT, F, MFp, 0, P, R(p->r_cR[k]), sP, P, 1.0));
+        // T_S[k, k+1] = -M_{P_k,F} X_FL M_{L,P_{k+1}},  T_S[k+1, k] = -M_{P_{k+1},L} X_LF M_{F,P_k}
+        NEGF_TRY(mm(0, P, L, F, MpF, 0, F, R(p->r_xfl[j]), p->r_xfl[j].sz, L, T, sT, L, 1.0));
+        NEGF_TRY(mm(0, P, P1, L, T, sT, L, HF(p->mlq_off[j]), 0, P1, R(p->r_Tu[k]), p->r_Tu[k].sz, P1, -1.0));
+        NEGF_TRY(mm(0, P1, F, L, HF(p->mql_off[j]), 0, L, R(p->r_xlf[j]), p->r_xlf[j].sz, F, T, sT, F, 1.0));
+        NEGF_TRY(mm(0, P1, P, F, T, sT, F, MFp, 0, P, R(p->r_Tl[k]), p->r_Tl[k].sz, P, -1.0));
       }
+      // base_k = A_k - cL_k - cR_k (the diagonal of T_S)
+      const int64_t P2 = sq(P);
+      NEGF_TRY(comb(p->r_base[k], P2, &p->r_A[k], 1.0, &p->r_cL[k], -1.0, k + 1 < nd ? &p->r_cR[k] : nullptr, -1.0,
+                    nullptr, 0.0));
     }
-    return cudaSuccess;
-  }
-
-  // Step 3: b3diag(T_S^{-1}) by block tridiagonal RGF (Alg. 1) in FP64, and
-  // the first super-row of T_S^{-1} when G_1N is wanted.
-  cudaError_t interface(bool want_row) {
-    const int n = nd;
-    const int64_t sSS = sq(p->Pmax);
-    NEGF_TRY(cp(TSd(n - 1), sq(p->Psz[n - 1]), p->Psz[n - 1], SS(), sSS, p->Psz[n - 1], p->Psz[n - 1], p->Psz[n - 1],
-                1.0, 0, C));
-    for (int k = n - 1; k >= 0; --k) {
+    // left-connected sweep over the separators
+    for (int k = 0; k < nd; ++k) {
       const int P = p->Psz[k];
-      NEGF_TRY(s.inv(SS(), sSS, tS(k), sq(P), P, C, p->dom_l[k] + 2));
-      if (k == 0) break;
-      const int P0 = p->Psz[k - 1];
-      NEGF_TRY(mm(false, P0, P, P, TSu(k - 1), (int64_t)P0 * P, P, tS(k), sq(P), P, YS(k), (int64_t)P0 * P, P, 1.0, false));
-      NEGF_TRY(mm(false, P, P0, P, tS(k), sq(P), P, TSl(k - 1), (int64_t)P0 * P, P0, XS(k), (int64_t)P0 * P, P0, 1.0, false));
-      NEGF_TRY(mm(false, P0, P0, P, YS(k), (int64_t)P0 * P, P, TSl(k - 1), (int64_t)P0 * P, P0, SS(), sSS, P0, -1.0, false,
-                  TSd(k - 1), sq(P0), P0));
+      const int64_t P2 = sq(P);
+      const negf_plan_s::Reg* LLk = nullptr;
+      if (k > 0) {   // LL_k = T_S[k,k-1] gLin_{k-1} T_S[k-1,k]
+        const int Pm = p->Psz[k - 1];
+        double2* T = R(p->r_itL);
+        NEGF_TRY(mm(0, P, Pm, Pm, R(p->r_Tl[k - 1]), p->r_Tl[k - 1].sz, Pm, R(p->r_gLin[k - 1]), p->r_gLin[k - 1].sz, Pm,
+                    T, p->r_itL.sz, Pm, 1.0));
+        NEGF_TRY(mm(0, P, P, Pm, T, p->r_itL.sz, Pm, R(p->r_Tu[k - 1]), p->r_Tu[k - 1].sz, P, R(p->r_LL[k]),
+                    p->r_LL[k].sz, P, 1.0));
+        LLk = &p->r_LL[k];
+      }
+      if (k + 1 < nd) {
+        NEGF_TRY(comb(p->r_gLin[k], P2, &p->r_base[k], 1.0, LLk, -1.0, nullptr, 0.0, nullptr, 0.0));
+        NEGF_TRY(inv_reg(p->r_gLin[k], k));
+        NEGF_TRY(comb(p->r_gLs[k], P2, &p->r_A[k], 1.0, &p->r_cL[k], -1.0, LLk, -1.0, nullptr, 0.0));
+        NEGF_TRY(inv_reg(p->r_gLs[k], k));
+      }
     }
-    NEGF_TRY(cp(tS(0), sq(p->Psz[0]), p->Psz[0], GSd(0), sq(p->Psz[0]), p->Psz[0], p->Psz[0], p->Psz[0], 1.0, 0, C));
-    for (int k = 1; k < n; ++k) {
-      const int P = p->Psz[k], P0 = p->Psz[k - 1];
-      NEGF_TRY(mm(false, P0, P, P0, GSd(k - 1), sq(P0), P0, YS(k), (int64_t)P0 * P, P, GSu(k - 1), (int64_t)P0 * P, P,
-                  -1.0, false));
-      NEGF_TRY(mm(false, P, P0, P0, XS(k), (int64_t)P0 * P, P0, GSd(k - 1), sq(P0), P0, GSl(k - 1), (int64_t)P0 * P, P0,
-                  -1.0, false));
-      NEGF_TRY(mm(false, P, P, P0, XS(k), (int64_t)P0 * P, P0, GSu(k - 1), (int64_t)P0 * P, P, GSd(k), sq(P), P, -1.0,
-                  false, tS(k), sq(P), P));
+    // right-connected sweep over the separators, and the diagonals of T_S^{-1}
+    for (int k = nd - 1; k >= 0; --k) {
+      const int P = p->Psz[k];
+      const int64_t P2 = sq(P);
+      const negf_plan_s::Reg* RRk = nullptr;
+      if (k + 1 < nd) {   // RR_k = T_S[k,k+1] gRin_{k+1} T_S[k+1,k]
+        const int Pn = p->Psz[k + 1];
+        double2* T = R(p->r_itR);
+        NEGF_TRY(mm(0, P, Pn, Pn, R(p->r_Tu[k]), p->r_Tu[k].sz, Pn, R(p->r_gRin[k + 1]), p->r_gRin[k + 1].sz, Pn, T,
+                    p->r_itR.sz, Pn, 1.0));
+        NEGF_TRY(mm(0, P, P, Pn, T, p->r_itR.sz, Pn, R(p->r_Tl[k]), p->r_Tl[k].sz, P, R(p->r_RR[k]), p->r_RR[k].sz, P,
+                    1.0));
+        RRk = &p->r_RR[k];
+      }
+      if (k > 0) {
+        NEGF_TRY(comb(p->r_gRin[k], P2, &p->r_base[k], 1.0, RRk, -1.0, nullptr, 0.0, nullptr, 0.0));
+        NEGF_TRY(inv_reg(p->r_gRin[k], k));
+      }
+      NEGF_TRY(comb(p->r_gRs[k], P2, &p->r_A[k], 1.0, k + 1 < nd ? &p->r_cR[k] : nullptr, -1.0, RRk, -1.0, nullptr, 0.0));
+      NEGF_TRY(inv_reg(p->r_gRs[k], k));
+      NEGF_TRY(comb(p->r_Gpp[k], P2, &p->r_base[k], 1.0, k > 0 ? &p->r_LL[k] : nullptr, -1.0, RRk, -1.0, nullptr, 0.0));
+      NEGF_TRY(inv_reg(p->r_Gpp[k], k));
     }
-    if (want_row) {
-      const int P0 = p->Psz[0];
-      NEGF_TRY(cp(GSd(0), sq(P0), P0, RS(0), sq(P0), P0, P0, P0, 1.0, 0, C));
-      for (int k = 1; k < n; ++k) {
-        const int P = p->Psz[k], Pq = p->Psz[k - 1];
-        NEGF_TRY(mm(false, P0, P, Pq, RS(k - 1), (int64_t)P0 * Pq, Pq, YS(k), (int64_t)Pq * P, P, RS(k), (int64_t)P0 * P,
-                    P, -1.0, false));
+    return cudaSuccess;
+  }
+
+  // Step 4 for domain j: boundary self-energies, the open sub-domain's RGF
+  // into the band, and the band blocks between the sub-domain and its
+  // separators.  For j = 0 with want_row, also G_{1,P_0} (into r_g1 slot 0).
+  cudaError_t open_domain(int j, bool want_row) {
+    const int f = p->dom_f[j], l = p->dom_l[j], F = p->Fsz[j], L = p->Lsz[j], P = p->Psz[j];
+    const int P0 = j > 0 ? p->Psz[j - 1] : 0;
+    double2* WR = R(p->r_wr[j]);
+    double2* VR = R(p->r_vr[j]);
+    double2* SR = R(p->r_sr[j]);
+    const int64_t sWR = p->r_wr[j].sz, sVR = p->r_vr[j].sz, sSR = p->r_sr[j].sz;
+    // W_R = M_{L,P} gR_P, V_R = gR_P M_{P,L}, Sigma_right = W_R M_{P,L}
+    NEGF_TRY(mm(0, L, P, P, HF(p->mlq_off[j]), 0, P, R(p->r_gRs[j]), p->r_gRs[j].sz, P, WR, sWR, P, 1.0));
+    NEGF_TRY(mm(0, P, L, P, R(p->r_gRs[j]), p->r_gRs[j].sz, P, HF(p->mql_off[j]), 0, L, VR, sVR, L, 1.0));
+    NEGF_TRY(mm(0, L, L, P, WR, sWR, P, HF(p->mql_off[j]), 0, L, SR, sSR, L, 1.0));
+    double2 *WL = nullptr, *VL = nullptr, *SL = nullptr;
+    const int64_t sWL = p->r_wl[j].sz, sVL = p->r_vl[j].sz, sSL = p->r_sl[j].sz;
+    if (j > 0) {   // W_L = M_{F,p} gL_p, V_L = gL_p M_{p,F}, Sigma_left = W_L M_{p,F}
+      WL = R(p->r_wl[j]); VL = R(p->r_vl[j]); SL = R(p->r_sl[j]);
+      NEGF_TRY(mm(0, F, P0, P0, HF(p->mfp_off[j]), 0, P0, R(p->r_gLs[j - 1]), p->r_gLs[j - 1].sz, P0, WL, sWL, P0, 1.0));
+      NEGF_TRY(mm(0, P0, F, P0, R(p->r_gLs[j - 1]), p->r_gLs[j - 1].sz, P0, HF(p->mpf_off[j]), 0, F, VL, sVL, F, 1.0));
+      NEGF_TRY(mm(0, F, F, P0, WL, sWL, P0, HF(p->mpf_off[j]), 0, F, SL, sSL, F, 1.0));
+    }
+    s.xr = SR; s.xr_s = sSR; s.xr_ld = L; s.xr_f = l - w + 1;
+    s.xl = SL; s.xl_s = sSL; s.xl_ld = F; s.xl_f = j > 0 ? f : -1;
+    NEGF_TRY(s.upward(true, f, l));
+    NEGF_TRY(s.downward(f, l));
+    s.xr = s.xl = nullptr;
+    // blocks between L and the right separator:
+    //   G_{a,s} = -sum_{c in L} G_{a,c} W_R[c, s],  G_{s,a} = -sum_{c in L} V_R[s, c] G_{c,a}
+    for (int a = l - w + 1; a <= l; ++a)
+      for (int sl = l + 1; sl <= l + w; ++sl) {
+        if (sl - a > w) continue;
+        bool first = true;
+        for (int c = l - w + 1; c <= l; ++c) {
+          NEGF_TRY(mm(1, b(a), b(sl), b(c), s.Gb(a, c), sG, b(c), WR + (int64_t)offL(c) * P + p->off_in[sl], sWR, P,
+                      s.Gb(a, sl), sG, b(sl), -1.0, !first));
+          NEGF_TRY(mm(1, b(sl), b(a), b(c), VR + (int64_t)p->off_in[sl] * L + offL(c), sVR, L, s.Gb(c, a), sG, b(a),
+                      s.Gb(sl, a), sG, b(a), -1.0, !first));
+          first = false;
+        }
+      }
+    if (j > 0)   // blocks between F and the left separator
+      for (int a = f; a < f + w; ++a)
+        for (int sl = f - w; sl < f; ++sl) {
+          if (a - sl > w) continue;
+          bool first = true;
+          for (int c = f; c < f + w; ++c) {
+            NEGF_TRY(mm(1, b(a), b(sl), b(c), s.Gb(a, c), sG, b(c), WL + (int64_t)offF(c) * P0 + p->off_in[sl], sWL, P0,
+                        s.Gb(a, sl), sG, b(sl), -1.0, !first));
+            NEGF_TRY(mm(1, b(sl), b(a), b(c), VL + (int64_t)p->off_in[sl] * F + offF(c), sVL, F, s.Gb(c, a), sG, b(a),
+                        s.Gb(sl, a), sG, b(a), -1.0, !first));
+            first = false;
+          }
+        }
+    if (j == 0 && want_row) {
+      // first row inside D2_0 (Eq. 4x4_exact_RGF first row, with this
+      // sub-domain's open multipliers), then G_{1,P_0} = -sum_{c in L} G_{1,c} W_R[c, :]
+      const int b0 = b(0);
+      NEGF_TRY(s.misc([&] { return negf::copy_blocks(s.Tblk(0), sq(b0), s.Rblk(0), s.sR(0), sq(b0), C, s.st); }));
+      for (int jj = 1; jj <= l; ++jj) {
+        const int lo = std::max(0, jj - w);
+        for (int c = lo; c < jj; ++c)
+          NEGF_TRY(mm(1, b0, b(jj), b(c), s.Rblk(c), s.sR(c), b(c), s.Yblk(c, jj), (int64_t)b(c) * b(jj), b(jj),
+                      s.Rblk(jj), s.sR(jj), b(jj), -1.0, c > lo));
+      }
+      double2* g0 = R(p->r_g1);
+      const int64_t sg = p->r_g1.sz;
+      bool first = true;
+      for (int c = l - w + 1; c <= l; ++c) {
+        NEGF_TRY(mm(1, b0, P, b(c), s.Rblk(c), s.sR(c), b(c), WR + (int64_t)offL(c) * P, sWR, P, g0, sg, P, -1.0, !first));
+        first = false;
       }
     }
     return cudaSuccess;
   }
 
-  // Step 4: the band of Eq. 2x2_explicit_inverse_parallel_DDRGF around domain j.
-  cudaError_t stitch(int j) {
-    const int f = p->dom_f[j], l = p->dom_l[j], P = p->Psz[j], P0 = Pp(j);
-    const double2* Gqq = GSd(j);
-    const double2* Gpp = j > 0 ? GSd(j - 1) : nullptr;
-    const double2* Gpq = j > 0 ? GSu(j - 1) : nullptr;   // P0 x P
-    const double2* Gqp = j > 0 ? GSl(j - 1) : nullptr;   // P x P0
-    const int64_t sPP = sq(P), sP0 = sq(P0), sX = (int64_t)P0 * P;
-    for (int a = f; a <= l; ++a) {   // Z_a = Gamma_S V_a
-      NEGF_TRY(mm(true, P, b(a), P, Gqq, sPP, P, Vq(a), (int64_t)b(a) * P, b(a), Zq(a), (int64_t)b(a) * P, b(a), 1.0, false));
-      if (P0) {
-        NEGF_TRY(mm(true, P, b(a), P0, Gqp, sX, P0, Vp(a), (int64_t)b(a) * P0, b(a), Zq(a), (int64_t)b(a) * P, b(a), 1.0, true));
-        NEGF_TRY(mm(true, P0, b(a), P0, Gpp, sP0, P0, Vp(a), (int64_t)b(a) * P0, b(a), Zp(a), (int64_t)b(a) * P0, b(a), 1.0,
-                    false));
-        NEGF_TRY(mm(true, P0, b(a), P, Gpq, sX, P, Vq(a), (int64_t)b(a) * P, b(a), Zp(a), (int64_t)b(a) * P0, b(a), 1.0, true));
-      }
+  // Separator band blocks from the diagonals of T_S^{-1}.
+  cudaError_t separators() {
+    for (int k = 0; k < nd; ++k) {
+      const int P = p->Psz[k], s0 = p->dom_l[k] + 1;
+      for (int a = s0; a < s0 + w; ++a)
+        for (int c = s0; c < s0 + w; ++c)
+          NEGF_TRY(cp(R(p->r_Gpp[k]) + (int64_t)p->off_in[a] * P + p->off_in[c], p->r_Gpp[k].sz, P, s.Gb(a, c), sG, b(c),
+                      b(a), b(c), 1.0, 0, C));
     }
-    for (int a = f; a <= l; ++a)     // G_ab = X_ab + W_a Gamma_S V_b
-      for (int c = std::max(f, a - w); c <= std::min(l, a + w); ++c) {
-        NEGF_TRY(mm(true, b(a), b(c), P, Wq(a), (int64_t)b(a) * P, P, Zq(c), (int64_t)b(c) * P, b(c), s.Gb(a, c), sG, b(c),
-                    1.0, true));
-        if (P0)
-          NEGF_TRY(mm(true, b(a), b(c), P0, Wp(a), (int64_t)b(a) * P0, P0, Zp(c), (int64_t)b(c) * P0, b(c), s.Gb(a, c), sG,
-                      b(c), 1.0, true));
-      }
-    // blocks between the domain and its separators: G_{a,s} = -W_a Gamma_S[:, s], G_{s,a} = -Gamma_S[s, :] V_a
-    for (int a = f; a <= l; ++a)
-      for (int sl = a - w; sl <= a + w; ++sl) {
-        if (sl < 0 || sl >= p->N || p->sep_of[sl] < 0) continue;
-        const bool right = p->sep_of[sl] == j;
-        const int o = p->off_in[sl];
-        // column s of Gamma_S restricted to the q and p super-rows
-        const double2* qcol = right ? Gqq + o : Gqp + o;          // q super-row
-        const int ldq = right ? P : P0;
-        const int64_t sq_ = right ? sPP : sX;
-        NEGF_TRY(mm(true, b(a), b(sl), P, Wq(a), (int64_t)b(a) * P, P, qcol, sq_, ldq, s.Gb(a, sl), sG, b(sl), -1.0, false));
-        if (P0) {
-          const double2* pcol = right ? Gpq + o : Gpp + o;        // p super-row
-          const int ldp = right ? P : P0;
-          const int64_t sp_ = right ? sX : sP0;
-          NEGF_TRY(mm(true, b(a), b(sl), P0, Wp(a), (int64_t)b(a) * P0, P0, pcol, sp_, ldp, s.Gb(a, sl), sG, b(sl), -1.0, true));
-        }
-        // row s of Gamma_S restricted to the q and p super-columns
-        const double2* qrow = right ? Gqq + (int64_t)o * P : Gpq + (int64_t)o * P;
-        const int64_t sqr = right ? sPP : sX;
-        NEGF_TRY(mm(true, b(sl), b(a), P, qrow, sqr, P, Vq(a), (int64_t)b(a) * P, b(a), s.Gb(sl, a), sG, b(a), -1.0, false));
-        if (P0) {
-          const double2* prow = right ? Gqp + (int64_t)o * P0 : Gpp + (int64_t)o * P0;
-          const int64_t spr = right ? sX : sP0;
-          NEGF_TRY(mm(true, b(sl), b(a), P0, prow, spr, P0, Vp(a), (int64_t)b(a) * P0, b(a), s.Gb(sl, a), sG, b(a), -1.0, true));
-        }
-      }
-    // separator band blocks (right separator of this domain): G_S itself
-    const int s0 = l + 1;
-    for (int a = s0; a < s0 + w; ++a)
-      for (int c = s0; c < s0 + w; ++c)
-        NEGF_TRY(cp(GSd(j) + (int64_t)p->off_in[a] * P + p->off_in[c], sPP, P, s.Gb(a, c), sG, b(c), b(a), b(c), 1.0, 0, C));
     return cudaSuccess;
   }
 
-  // G_1N = G_{1,N}: layer 1 is in D2_1 and layer N in the last separator:
-  // G_{1,N} = -W_1 (T_S^{-1})_{p_1, p_n}[:, N].
+  // G_1N: G_{1,P_k} = -G_{1,P_{k-1}} T_S[k-1,k] gR_k through the separators
+  // (first-row relation of the chain reduced to D2_0 and the separators),
+  // then the columns of layer N.
   cudaError_t g1n(double2* out, int64_t sOut) {
-    const int N = p->N, P0 = p->Psz[0], Pn = p->Psz[nd - 1];
-    return mm(true, b(0), b(N - 1), P0, Wq(0), (int64_t)b(0) * P0, P0, RS(nd - 1) + p->off_in[N - 1],
-              (int64_t)P0 * Pn, Pn, out, sOut, b(N - 1), -1.0, false);
+    const int N = p->N, b0 = b(0);
+    const int64_t slot = (int64_t)b0 * p->Pmax, sg = p->r_g1.sz;
+    double2* base = R(p->r_g1);
+    double2* T = R(p->r_g1t);
+    int cur = 0;
+    for (int k = 1; k < nd; ++k) {
+      const int Pm = p->Psz[k - 1], P = p->Psz[k];
+      NEGF_TRY(mm(0, b0, P, Pm, base + cur * slot, sg, Pm, R(p->r_Tu[k - 1]), p->r_Tu[k - 1].sz, P, T, p->r_g1t.sz, P, 1.0));
+      NEGF_TRY(mm(0, b0, P, P, T, p->r_g1t.sz, P, R(p->r_gRin[k]), p->r_gRin[k].sz, P, base + (1 - cur) * slot, sg, P,
+                  -1.0));
+      cur = 1 - cur;
+    }
+    const int Pn = p->Psz[nd - 1];
+    return cp(base + cur * slot + p->off_in[N - 1], sg, Pn, out, sOut, b(N - 1), b0, b(N - 1), 1.0, 0, C);
   }
 
   // Runs f(dd_j, j) for every sub-domain j concurrently: domain j of this
   // energy group on its own stream (graph branch), joined back afterwards.
   // Each domain sweeps in its own Schur-window slots; everything else a
-  // domain writes (its layers' halos, W / V / Z, band blocks next to its
-  // separators) is disjoint from the other domains'.
+  // domain writes is disjoint from the other domains'.
   template <class F>
   cudaError_t for_domains(F f) {
     const int g = s.grp;
@@ -377,10 +576,14 @@ struct DD {
   }
 
   cudaError_t run(bool want_band, double2* g1n_out, int64_t s1) {
-    NEGF_TRY(for_domains([&](DD& d, int j) { return d.domain(j); }));
-    NEGF_TRY(schur());
-    NEGF_TRY(interface(g1n_out != nullptr));
-    if (want_band) NEGF_TRY(for_domains([&](DD& d, int j) { return d.stitch(j); }));
+    NEGF_TRY(for_domains([&](DD& d, int j) { return d.corners(j); }));
+    NEGF_TRY(interface());
+    if (want_band) {
+      NEGF_TRY(for_domains([&](DD& d, int j) { return d.open_domain(j, j == 0 && g1n_out != nullptr); }));
+      NEGF_TRY(separators());
+    } else {
+      NEGF_TRY(open_domain(0, true));
+    }
     if (g1n_out) NEGF_TRY(g1n(g1n_out, s1));
     return cudaSuccess;
   }

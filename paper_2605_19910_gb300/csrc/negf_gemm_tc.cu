@@ -36,6 +36,8 @@
 // complex columns.  Operands use the K-major, non-swizzled canonical layout
 // (8-row x 16-byte core matrices).  One thread issues the MMAs; completion is
 // tracked with an mbarrier whose wait is bounded.
+#include <type_traits>
+
 #include "negf_common.cuh"
 #include "negf_kernels.h"
 
@@ -107,6 +109,59 @@ __device__ __forceinline__ u64 fixed_abs(u64 u, int e_scale, int frac_bits) {
 // BF16 bits of the small integer v (< 256): exact through FP32 (2^23 + v), sign added after
 __device__ __forceinline__ uint32_t bf16_of_small(uint32_t v) {
   return __float_as_uint(__uint_as_float(0x4B000000u | v) - 8388608.0f) >> 16;
+}
+
+// |x| * 2^(frac_bits - e_scale) truncated, for frac_bits <= 32: the result
+// fits 32 bits.  With |x| < 2^e_scale the right shift of the 53-bit mantissa
+// is k = 1075 - be - frac_bits + e_scale >= 21.
+__device__ __forceinline__ uint32_t fixed32(u64 u, int e_scale, int frac_bits) {
+  const int be = (int)((u >> 52) & 0x7FF);
+  const int k = 1075 - be - frac_bits + e_scale;
+  const uint32_t lo = (uint32_t)u, hi = ((uint32_t)(u >> 32) & 0xFFFFFu) | 0x100000u;
+  if (be == 0 || k >= 53) return 0u;
+  return k >= 32 ? hi >> (k - 32) : __funnelshift_r(lo, hi, k);
+}
+
+// FP32 bits of the small integer in byte `bidx` of x (2^23 + byte - 2^23, exact):
+// one byte permute builds 0x4B0000bb, one FP32 subtraction gives the value.
+template <int BIDX>
+__device__ __forceinline__ uint32_t f32_of_byte(uint32_t x) {
+  return __float_as_uint(__uint_as_float(__byte_perm(x, 0x4B000000u, 0x7440u | BIDX)) - 8388608.0f);
+}
+__device__ __forceinline__ uint32_t f32_of_byte_rt(uint32_t x, int bidx) {
+  return __float_as_uint(__uint_as_float(__byte_perm(x, 0x4B000000u, 0x7440u | (uint32_t)bidx)) - 8388608.0f);
+}
+// FP32 bits of the s-bit field at bit `sh` of the 64-bit value (hi:lo).
+__device__ __forceinline__ uint32_t f32_of_field(uint32_t lo, uint32_t hi, int sh, uint32_t mask) {
+  const uint32_t v = sh >= 32 ? hi >> (sh - 32) : __funnelshift_r(lo, hi, sh);
+  return __float_as_uint(__uint_as_float((v & mask) | 0x4B000000u) - 8388608.0f);
+}
+// Two FP32 integers -> one word of two BF16 (their high halves), with signs.
+__device__ __forceinline__ uint32_t pack_bf16x2(uint32_t f0, uint32_t f1, uint32_t signs) {
+  return __byte_perm(f0, f1, 0x7632u) | signs;
+}
+// BF16 sign bits of elements 2h, 2h+1 of an 8-element sign mask.
+__device__ __forceinline__ uint32_t pair_signs(uint32_t smask8, int h) {
+  return (((smask8 >> (2 * h)) & 1u) << 15) | (((smask8 >> (2 * h + 1)) & 1u) << 31);
+}
+
+// T += (-1)^neg * x exactly on the integer grid of unit 2^E (x: FP64 bits),
+// truncating the bits of x below 2^E (below the product's own resolution).
+// Returns false where the integer grid cannot hold the sum (x more than
+// 2^DMAX units above the grid's range, or a non-finite x): the caller then
+// adds in floating point.
+template <class Acc, int DMAX>
+__device__ __forceinline__ bool grid_add(Acc& T, u64 x, bool neg, int E) {
+  const int be = (int)((x >> 52) & 0x7FF);
+  if (be == 0) return true;                          // zero (or a negligible denormal)
+  if (be == 0x7FF) return false;
+  const u64 m = (x & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int d = be - 1075 - E;
+  if (d > DMAX) return false;
+  Acc v = d >= 0 ? ((Acc)m << d) : (d > -64 ? (Acc)(m >> (-d)) : (Acc)0);
+  if (((x >> 63) != 0) != neg) v = -v;
+  T += v;
+  return true;
 }
 
 // Signed 64-bit integer T times 2^e2 as IEEE double bits (round to nearest even)
@@ -263,11 +318,54 @@ __device__ __forceinline__ long long acc_int(uint32_t bits) {
   return (long long)__float2int_rn(__uint_as_float(bits));
 }
 
-// WIDE: products longer than 64-bit level combination allows.  Every build
-// is held to 64 registers so that four CTAs fit an SM.  BC: op(B) = B^H.
-template <bool WIDE, bool BC>
+// Slices of 8 consecutive K values of one operand row (A) or column (B):
+// for each slice l, 4 words of two BF16 digits with the values' signs.
+// S8: 8-bit slices of a 32-bit fixed-point value (a byte permute per digit);
+// otherwise s-bit fields of a 64-bit fixed-point value (a funnel shift per
+// digit).
+template <bool S8>
+struct Digits8 {
+  uint32_t lo[8], hi[8];
+  uint32_t sgn = 0;
+  __device__ __forceinline__ void load(const u64* v, int e_scale, int frac) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (S8) {
+        lo[j] = fixed32(v[j], e_scale, frac);
+        hi[j] = 0u;
+      } else {
+        const u64 f = fixed_abs(v[j], e_scale, frac);
+        lo[j] = (uint32_t)f;
+        hi[j] = (uint32_t)(f >> 32);
+      }
+      sgn |= (uint32_t)(v[j] >> 63) << j;
+    }
+  }
+  // digit l (0 = most significant) of all 8 values as 4 packed words
+  __device__ __forceinline__ void slice(int l, int s, int L, uint32_t smask, uint32_t* out) const {
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      uint32_t f0, f1;
+      if (S8) {
+        f0 = f32_of_byte_rt(lo[2 * h], L - 1 - l);
+        f1 = f32_of_byte_rt(lo[2 * h + 1], L - 1 - l);
+      } else {
+        const int sh = s * (L - 1 - l);
+        f0 = f32_of_field(lo[2 * h], hi[2 * h], sh, smask);
+        f1 = f32_of_field(lo[2 * h + 1], hi[2 * h + 1], sh, smask);
+      }
+      out[h] = pack_bf16x2(f0, f1, pair_signs(sgn, h));
+    }
+  }
+};
+
+// S8: 8-bit slices of products up to 32 bits.  WIDE: products longer than
+// the 64-bit level combination allows.  Every build is held to 64 registers
+// so that four CTAs fit an SM.  BC: op(B) = B^H.
+template <bool S8, bool WIDE, bool BC>
 __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
   using CK = Chunk<16>;
+  using Acc = typename std::conditional<WIDE, __int128, long long>::type;
   constexpr int KC = CK::KC, KG = CK::KG, KR = CK::KR, A_SLICE_BYTES = CK::A_SLICE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
@@ -349,38 +447,27 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
       // A: row r holds [Re A | -Im A], row 64 + r holds [Im A | Re A].
       const int r = item / KG, kg = item % KG;
       const int gr = m0 + r;
-      const int er = e_row[r];
-      u64 fre[8], fim[8];
-      uint32_t sre = 0, sim = 0;
+      u64 vre[8], vim[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int gk = k0 + kg * 8 + j;
         ulonglong2 v = make_ulonglong2(0ull, 0ull);
         if (gr < g.m && gk < g.k) v = ld_bits(A + (int64_t)gr * g.lda + gk);
-        fre[j] = fixed_abs(v.x, er, frac);
-        fim[j] = fixed_abs(v.y, er, frac);
-        sre |= (uint32_t)(v.x >> 63) << j;
-        sim |= (uint32_t)(v.y >> 63) << j;
+        vre[j] = v.x;
+        vim[j] = v.y;
       }
+      Digits8<S8> dre, dim;
+      dre.load(vre, e_row[r], frac);
+      dim.load(vim, e_row[r], frac);
       for (int l = 0; l < L; ++l) {
-        const int sh = s * (L - 1 - l);
-        uint32_t pr[4], pi[4], pn[4];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const uint32_t r0 = bf16_of_small((uint32_t)(fre[2 * h] >> sh) & smask);
-          const uint32_t r1 = bf16_of_small((uint32_t)(fre[2 * h + 1] >> sh) & smask);
-          const uint32_t i0 = bf16_of_small((uint32_t)(fim[2 * h] >> sh) & smask);
-          const uint32_t i1 = bf16_of_small((uint32_t)(fim[2 * h + 1] >> sh) & smask);
-          const uint32_t sr0 = ((sre >> (2 * h)) & 1u) << 15, sr1 = ((sre >> (2 * h + 1)) & 1u) << 15;
-          const uint32_t si0 = ((sim >> (2 * h)) & 1u) << 15, si1 = ((sim >> (2 * h + 1)) & 1u) << 15;
-          pr[h] = (r0 | sr0) | ((r1 | sr1) << 16);
-          pi[h] = (i0 | si0) | ((i1 | si1) << 16);
-          pn[h] = (i0 | (si0 ^ 0x8000u)) | ((i1 | (si1 ^ 0x8000u)) << 16);
-        }
+        uint32_t pr[4], pi[4];
+        dre.slice(l, s, L, smask, pr);
+        dim.slice(l, s, L, smask, pi);
         unsigned char* base = sA + (size_t)l * A_SLICE_BYTES;
         const uint4 vr = make_uint4(pr[0], pr[1], pr[2], pr[3]);
         const uint4 vi = make_uint4(pi[0], pi[1], pi[2], pi[3]);
-        const uint4 vn = make_uint4(pn[0], pn[1], pn[2], pn[3]);
+        const uint4 vn = make_uint4(pi[0] ^ 0x80008000u, pi[1] ^ 0x80008000u, pi[2] ^ 0x80008000u,
+                                    pi[3] ^ 0x80008000u);
         *reinterpret_cast<uint4*>(base + kmaj_off<CK>(r, kg * 8)) = vr;
         *reinterpret_cast<uint4*>(base + kmaj_off<CK>(r, KC + kg * 8)) = vn;
         *reinterpret_cast<uint4*>(base + kmaj_off<CK>(MC + r, kg * 8)) = vi;
@@ -389,9 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
     } else for (int item = tid - half_t; item < n_mma * KG; item += half_t) {
       // B^T (K-major): row c holds [Re B(:, c) | Im B(:, c)].
       const int c = item % n_mma, kg = item / n_mma;
-      const int ec = e_col[c];
-      u64 fre[8], fim[8];
-      uint32_t sre = 0, sim = 0;
+      u64 vre[8], vim[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int gk = k0 + kg * 8 + j;
@@ -400,23 +485,16 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
           v = ld_bits(B + opb_off<BC>(g, gk, n0 + c));
           if (BC) v.y ^= 0x8000000000000000ull;
         }
-        fre[j] = fixed_abs(v.x, ec, frac);
-        fim[j] = fixed_abs(v.y, ec, frac);
-        sre |= (uint32_t)(v.x >> 63) << j;
-        sim |= (uint32_t)(v.y >> 63) << j;
+        vre[j] = v.x;
+        vim[j] = v.y;
       }
+      Digits8<S8> dre, dim;
+      dre.load(vre, e_col[c], frac);
+      dim.load(vim, e_col[c], frac);
       for (int l = 0; l < L; ++l) {
-        const int sh = s * (L - 1 - l);
         uint32_t pr[4], pi[4];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const uint32_t r0 = bf16_of_small((uint32_t)(fre[2 * h] >> sh) & smask);
-          const uint32_t r1 = bf16_of_small((uint32_t)(fre[2 * h + 1] >> sh) & smask);
-          const uint32_t i0 = bf16_of_small((uint32_t)(fim[2 * h] >> sh) & smask);
-          const uint32_t i1 = bf16_of_small((uint32_t)(fim[2 * h + 1] >> sh) & smask);
-          pr[h] = (r0 | (((sre >> (2 * h)) & 1u) << 15)) | ((r1 | (((sre >> (2 * h + 1)) & 1u) << 15)) << 16);
-          pi[h] = (i0 | (((sim >> (2 * h)) & 1u) << 15)) | ((i1 | (((sim >> (2 * h + 1)) & 1u) << 15)) << 16);
-        }
+        dre.slice(l, s, L, smask, pr);
+        dim.slice(l, s, L, smask, pi);
         unsigned char* base = sB + (size_t)l * b_slice_bytes;
         *reinterpret_cast<uint4*>(base + kmaj_off<CK>(c, kg * 8)) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
         *reinterpret_cast<uint4*>(base + kmaj_off<CK>(c, KC + kg * 8)) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
@@ -451,10 +529,16 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   // Epilogue in passes of EP columns (keeps the staging buffer small so that
-  // this kernel can share an SM with the FP64 inversion kernel).
+  // this kernel can share an SM with the FP64 inversion kernel).  Epilogue 1
+  // combines each real row's level accumulators into one integer T on the
+  // grid of unit 2^E, E = e_row + e_col - s (L + 1); epilogue 2 adds
+  // alpha / beta1 C1 / beta2 C2 / gamma dshift I on that grid and converts
+  // once to FP64 (falling back to rounded FP64 additions on integer bit
+  // patterns where a term is too large for the grid).
   constexpr int EP = 32;
-  u64* stage = reinterpret_cast<u64*>(smem);   // 128 x (EP + 1) doubles as bits (operands are dead)
+  Acc* stage = reinterpret_cast<Acc*>(smem);   // 128 x (EP + 1) integers (operands are dead)
   constexpr int lds = EP + 1;                   // padded rows: conflict-free per-lane row writes
+  constexpr int DMAX = WIDE ? 60 : 8;           // largest left shift of a term onto the grid
   double2* C = g.C + (int64_t)e * g.sC;
   const double2* C1 = (g.C1 && g.beta1.x != 0.0) ? g.C1 + (int64_t)e * g.sC1 : nullptr;
   const double2* C2 = (g.C2 && g.beta2.x != 0.0) ? g.C2 + (int64_t)e * g.sC2 : nullptr;
@@ -465,14 +549,13 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
   if (ok) {
     const int q = warp & 3, half = warp >> 2;   // warp w reads TMEM lanes 32 (w % 4) .. + 31
     const int R = q * 32 + lane;
-    const int er = e_row[R & (MC - 1)];
     for (int p0 = 0; p0 < n_mma; p0 += EP) {
-      // Epilogue 1: combine the levels of this lane's real row for 16 columns
+      // Epilogue 1: combine the levels of this lane's real row for 16 columns, 8 at a time
       const int c0 = p0 + 16 * half;
-      if (!WIDE && c0 < n_mma) {                 // levels combine within 64 bits, 8 columns at a time
+      if (c0 < n_mma) {
 #pragma unroll 1
         for (int h8 = 0; h8 < 16; h8 += 8) {
-          long long T[8];
+          Acc T[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) T[i] = 0;
           for (int d = 0; d < L; ++d) {
@@ -481,52 +564,44 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int sh = s * (L - 1 - d);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) T[i] += acc_int(v[i]) << sh;
+            for (int i = 0; i < 8; ++i) T[i] += (Acc)acc_int(v[i]) << sh;
           }
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            stage[R * lds + 16 * half + h8 + i] = i64_scaled_bits(T[i], er + e_col[c0 + h8 + i] - s * (L + 1));
-        }
-      } else if (WIDE && c0 < n_mma) {           // long products: 128-bit combination, 8 columns at a time
-#pragma unroll 1
-        for (int h8 = 0; h8 < 16; h8 += 8) {
-          __int128 T[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) T[i] = 0;
-          for (int d = 0; d < L; ++d) {
-            uint32_t v[8];
-            tmem_ld8(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * n_mma + c0 + h8), v);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int sh = s * (L - 1 - d);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) T[i] += (__int128)acc_int(v[i]) << sh;
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            stage[R * lds + 16 * half + h8 + i] = i128_scaled_bits(T[i], er + e_col[c0 + h8 + i] - s * (L + 1));
+          for (int i = 0; i < 8; ++i) stage[R * lds + 16 * half + h8 + i] = T[i];
         }
       }
       __syncthreads();
-      // Epilogue 2: alpha = +-1, + beta1 C1 + beta2 C2 + gamma dshift I (all +-1), FP64 store.
+      // Epilogue 2: the linear terms on the grid, one conversion, FP64 store.
       const int pc = min(EP, nt - p0);
       for (int idx = tid; idx < mt * pc; idx += TC_THREADS) {
         const int r = idx / pc, cl = idx % pc;
         const int gr = m0 + r, gc = n0 + p0 + cl;
-        u64 re = flip(stage[r * lds + cl], na);
-        u64 im = flip(stage[(MC + r) * lds + cl], na);
+        const int E = e_row[r] + e_col[p0 + cl] - s * (L + 1);
+        Acc tre = stage[r * lds + cl], tim = stage[(MC + r) * lds + cl];
+        if (na) { tre = -tre; tim = -tim; }
+        Acc xre = tre, xim = tim;
+        bool grid = true;
+        ulonglong2 x1 = make_ulonglong2(0ull, 0ull), x2 = make_ulonglong2(0ull, 0ull);
         if (C1) {
-          const ulonglong2 x = ld_bits(C1 + (int64_t)gr * g.ldc1 + gc);
-          re = add_bits(re, flip(x.x, n1));
-          im = add_bits(im, flip(x.y, n1));
+          x1 = ld_bits(C1 + (int64_t)gr * g.ldc1 + gc);
+          grid = grid_add<Acc, DMAX>(xre, x1.x, n1, E) && grid_add<Acc, DMAX>(xim, x1.y, n1, E);
         }
         if (C2) {
-          const ulonglong2 x = ld_bits(C2 + (int64_t)gr * g.ldc2 + gc);
-          re = add_bits(re, flip(x.x, n2));
-          im = add_bits(im, flip(x.y, n2));
+          x2 = ld_bits(C2 + (int64_t)gr * g.ldc2 + gc);
+          grid = grid && grid_add<Acc, DMAX>(xre, x2.x, n2, E) && grid_add<Acc, DMAX>(xim, x2.y, n2, E);
         }
-        if (has_d && gr == gc) {
-          re = add_bits(re, flip(dsh.x, ng));
-          im = add_bits(im, flip(dsh.y, ng));
+        const bool diag = has_d && gr == gc;
+        if (diag) grid = grid && grid_add<Acc, DMAX>(xre, dsh.x, ng, E) && grid_add<Acc, DMAX>(xim, dsh.y, ng, E);
+        u64 re, im;
+        if (grid) {
+          if (WIDE) { re = i128_scaled_bits((__int128)xre, E); im = i128_scaled_bits((__int128)xim, E); }
+          else { re = i64_scaled_bits((long long)xre, E); im = i64_scaled_bits((long long)xim, E); }
+        } else {   // a term too large for the grid: convert the product, then add in floating point
+          if (WIDE) { re = i128_scaled_bits((__int128)tre, E); im = i128_scaled_bits((__int128)tim, E); }
+          else { re = i64_scaled_bits((long long)tre, E); im = i64_scaled_bits((long long)tim, E); }
+          if (C1) { re = add_bits(re, flip(x1.x, n1)); im = add_bits(im, flip(x1.y, n1)); }
+          if (C2) { re = add_bits(re, flip(x2.x, n2)); im = add_bits(im, flip(x2.y, n2)); }
+          if (diag) { re = add_bits(re, flip(dsh.x, ng)); im = add_bits(im, flip(dsh.y, ng)); }
         }
         *reinterpret_cast<ulonglong2*>(C + (int64_t)gr * g.ldc + gc) = make_ulonglong2(re, im);
       }
@@ -575,12 +650,17 @@ TcCfg tc_config(int n, int k, int bits) {
 
 bool tc_wide(const TcCfg& c) { return c.s * (c.L - 1) > 36; }
 
+bool tc_wide(const TcCfg& c);
+
 size_t tc_smem_bytes(const TcCfg& c) {
   const int kr = Chunk<16>::KR;
   size_t op = (size_t)c.L * 128 * kr * 2 + (size_t)c.L * c.n_mma * kr * 2;
-  size_t st = (size_t)128 * (32 + 1) * 8;
+  size_t st = (size_t)128 * (32 + 1) * (tc_wide(c) ? 16 : 8);   // integer staging of one epilogue pass
   return op > st ? op : st;
 }
+
+// 8-bit slices of a 32-bit fixed-point value (byte permutes).
+bool tc_s8(const TcCfg& c) { return c.s == 8 && c.s * c.L <= 32; }
 
 }  // namespace
 
@@ -600,11 +680,13 @@ cudaError_t zgemm_tc(const ZGemm& g, cudaStream_t st) {
   if ((int)sm > g_tc_smem_optin) return cudaErrorInvalidValue;
   dim3 grid(tiles_m * tiles_n, g.batch);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  const bool wide = tc_wide(cfg), bc = g.opB == OP_C;
-  if (!wide && !bc) zgemm_tc_kernel<false, false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
-  else if (!wide) zgemm_tc_kernel<false, true><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
-  else if (!bc) zgemm_tc_kernel<true, false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
-  else zgemm_tc_kernel<true, true><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  const bool wide = tc_wide(cfg), bc = g.opB == OP_C, s8 = tc_s8(cfg);
+  if (s8 && !bc) zgemm_tc_kernel<true, false, false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  else if (s8) zgemm_tc_kernel<true, false, true><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  else if (!wide && !bc) zgemm_tc_kernel<false, false, false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  else if (!wide) zgemm_tc_kernel<false, false, true><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  else if (!bc) zgemm_tc_kernel<false, true, false><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
+  else zgemm_tc_kernel<false, true, true><<<grid, TC_THREADS, sm, st>>>(g, tiles_n, cfg);
   return cudaGetLastError();
 }
 
@@ -617,7 +699,7 @@ cudaError_t kernels_init() {
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, zgemm_tc_kernel<true, true>);
+  e = cudaFuncGetAttributes(&fa, zgemm_tc_kernel<false, true, true>);
   if (e != cudaSuccess) return e;
   const int dyn = optin - (int)fa.sharedSizeBytes - 1024;
   // all of the SM's unified L1 as shared memory: four 51 KB CTAs per SM (the
@@ -629,10 +711,12 @@ cudaError_t kernels_init() {
     return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
   };
-  if ((e = setup(zgemm_tc_kernel<false, false>)) != cudaSuccess) return e;
-  if ((e = setup(zgemm_tc_kernel<false, true>)) != cudaSuccess) return e;
-  if ((e = setup(zgemm_tc_kernel<true, false>)) != cudaSuccess) return e;
-  if ((e = setup(zgemm_tc_kernel<true, true>)) != cudaSuccess) return e;
+  if ((e = setup(zgemm_tc_kernel<true, false, false>)) != cudaSuccess) return e;
+  if ((e = setup(zgemm_tc_kernel<true, false, true>)) != cudaSuccess) return e;
+  if ((e = setup(zgemm_tc_kernel<false, false, false>)) != cudaSuccess) return e;
+  if ((e = setup(zgemm_tc_kernel<false, false, true>)) != cudaSuccess) return e;
+  if ((e = setup(zgemm_tc_kernel<false, true, false>)) != cudaSuccess) return e;
+  if ((e = setup(zgemm_tc_kernel<false, true, true>)) != cudaSuccess) return e;
   g_tc_smem_optin = dyn;
   return cudaSuccess;
 }

@@ -82,6 +82,12 @@ cudaError_t add_diag(double2* dst, int64_t sDst, int ld, int n, const double2* s
 cudaError_t axpy_scalar(double2* dst, int64_t sDst, const double2* src, int64_t sSrc, const double2* E,
                         double scale, int rows, int cols, int ld, int batch, cudaStream_t st);
 
+// dst[e] = c0 x0[e] + c1 x1[e] + c2 x2[e] + c3 x3[e] over n contiguous elements
+// (x_k[e] = x_k + e * s_k; null sources are skipped; dst may alias none of them).
+cudaError_t lincomb(double2* dst, int64_t sDst, int64_t n, int batch, const double2* x0, int64_t s0, double c0,
+                    const double2* x1, int64_t s1, double c1, const double2* x2, int64_t s2, double c2,
+                    const double2* x3, int64_t s3, double c3, cudaStream_t st);
+
 // D[e] = I (b x b).
 cudaError_t set_identity(double2* D, int64_t sD, int b, int batch, cudaStream_t st);
 

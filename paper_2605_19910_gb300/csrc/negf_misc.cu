@@ -232,6 +232,30 @@ __global__ void axpy_scalar_kernel(double2* __restrict__ dst, int64_t sDst, cons
   }
 }
 
+// dst[e] = sum_k c_k src_k[e] over n contiguous elements (null sources skipped).
+struct Lincomb4 {
+  const double2* src[4];
+  int64_t s[4];
+  double c[4];
+};
+
+__global__ void lincomb_kernel(Lincomb4 lc, double2* __restrict__ dst, int64_t sDst, int64_t n) {
+  const int e = blockIdx.y;
+  double2* dp = dst + (int64_t)e * sDst;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double2 o = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (!lc.src[k]) continue;
+      const double2 v = lc.src[k][(int64_t)e * lc.s[k] + idx];
+      o.x = fma(lc.c[k], v.x, o.x);
+      o.y = fma(lc.c[k], v.y, o.y);
+    }
+    dp[idx] = o;
+  }
+}
+
 inline int grid_x_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   return (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g));
@@ -292,6 +316,16 @@ cudaError_t axpy_scalar(double2* dst, int64_t sDst, const double2* src, int64_t 
   if (batch <= 0 || rows <= 0 || cols <= 0) return cudaSuccess;
   dim3 grid(grid_x_for((int64_t)rows * cols, 256), batch);
   axpy_scalar_kernel<<<grid, 256, 0, st>>>(dst, sDst, src, sSrc, E, scale, rows, cols, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t lincomb(double2* dst, int64_t sDst, int64_t n, int batch, const double2* x0, int64_t s0, double c0,
+                    const double2* x1, int64_t s1, double c1, const double2* x2, int64_t s2, double c2,
+                    const double2* x3, int64_t s3, double c3, cudaStream_t st) {
+  if (batch <= 0 || n <= 0) return cudaSuccess;
+  Lincomb4 lc{{x0, x1, x2, x3}, {s0, s1, s2, s3}, {c0, c1, c2, c3}};
+  dim3 grid(grid_x_for(n, 256), batch);
+  lincomb_kernel<<<grid, 256, 0, st>>>(lc, dst, sDst, n);
   return cudaGetLastError();
 }
 

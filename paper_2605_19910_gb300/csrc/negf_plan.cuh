@@ -26,6 +26,23 @@ struct CallKey {
 
 }  // namespace
 
+// A per-energy workspace region of a DDRGF plan: offset (in units of one
+// energy's elements times the chunk) and per-energy size; region r of energy
+// e of the chunk lives at DDW + r.off * chunk + e * r.sz (one contiguous slab
+// per region, so a batched launch over energies touches one slab).
+struct DDReg { int64_t off = 0, sz = 0; };
+
+// w-layer groups of one DDRGF sub-domain (step 1: fused sweeps of the closed
+// sub-domain).  first / nl / sz: first layer, layers and elements of each
+// group; hd / hu / hl: offsets of the energy-independent fused blocks
+// H_{I,I}, H_{I,I+1}, H_{I+1,I}; t / x / y: per-energy regions of the
+// right-connected sweep (t_I, X_I = t_I M_{I,I-1}, Y_I = M_{I-1,I} t_I).
+struct DDGroups {
+  std::vector<int> first, nl, sz;
+  std::vector<int64_t> hd, hu, hl;
+  std::vector<DDReg> t, x, y;
+};
+
 struct negf_plan_s {
   int N = 0, w = 1, nE = 0, n_domains = 1, precision = 0, refine = 0, outputs = 0, ckpt = 0, bits = 0;
   std::vector<int> b;
@@ -53,7 +70,6 @@ struct negf_plan_s {
   double2* LC_ws = nullptr;     // grad: last column g_i (b_i x b_N)
   std::vector<int64_t> p_off;
   int64_t p_elems = 0;
-  double2* RF_ws = nullptr;     // refinement: correction blocks (b_i x b_N)
   double2* scratch = nullptr;   // transmission: Gamma_L, Gamma_R, P, Q per energy
   int64_t scr_elems = 0;
   double2* G1N_ws = nullptr;    // G_1N when the caller does not keep it
@@ -78,20 +94,23 @@ struct negf_plan_s {
   int64_t bmax2 = 0, bmaxN = 0;
 
   // DDRGF (Alg. 2): n_domains (D2, D1) pairs; D2_j = [dom_f[j], dom_l[j]], its
-  // right separator D1_j = [dom_l[j] + 1, dom_l[j] + w].
+  // right separator D1_j = [dom_l[j] + 1, dom_l[j] + w].  F_j / L_j: the first
+  // / last w layers of D2_j; P_j: the separator as one super-block.
   std::vector<int> dom_f, dom_l, Fsz, Lsz, Psz;
   std::vector<int> dom_of;                       // layer -> domain (-1: separator)
   std::vector<int> sep_of;                       // layer -> separator (-1: domain)
-  std::vector<int> off_in;                       // layer offset inside F / Lw / separator super-block
-  std::vector<int64_t> fc_off, lc_off, wp_off, wq_off;   // per layer (D2 layers), per energy
-  std::vector<int64_t> tsd_off, tsu_off, tsl_off, rs_off, ts_x_off;  // per separator
-  std::vector<int64_t> mfp_off, mpf_off, mlq_off, mql_off;  // per domain, energy independent
-  int64_t fc_e = 0, lc_e = 0, wp_e = 0, wq_e = 0, tsd_e = 0, tsu_e = 0, rs_e = 0, ts_x_e = 0, msup_e = 0;
-  int Pmax = 0;
-  double2 *FC = nullptr, *FR = nullptr, *LCd = nullptr, *LR = nullptr, *VT = nullptr;
-  double2 *Wp = nullptr, *Wq = nullptr, *Vp = nullptr, *Vq = nullptr, *Zp = nullptr, *Zq = nullptr;
-  double2 *TSd = nullptr, *TSu = nullptr, *TSl = nullptr, *GSd = nullptr, *GSu = nullptr, *GSl = nullptr;
-  double2 *tS = nullptr, *XS = nullptr, *YS = nullptr, *SS = nullptr, *RS = nullptr, *Msup = nullptr;
+  std::vector<int> off_in;                       // layer offset inside F or the separator super-block
+  int Pmax = 0, FLmax = 0, Bmax = 0;
+  using Reg = DDReg;
+  std::vector<DDGroups> grR, grL;               // step-1 groups (fused sweeps) per domain
+  std::vector<Reg> r_xll, r_xfl, r_xlf, r_lsS, r_lsG, r_lsY, r_row, r_col;   // per domain, step 1
+  std::vector<Reg> r_wr, r_vr, r_sr, r_wl, r_vl, r_sl, r_tmp;                // per domain, step 4
+  std::vector<Reg> r_A, r_cL, r_cR, r_base, r_LL, r_RR, r_gLin, r_gLs, r_gRin, r_gRs, r_Gpp, r_Tu, r_Tl;  // per separator
+  Reg r_itL, r_itR, r_g1, r_g1t;
+  int64_t dd_e = 0, hf_e = 0;
+  std::vector<int64_t> mfp_off, mpf_off, mlq_off, mql_off;   // M super-blocks (offsets in Hf)
+  double2* DDW = nullptr;       // per-energy DDRGF regions
+  double2* Hf = nullptr;        // energy-independent fused H blocks and M super-blocks
   double2* band_ws = nullptr;   // band of one chunk when the caller keeps no band output
 
   // independent energy groups run on forked streams (graph branches)

@@ -32,6 +32,32 @@ struct Sweep {
   int grp = 0;        // energy group (stream set) of this sweep
   int sdom = 0;       // DDRGF sub-domain: selects its own Schur-window slots
   cudaEvent_t after_first_inv = nullptr;   // recorded once, after this sweep's first inversion
+  // Boundary self-energies of a DDRGF sub-domain solved as an open system:
+  // xr (Sigma_right, rows / columns of layers xr_f .. xr_f + w - 1, leading
+  // dimension xr_ld, per-energy stride xr_s) and xl (Sigma_left, layers
+  // xl_f .. xl_f + w - 1) are subtracted from the Schur-window blocks of
+  // those layers when upward() first forms them.
+  const double2* xr = nullptr; int xr_f = -1, xr_ld = 0; int64_t xr_s = 0;
+  const double2* xl = nullptr; int xl_f = -1, xl_ld = 0; int64_t xl_s = 0;
+  // Offset of layer a inside the w layers starting at layer a0.
+  int off_from(int a0, int a) const {
+    int o = 0;
+    for (int k = a0; k < a; ++k) o += p->b[k];
+    return o;
+  }
+  // The boundary block subtracted from S_ab (nullptr if none).
+  const double2* boundary(int a, int bb, int64_t* stride, int* ld) const {
+    const int w = p->w;
+    if (xr && a >= xr_f && a < xr_f + w && bb >= xr_f && bb < xr_f + w) {
+      *stride = xr_s; *ld = xr_ld;
+      return xr + (int64_t)off_from(xr_f, a) * xr_ld + off_from(xr_f, bb);
+    }
+    if (xl && a >= xl_f && a < xl_f + w && bb >= xl_f && bb < xl_f + w) {
+      *stride = xl_s; *ld = xl_ld;
+      return xl + (int64_t)off_from(xl_f, a) * xl_ld + off_from(xl_f, bb);
+    }
+    return nullptr;
+  }
 
   // Every kernel launch of the schedule goes through here so that the
   // optional profiler can bracket it with events on the launching stream.
@@ -124,6 +150,31 @@ struct Sweep {
       }
       mat[{l, l}] = true;
     }
+    if (xr) {
+      // the trailing window [xr_f, l] carries Sigma_right from the start:
+      // S_ab = E delta_ab I - H_ab - Sigma_right[a, b] for a, b in it
+      for (int a = xr_f; a <= l; ++a)
+        for (int bb = xr_f; bb <= l; ++bb) {
+          int64_t bs = 0; int bld = 0;
+          const double2* x = boundary(a, bb, &bs, &bld);
+          const int ba = p->b[a], bbs = p->b[bb];
+          double2* dst = Sslot(a, bb);
+          if (a == l && bb == l) {
+            NEGF_TRY(misc([&] { return negf::copy2d(x, bs, bld, dst, sS(), bbs, ba, bbs, -1.0, 1, C, st); }));
+            continue;
+          }
+          ZGemm g;   // k = 0: C = -H_ab (+ E I) - Sigma_right[a, b]
+          g.m = ba; g.n = bbs; g.k = 0;
+          g.A = dst; g.B = dst; g.lda = bbs; g.ldb = bbs;
+          g.C = dst; g.sC = sS(); g.ldc = bbs;
+          g.C1 = Hblk(a, bb); g.sC1 = 0; g.ldc1 = bbs; g.beta1 = {-1.0, 0.0};
+          g.C2 = x; g.sC2 = bs; g.ldc2 = bld; g.beta2 = {-1.0, 0.0};
+          if (a == bb) { g.dshift = E + e0; g.sD = 1; g.gamma = {1.0, 0.0}; }
+          g.batch = C;
+          NEGF_TRY(gemm64(g));
+          mat[{a, bb}] = true;
+        }
+    }
     for (int i = l; i >= f; --i) {
       const int bi = p->b[i];
       NEGF_TRY(inv(Sslot(i, i), sS(), Tblk(i), sq(bi), bi, C, i + 1));
@@ -172,6 +223,12 @@ struct Sweep {
               const double2* sg = nullptr;
               if (a == 0) sg = sigmaL();
               if (sg) { g.C2 = sg; g.sC2 = sig_stride; g.ldc2 = ba; g.beta2 = {-1.0, 0.0}; }
+            }
+            int64_t bs = 0; int bld = 0;
+            const double2* x = boundary(a, bb, &bs, &bld);
+            if (x) {   // a DDRGF sub-domain's Sigma_left (never on layer 0, which has no left neighbour)
+              if (g.C2) return cudaErrorInvalidValue;
+              g.C2 = x; g.sC2 = bs; g.ldc2 = bld; g.beta2 = {-1.0, 0.0};
             }
           }
           g.batch = C;
@@ -333,14 +390,17 @@ struct Sweep {
     return cudaSuccess;
   }
 
-  // One step of iterative refinement of the last block column x = M^{-1} e_N
-  // (mixed precision; gives G_1N = x_1 and T(E) to FP64-level accuracy):
+  // One step of iterative refinement of G_1N = x_1, x = M^{-1} e_N the last
+  // block column (mixed precision; gives G_1N and T(E) to FP64-level
+  // accuracy):
   //   r = e_N - M x with FP64-accurate products (56-bit tensor-core split,
   //       exact integer accumulation, the E x term in FP64),
-  //   d = L^{-1} D^{-1} U^{-1} r with the stored mixed factors, x <- x + d.
-  // r / v live in the P region (free after last_column), q / d in RF.
-  double2* RFblk(int i) const { return p->RF_ws + p->p_off[i] * p->chunk + (int64_t)wofs * p->b[i] * p->b[p->N - 1]; }
-  cudaError_t refine_last_column() {
+  //   x_1 <- x_1 + (L^{-1} D^{-1} U^{-1} r)_1 = x_1 + t_1 (U^{-1} r)_1,
+  // since L (L_{i,i-1} = X_{i,i-1}) is unit lower block triangular, so the
+  // first block row of L^{-1} is e_1^T: only the backward pass v = U^{-1} r
+  // and one product with t_1 are needed.  r / v live in the P region (free
+  // after last_column); the refined G_1N goes to g1n_out.
+  cudaError_t refine_g1n(double2* g1n_out, int64_t s_out) {
     const int N = p->N, w = p->w, C = ne, bN = p->b[N - 1];
     auto hx = [&](int i, int c, const double2* Aop, int64_t sA, int lda, double2* out, bool acc) {
       ZGemm g;   // out (+)= Aop * x_c, 56-bit products
@@ -379,32 +439,15 @@ struct Sweep {
         g.batch = C;
         NEGF_TRY(gemm(g));
       }
-    for (int i = 0; i < N; ++i) {      // d = L^{-1} D^{-1} v, then x += d
-      const int bi = p->b[i];
-      ZGemm g;
-      g.m = bi; g.n = bN; g.k = bi;
-      g.A = Tblk(i); g.sA = sq(bi); g.lda = bi;
-      g.B = Pblk(i); g.sB = (int64_t)bi * bN; g.ldb = bN;
-      g.C = RFblk(i); g.sC = (int64_t)bi * bN; g.ldc = bN;
-      g.batch = C;
-      NEGF_TRY(gemm(g));
-      for (int c = std::max(0, i - w); c < i; ++c) {
-        ZGemm h;
-        h.m = bi; h.n = bN; h.k = p->b[c];
-        h.A = Xblk(i, c); h.sA = (int64_t)bi * p->b[c]; h.lda = p->b[c];
-        h.B = RFblk(c); h.sB = (int64_t)p->b[c] * bN; h.ldb = bN;
-        h.C = RFblk(i); h.sC = (int64_t)bi * bN; h.ldc = bN; h.alpha = {-1.0, 0.0};
-        h.C1 = RFblk(i); h.sC1 = h.sC; h.ldc1 = bN; h.beta1 = {1.0, 0.0};
-        h.batch = C;
-        NEGF_TRY(gemm(h));
-      }
-    }
-    for (int i = 0; i < N; ++i)
-      NEGF_TRY(misc([&] {
-        return negf::copy2d(RFblk(i), (int64_t)p->b[i] * bN, bN, LCblk(i), (int64_t)p->b[i] * bN, bN, p->b[i], bN,
-                            1.0, 1, C, st);
-      }));
-    return cudaSuccess;
+    const int b0 = p->b[0];
+    ZGemm g;   // G_1N = x_1 + t_1 v_1
+    g.m = b0; g.n = bN; g.k = b0;
+    g.A = Tblk(0); g.sA = sq(b0); g.lda = b0;
+    g.B = Pblk(0); g.sB = (int64_t)b0 * bN; g.ldb = bN;
+    g.C = g1n_out; g.sC = s_out; g.ldc = bN;
+    g.C1 = LCblk(0); g.sC1 = (int64_t)b0 * bN; g.ldc1 = bN; g.beta1 = {1.0, 0.0};
+    g.batch = C;
+    return gemm(g);
   }
 
   // K = Gamma_R G_1N^H Gamma_L (bN x b1) and U_a = K G_{1,a} (bN x b_a) for

@@ -1,11 +1,16 @@
-"""Parity of the CUDA DDRGF path (Alg. 2: per-domain extended RGF, FP64
-interface Schur system, stitching) with the oracle, through the C-ABI.
+"""Parity of the CUDA DDRGF path (Alg. 2: the closed sub-domains' corner
+blocks, the FP64 interface system T_S, its connected Green's functions, each
+sub-domain re-solved with its boundary self-energies) with the oracle,
+through the C-ABI.
 
-DDRGF inverts every sub-domain as a closed system.  In the regime of the
-paper's experiments (diagonally dominant matrices, Sec. 4.1) its results
-match the oracle to 1e-11; at eta = 1e-6 with non-dominant H the sub-domains
-can be nearly singular and the halo chains amplify rounding, so the
-full-size case below checks a documented error bound instead."""
+In the regime of the paper's experiments (diagonally dominant matrices,
+Sec. 4.1) DDRGF matches RGF to the FP64 bar, at full size too.  At eta = 1e-6
+with non-dominant H some closed sub-domains are nearly singular: there Alg. 2
+itself, realised with LAPACK's pivoted sub-domain inverses (the oracle's
+ddrgf_selected), already departs from RGF by up to 3.6e-10 on the
+pentadiagonal workload, so the full-size FP64 case is held to that
+algorithm's own deviation at each sampled energy (times 100) where it exceeds
+the FP64 bar."""
 import numpy as np
 import pytest
 
@@ -60,7 +65,7 @@ def test_ddrgf_variable_sizes_and_explicit_split(P):
     prob = make_problem(17, b=None, size_range=(3, 20), w=1, n_energies=4, eta=1e-3, seed=47, diag_shift=DOM)
     run_dd(P, prob, 3, first=[0, 5, 12])
     prob = make_problem(19, b=None, size_range=(2, 12), w=2, n_energies=3, eta=1e-3, seed=48, diag_shift=DOM)
-    run_dd(P, prob, 3, first=[0, 6, 11])
+    run_dd(P, prob, 3, first=[0, 7, 13])
 
 
 def test_ddrgf_default_split_balances_block_weights(P):
@@ -77,46 +82,79 @@ def test_ddrgf_mixed_bulk_fp64_interface(P, w, N, nd, b):
     run_dd(P, prob, nd, precision="mixed", tol=MIXED_TOL)
 
 
-def test_ddrgf_penta256x32_mixed_full_size_error_bound(P):
-    """The pentadiagonal workload (256 x 32, n = 5, 1024 energies, 8 domains,
-    eta = 1e-6) with mixed sub-domain sweeps at the 56-bit default: sampled
-    energies within the mixed bar (measured max 4.7e-7, FP64 DDRGF 1.3e-6)."""
+def _penta_dd(P, precision, n_domains=8, **over):
     import torch
-    prob = workload("penta256x32")
+    prob = workload("penta256x32", **over)
     Hp, sL, sR, E = to_dev(prob, torch)
     nE = len(prob.energies)
-    plan = P.Plan(prob.sizes, 5, nE, n_domains=8, precision="mixed", outputs=P.NEGF_OUT_BAND)
-    Gb, _ = plan.solve(Hp, sL, sR, E, g1n=False)
-    assert not plan.info.cpu().numpy().any()
-    plan.close()
-    errs = []
-    for e in range(0, nE, 128):
-        ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, 2)
-        errs.append(band_rel_err(Gb[e].cpu().numpy(), ref["band"], prob.sizes, 2))
-    assert max(errs) < MIXED_TOL, errs
-    assert np.median(errs) < 1e-8, errs
-
-
-def test_ddrgf_penta256x32_full_size_error_bound(P):
-    """256 blocks x b = 32, n = 5, 1024 energies, 8 domains, eta = 1e-6 (the
-    benchmark-sized pentadiagonal workload): sampled energies against the
-    oracle with the bound that this regime allows (closed sub-domains near
-    resonance): every sampled energy below 1e-5, the median below 1e-8."""
-    import torch
-    prob = workload("penta256x32")
-    Hp, sL, sR, E = to_dev(prob, torch)
-    nE = len(prob.energies)
-    plan = P.Plan(prob.sizes, 5, nE, n_domains=8, outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_G1N)
+    plan = P.Plan(prob.sizes, 5, nE, n_domains=n_domains, precision=precision,
+                  outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_G1N)
     Gb, G1 = plan.solve(Hp, sL, sR, E)
     assert not plan.info.cpu().numpy().any()
     plan.close()
-    Gb = Gb.cpu().numpy()
+    return prob, Gb.cpu().numpy(), G1.cpu().numpy()
+
+
+def test_ddrgf_penta256x32_mixed_full_size(P):
+    """The pentadiagonal workload (256 x 32, n = 5, 1024 energies, 8 domains,
+    eta = 1e-6) with mixed sub-domain sweeps at the defaults: sampled
+    energies within the mixed bar, per energy and per output kind."""
+    prob, Gb, G1 = _penta_dd(P, "mixed")
     errs = []
-    for e in range(0, nE, 128):
-        ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, 2)
-        errs.append(band_rel_err(Gb[e], ref["band"], prob.sizes, 2))
-    assert max(errs) < 1e-5, errs
-    assert np.median(errs) < 1e-8, errs
+    for e in range(0, len(prob.energies), 128):
+        ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, 2, first_row=True)
+        errs.append(max(band_rel_err(Gb[e], ref["band"], prob.sizes, 2), rel_err(G1[e], ref["G1N"])))
+    assert max(errs) < MIXED_TOL, errs
+
+
+def test_ddrgf_penta256x32_fp64_full_size(P):
+    """256 blocks x b = 32, n = 5, 1024 energies, 8 domains, eta = 1e-6, FP64:
+    at every sampled energy the band and G_1N are within max(FP64_TOL, 100 x
+    d_alg2) of the oracle's RGF, where d_alg2 is how far the oracle's own
+    Alg. 2 (pivoted LAPACK sub-domain inverses, the stitching formula) lies
+    from that RGF at the same energy: the FP64 bar wherever Alg. 2 itself
+    holds it."""
+    prob, Gb, G1 = _penta_dd(P, "fp64")
+    report = []
+    for e in range(0, len(prob.energies), 128):
+        M = O.system_blocks(prob, prob.energies[e])
+        ref = O.rgf_selected(M, prob.sizes, 2, first_row=True)
+        d_alg2 = band_rel_err(P.pack_band(O.ddrgf_selected(M, prob.sizes, 2, 8)["band"], prob.sizes, 2),
+                              ref["band"], prob.sizes, 2)
+        bar = max(FP64_TOL, 100.0 * d_alg2)
+        err = max(band_rel_err(Gb[e], ref["band"], prob.sizes, 2), rel_err(G1[e], ref["G1N"]))
+        report.append((e, err, d_alg2))
+        assert err < bar, report
+
+
+def test_ddrgf_penta256x32_dominant_full_size_at_fp64_bar(P):
+    """The same chain in the paper's regime: layer diagonals shifted by 4, so
+    that the spectrum of H starts near E = 0.4 and M = E I - H - Sigma is
+    diagonally dominant for the sampled energies E in [-2, -0.3]: every one
+    at the FP64 bar."""
+    prob, Gb, G1 = _penta_dd(P, "fp64", n_energies=64, diag_shift=DOM)
+    for e in range(0, 28, 9):
+        ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, 2, first_row=True)
+        assert band_rel_err(Gb[e], ref["band"], prob.sizes, 2) < FP64_TOL, e
+        assert rel_err(G1[e], ref["G1N"]) < FP64_TOL, e
+
+
+def test_ddrgf_wire1024_32_domains_mixed_defaults(P):
+    """The 1024-layer nanowire (b uniform in {96..160}, 128 energies,
+    eta = 1e-6) by DDRGF with 32 domains on the mixed path at the plan's
+    defaults: two sampled energies within the mixed bar (band and G_1N)."""
+    import torch
+    prob = workload("wire1024")
+    Hp, sL, sR, E = to_dev(prob, torch)
+    nE = len(prob.energies)
+    plan = P.Plan(prob.sizes, 3, nE, n_domains=32, precision="mixed", outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_G1N)
+    Gb, G1 = plan.solve(Hp, sL, sR, E)
+    assert not plan.info.cpu().numpy().any()
+    plan.close()
+    for e in (5, 97):
+        ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, 1, first_row=True)
+        assert band_rel_err(Gb[e].cpu().numpy(), ref["band"], prob.sizes, 1) < MIXED_TOL, e
+        assert rel_err(G1[e].cpu().numpy(), ref["G1N"]) < MIXED_TOL, e
 
 
 def test_auto_domains_plans_follow_the_cost_model(P):
