@@ -292,8 +292,20 @@ int32_t negf_plan_groups(const negf_plan_t* p);
  * a count out of range, NEGF_ERR_UNSUPPORTED for changing a DDRGF plan. */
 negf_status negf_plan_set_groups(negf_plan_t* p, int32_t groups);
 
+/* Bound of the tensor-core product kernel's wait for its MMAs (the one
+ * device-side wait of the library: polls of mbarrier.try_wait per K chunk,
+ * after which the kernel stops, drains the MMAs already issued with the
+ * default bound, frees its tensor memory, records NEGF_ERR_TIMEOUT in the
+ * plan's error word and leaves that product unwritten).  For tests of the
+ * timeout path (polls = 0 makes every wait run out at once) and for
+ * callers that want a tighter watchdog.  polls < 0 restores the default
+ * (2^26).  Later calls capture a new graph.  NEGF_ERR_ARG for NULL. */
+negf_status negf_plan_set_wait_limit(negf_plan_t* p, int64_t polls);
+
 /* Wait for the plan's stream, then return the first error the device
- * reported since the previous negf_sync (and clear it). */
+ * reported since the previous negf_sync (and clear it): a timeout first
+ * (the products it left unwritten make later pivots meaningless), then a
+ * non-finite pivot, then a singular one. */
 negf_status negf_sync(negf_plan_t* p);
 
 /* Release the workspace and the plan.  NULL is allowed. */

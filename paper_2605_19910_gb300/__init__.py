@@ -54,7 +54,7 @@ EXPORTED = [
     "negf_plan_set_groups", "negf_lesser", "negf_solve_host",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
-    "negf_fp64_peak",
+    "negf_fp64_peak", "negf_plan_set_wait_limit",
 ]
 
 NEGF_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -149,6 +149,8 @@ def _load():
     lib.negf_auto_domains.restype = i32
     lib.negf_fp64_peak.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     lib.negf_fp64_peak.restype = st
+    lib.negf_plan_set_wait_limit.argtypes = [vp, i64]
+    lib.negf_plan_set_wait_limit.restype = st
     return lib
 
 
@@ -284,6 +286,11 @@ def negf_plan_groups(plan):
 def negf_plan_set_groups(plan, groups):
     """``negf_plan_set_groups`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_plan_set_groups(plan, int(groups))
+
+
+def negf_plan_set_wait_limit(plan, polls):
+    """``negf_plan_set_wait_limit`` of include/negf.h (argument marshalling only)."""
+    return _lib.negf_plan_set_wait_limit(plan, int(polls))
 
 
 def negf_plan_n_domains(plan):

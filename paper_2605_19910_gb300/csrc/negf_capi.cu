@@ -393,11 +393,14 @@ negf_status negf_sync(negf_plan_t* p) {
   e = cudaMemcpy(&word, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return NEGF_ERR_CUDA;
   if (word) cudaMemset(p->d_err, 0, sizeof(int));
+  // a wait that gave up leaves the product unwritten: later pivots are
+  // consequences, so the timeout is reported first
+  if (word & negf::ERRBIT_TIMEOUT) return NEGF_ERR_TIMEOUT;
   if (word & negf::ERRBIT_NONFINITE) return NEGF_ERR_NONFINITE;
   if (word & negf::ERRBIT_SINGULAR) return NEGF_ERR_SINGULAR;
-  if (word & negf::ERRBIT_TIMEOUT) return NEGF_ERR_TIMEOUT;
   return NEGF_OK;
 }
+
 
 }  // extern "C"
 
@@ -923,6 +926,16 @@ negf_status negf_plan_set_groups(negf_plan_t* p, int32_t groups) {
     if (p->n_domains > 1) return NEGF_ERR_UNSUPPORTED;   // per-group domain streams are fixed
     p->groups = groups;
     drop_graph(p);
+  }
+  return NEGF_OK;
+}
+
+negf_status negf_plan_set_wait_limit(negf_plan_t* p, int64_t polls) {
+  if (!p) return NEGF_ERR_ARG;
+  const long long v = polls < 0 ? -1 : (long long)polls;
+  if (v != p->wait_limit) {
+    p->wait_limit = v;
+    drop_graph(p);   // the limit is a kernel argument of the captured schedule
   }
   return NEGF_OK;
 }

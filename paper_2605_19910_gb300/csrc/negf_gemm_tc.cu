@@ -289,8 +289,8 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = WAIT_LIMIT) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
     }
     __syncthreads();
     last_parity = (uint32_t)(ch & 1);
-    ok = mbar_wait(mb, last_parity);
+    ok = mbar_wait(mb, last_parity, g.wait_limit >= 0 ? g.wait_limit : WAIT_LIMIT);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
       __syncthreads();
     }
   } else {
-    mbar_wait(mb, last_parity);       // second bounded wait for MMAs still in flight
+    mbar_wait(mb, last_parity);       // drain: bounded wait (default limit) for MMAs still in flight
     if (tid == 0 && g.errword) atomicOr(g.errword, ERRBIT_TIMEOUT);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -28,6 +28,7 @@ struct ZGemm {
   const double* weight = nullptr;
   int* errword = nullptr;   // device error word for bounded-wait timeouts (tensor-core path)
   int bits = 0;             // tensor-core path: significant bits of the product (0 = 32; up to 56)
+  long long wait_limit = -1;  // tensor-core path: polls of the MMA-completion wait (< 0: the default)
   int batch = 1;
   int reduce = 0;
 };

@@ -45,6 +45,7 @@ struct DDGroups {
 
 struct negf_plan_s {
   int N = 0, w = 1, nE = 0, n_domains = 1, precision = 0, refine = 0, outputs = 0, ckpt = 0, bits = 0;
+  long long wait_limit = -1;       // tensor-core MMA-completion wait polls (< 0: the kernel's default)
   std::vector<int> b;
   std::vector<int64_t> band_off;   // (d + w) * N + i -> element offset or -1
   int64_t band_elems = 0;
