@@ -213,6 +213,19 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
                       negf_c128* dH, negf_c128* dSigma_L, negf_c128* dSigma_R,
                       int32_t* info);
 
+/* negf_grad with separate output strides for the self-energy gradients:
+ * dSigma_L at dSigma_L + e * dSigma_L_stride (0 = summed over energies into
+ * one matrix), dSigma_R likewise, independently of sigma_E_stride (a lead
+ * given once for all energies can have per-energy gradients and the other
+ * way round).  Each output stride is 0 or at least max(b_1^2, b_N^2)
+ * (otherwise NEGF_ERR_ARG).  negf_grad is this call with both output strides
+ * equal to sigma_E_stride. */
+negf_status negf_grad_strided(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                              const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                              const double* dL_dT, double* T, negf_c128* dH, negf_c128* dSigma_L,
+                              int64_t dSigma_L_stride, negf_c128* dSigma_R, int64_t dSigma_R_stride,
+                              int32_t* info);
+
 /* negf_solve with the caller's buffers in HOST memory (same arguments and
  * layouts as negf_solve, every pointer a host pointer): the inputs are
  * copied to device buffers the plan owns (allocated at the first call, kept
@@ -221,8 +234,12 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
  * info are copied back, all on the plan's stream.  Synchronous: returns when
  * the outputs are in host memory, with negf_sync's status.  Page-locked host
  * memory (cudaHostAlloc, torch pin_memory) lets the copies run at the link's
- * rate; pageable memory works, more slowly.  NEGF_ERR_NOMEM if the device
- * buffers cannot be allocated. */
+ * rate; pageable memory works, more slowly.  With page-locked G_band / G_1N
+ * on a plain RGF plan (n_domains == 1) the copies back overlap the solve:
+ * each energy group copies its band in pieces of layers as its downward
+ * pass completes them, on a copy stream of its own, and its G_1N after that.
+ * NEGF_ERR_NOMEM if the device buffers cannot be allocated;
+ * NEGF_ERR_UNSUPPORTED for a band on a checkpointed adjoint plan. */
 negf_status negf_solve_host(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
                             const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                             negf_c128* G_band, negf_c128* G_1N, int32_t* info);

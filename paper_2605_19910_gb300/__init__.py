@@ -54,7 +54,7 @@ EXPORTED = [
     "negf_plan_set_groups", "negf_lesser", "negf_solve_host",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
-    "negf_fp64_peak", "negf_plan_set_wait_limit",
+    "negf_fp64_peak", "negf_plan_set_wait_limit", "negf_grad_strided",
 ]
 
 NEGF_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -151,6 +151,8 @@ def _load():
     lib.negf_fp64_peak.restype = st
     lib.negf_plan_set_wait_limit.argtypes = [vp, i64]
     lib.negf_plan_set_wait_limit.restype = st
+    lib.negf_grad_strided.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, i64, vp, i64, vp]
+    lib.negf_grad_strided.restype = st
     return lib
 
 
@@ -330,6 +332,14 @@ def negf_grad(plan, H, sigma_L, sigma_R, sigma_E_stride, E, dL_dT, T, dH, dSigma
     """``negf_grad`` of include/negf.h (argument marshalling only)."""
     return _lib.negf_grad(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
                           _ptr(dL_dT), _ptr(T), _ptr(dH), _ptr(dSigma_L), _ptr(dSigma_R), _ptr(info))
+
+
+def negf_grad_strided(plan, H, sigma_L, sigma_R, sigma_E_stride, E, dL_dT, T, dH, dSigma_L, dSigma_L_stride,
+                      dSigma_R, dSigma_R_stride, info):
+    """``negf_grad_strided`` of include/negf.h (argument marshalling only)."""
+    return _lib.negf_grad_strided(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
+                                  _ptr(dL_dT), _ptr(T), _ptr(dH), _ptr(dSigma_L), int(dSigma_L_stride),
+                                  _ptr(dSigma_R), int(dSigma_R_stride), _ptr(info))
 
 
 def negf_sync(plan):
@@ -671,27 +681,34 @@ class Plan:
         return T
 
     def grad(self, H, sigma_L, sigma_R, E, dL_dT, sync=True):
-        """Returns ``(T, dH, dSigma_L, dSigma_R)``."""
+        """Returns ``(T, dH, dSigma_L, dSigma_R)``; each self-energy gradient
+        has the shape of its input (a Sigma given once for all energies gets
+        the energy-summed gradient, computed by the library)."""
         torch = self.torch
-        T = torch.empty(self.n_energies, dtype=torch.float64, device="cuda")
+        nE = self.n_energies
+        T = torch.empty(nE, dtype=torch.float64, device="cuda")
         dH = torch.empty(self.band_elems, dtype=torch.complex128, device="cuda")
-        shapes = (sigma_L.shape, sigma_R.shape)
+        per = (sigma_L.dim() == 3, sigma_R.dim() == 3)
         sigma_L, sigma_R, stride = self._sigmas(sigma_L, sigma_R)
-        dSL = torch.empty_like(sigma_L)
-        dSR = torch.empty_like(sigma_R)
+        b = (self.sizes[0], self.sizes[-1])
+        outs, ostr = [], []
+        for side in range(2):
+            if per[side]:
+                outs.append(torch.empty(nE, stride, dtype=torch.complex128, device="cuda"))
+                ostr.append(stride)
+            else:
+                outs.append(torch.empty(b[side], b[side], dtype=torch.complex128, device="cuda"))
+                ostr.append(0)
         dL = dL_dT.contiguous()
         self._enter()
-        st = negf_grad(self.handle, H, sigma_L, sigma_R, stride, E, dL, T, dH, dSL, dSR, self.info)
+        st = negf_grad_strided(self.handle, H, sigma_L, sigma_R, stride, E, dL, T, dH, outs[0], ostr[0], outs[1],
+                               ostr[1], self.info)
         self._leave()
-        self._check(st, "negf_grad")
+        self._check(st, "negf_grad_strided")
         if sync:
             self.sync()
-        dSL = self._unpad(dSL, self.sizes[0], stride)
-        dSR = self._unpad(dSR, self.sizes[-1], stride)
-        if len(shapes[0]) == 2 and stride:      # one Sigma broadcast to every energy: sum
-            dSL = dSL.sum(0)
-        if len(shapes[1]) == 2 and stride:
-            dSR = dSR.sum(0)
+        dSL = self._unpad(outs[0], b[0], ostr[0])
+        dSR = self._unpad(outs[1], b[1], ostr[1])
         return T, dH, dSL, dSR
 
 

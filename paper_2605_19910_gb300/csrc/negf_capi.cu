@@ -379,6 +379,9 @@ void negf_destroy(negf_plan_t* p) {
   for (auto s3 : p->dstream) if (s3) cudaStreamDestroy(s3);
   for (auto e4 : p->dfork) cudaEventDestroy(e4);
   for (auto e5 : p->djoin) cudaEventDestroy(e5);
+  for (auto c : p->cstream) cudaStreamDestroy(c);
+  for (auto c : p->cready) cudaEventDestroy(c);
+  for (auto c : p->cdone) cudaEventDestroy(c);
   cudaFree(p->ws);
   cudaFree(p->d_err);
   if (p->host_io) cudaFree(p->host_io);
@@ -407,7 +410,7 @@ negf_status negf_sync(negf_plan_t* p) {
 namespace {
 
 
-enum CallKind { CALL_SOLVE = 1, CALL_TRANS = 2, CALL_GRAD = 3 };
+enum CallKind { CALL_SOLVE = 1, CALL_TRANS = 2, CALL_GRAD = 3, CALL_SOLVE_HOST = 5 };
 
 // Splits the energies [e0, e0 + ne) of one chunk into p->groups independent
 // ranges, forks them onto the plan's side streams and joins them back, so
@@ -484,6 +487,70 @@ negf_status run_captured(negf_plan_s* p, const CallKey& key, F body) {
 
 }  // namespace
 
+namespace {
+
+// The schedule of negf_solve on device buffers.  With host_band / host_g1n
+// (page-locked host memory, plain RGF plans) every energy group also copies
+// its band back in layer pieces on its own copy stream as its downward pass
+// completes them, and its G_1N after that; the copy streams join the plan's
+// stream at the end.
+cudaError_t solve_body(negf_plan_s* p, const negf_c128* H, const negf_c128* sigma_L, const negf_c128* sigma_R,
+                       int64_t sigma_E_stride, const negf_c128* E, negf_c128* G_band, negf_c128* G_1N,
+                       int32_t* info, negf_c128* host_band, negf_c128* host_g1n) {
+  NEGF_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * p->nE, p->stream));
+  const bool host = host_band || host_g1n;
+  const int64_t s1 = (int64_t)p->b[0] * p->b[p->N - 1];
+  for (int e0 = 0; e0 < p->nE; e0 += p->chunk) {
+    Sweep base{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
+               sigma_E_stride, (const double2*)E, (double2*)G_band, (double2*)G_1N, info,
+               e0, std::min(p->chunk, p->nE - e0)};
+    if (p->n_domains > 1) {
+      if (!G_band) { base.Gband = p->band_ws; base.gb_e0 = e0; }
+      if (e0 == 0) NEGF_TRY(DD(p, base).assemble_static());
+      NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
+        return DD(p, s).run(true, G_1N ? (double2*)G_1N + (int64_t)s.e0 * s1 : nullptr, s1);
+      }));
+      continue;
+    }
+    NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
+      if (host) {
+        s.host_band = (double2*)host_band;
+        s.cst = p->cstream[s.grp];
+        s.cready = p->cready[s.grp];
+      }
+      if (p->ck_k > 0) {
+        NEGF_TRY(s.ck_forward((double2*)G_1N + (int64_t)s.e0 * s1, s1));
+      } else {
+        NEGF_TRY(s.upward(G_band != nullptr || (G_1N && p->refine)));
+        if (G_band) NEGF_TRY(s.downward());
+        if (G_1N && p->refine) {   // G_1N = first block of the last column, refined
+          NEGF_TRY(s.last_column());
+          NEGF_TRY(s.refine_g1n((double2*)G_1N + (int64_t)s.e0 * s1, s1));
+        } else if (G_1N) {
+          NEGF_TRY(s.first_row((double2*)G_1N + (int64_t)s.e0 * s1, s1));
+        }
+      }
+      if (host_g1n) {
+        NEGF_TRY(cudaEventRecord(s.cready, s.st));
+        NEGF_TRY(cudaStreamWaitEvent(s.cst, s.cready, 0));
+        NEGF_TRY(cudaMemcpyAsync(host_g1n + (int64_t)s.e0 * s1, G_1N + (int64_t)s.e0 * s1,
+                                 (size_t)(s.ne * s1) * sizeof(negf_c128), cudaMemcpyDeviceToHost, s.cst));
+      }
+      return cudaSuccess;
+    }));
+  }
+  if (host) {   // join every group's copy stream
+    const int G = std::min(p->groups, p->chunk);
+    for (int g = 0; g < G; ++g) {
+      NEGF_TRY(cudaEventRecord(p->cdone[g], p->cstream[g]));
+      NEGF_TRY(cudaStreamWaitEvent(p->stream, p->cdone[g], 0));
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
 extern "C" {
 
 negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
@@ -500,33 +567,7 @@ negf_status negf_solve(negf_plan_t* p, const negf_c128* H, const negf_c128* sigm
   const void* ptrs[] = {H, sigma_L, sigma_R, E, G_band, G_1N, info};
   std::memcpy(key.p, ptrs, sizeof(ptrs));
   return run_captured(p, key, [&]() -> cudaError_t {
-    NEGF_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * p->nE, p->stream));
-    for (int e0 = 0; e0 < p->nE; e0 += p->chunk) {
-      Sweep base{p, p->stream, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R,
-                 sigma_E_stride, (const double2*)E, (double2*)G_band, (double2*)G_1N, info,
-                 e0, std::min(p->chunk, p->nE - e0)};
-      const int64_t s1 = (int64_t)p->b[0] * p->b[p->N - 1];
-      if (p->n_domains > 1) {
-        if (!G_band) { base.Gband = p->band_ws; base.gb_e0 = e0; }
-        if (e0 == 0) NEGF_TRY(DD(p, base).assemble_static());
-        NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
-          return DD(p, s).run(true, G_1N ? (double2*)G_1N + (int64_t)s.e0 * s1 : nullptr, s1);
-        }));
-        continue;
-      }
-      NEGF_TRY(for_groups(p, base, [&](Sweep& s) -> cudaError_t {
-        if (p->ck_k > 0) return s.ck_forward((double2*)G_1N + (int64_t)s.e0 * s1, s1);
-        NEGF_TRY(s.upward(G_band != nullptr || (G_1N && p->refine)));
-        if (G_band) NEGF_TRY(s.downward());
-        if (G_1N && p->refine) {   // G_1N = first block of the last column, refined
-          NEGF_TRY(s.last_column());
-          return s.refine_g1n((double2*)G_1N + (int64_t)s.e0 * s1, s1);
-        }
-        if (G_1N) NEGF_TRY(s.first_row((double2*)G_1N + (int64_t)s.e0 * s1, s1));
-        return cudaSuccess;
-      }));
-    }
-    return cudaSuccess;
+    return solve_body(p, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info, nullptr, nullptr);
   });
 }
 
@@ -576,14 +617,27 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
                       const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                       const double* dL_dT, double* T, negf_c128* dH, negf_c128* dSigma_L,
                       negf_c128* dSigma_R, int32_t* info) {
+  return negf_grad_strided(p, H, sigma_L, sigma_R, sigma_E_stride, E, dL_dT, T, dH, dSigma_L, sigma_E_stride,
+                           dSigma_R, sigma_E_stride, info);
+}
+
+negf_status negf_grad_strided(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                              const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                              const double* dL_dT, double* T, negf_c128* dH, negf_c128* dSigma_L,
+                              int64_t dSigma_L_stride, negf_c128* dSigma_R, int64_t dSigma_R_stride,
+                              int32_t* info) {
   if (!p || !H || !E || !info || !dL_dT || !dH || !sigma_L || !sigma_R || bad_sigma_stride(p, sigma_E_stride))
     return NEGF_ERR_ARG;
+  if (bad_sigma_stride(p, dSigma_L_stride) || bad_sigma_stride(p, dSigma_R_stride)) return NEGF_ERR_ARG;
   if (!(p->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
   CallKey key{};
   key.kind = CALL_GRAD;
   key.stride = sigma_E_stride;
-  const void* ptrs[] = {H, sigma_L, sigma_R, E, dL_dT, T, dH, dSigma_L, dSigma_R, info};
+  const void* ptrs[] = {H, sigma_L, sigma_R, E, dL_dT, T, dH, dSigma_L, dSigma_R, info,
+                        (const void*)(intptr_t)dSigma_L_stride, (const void*)(intptr_t)dSigma_R_stride};
   std::memcpy(key.p, ptrs, sizeof(ptrs));
+  // output stride of the gradient of Sigma_L (side 0) / Sigma_R (side 1): 0 sums over energies
+  auto ostride = [&](int side) { return side == 0 ? dSigma_L_stride : dSigma_R_stride; };
   const int N = p->N, b0 = p->b[0], bN = p->b[N - 1];
   const int64_t s1 = (int64_t)b0 * bN;
   const bool ck = p->ck_k > 0;
@@ -617,13 +671,14 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
       // per-energy Sigma: the M-path part 2 w_e (G_{i,N} U_i)^H of layer 0 / N-1
       auto sigma_mpath = [&](int side, const double2* Ui, int64_t sUi, const double2* Li, int64_t sLi) {
         negf_c128* dS = side == 0 ? dSigma_L : dSigma_R;
-        if (!dS || sigma_E_stride == 0) return cudaSuccess;
+        const int64_t os = ostride(side);
+        if (!dS || os == 0) return cudaSuccess;
         const int bs = side == 0 ? b0 : bN;
         ZGemm h;
         h.m = bs; h.n = bs; h.k = bN;
         h.A = Ui; h.sA = sUi; h.lda = bs; h.opA = negf::OP_C;
         h.B = Li; h.sB = sLi; h.ldb = bN; h.opB = negf::OP_C;
-        h.C = (double2*)dS + (int64_t)e0 * sigma_E_stride; h.sC = sigma_E_stride; h.ldc = bs;
+        h.C = (double2*)dS + (int64_t)e0 * os; h.sC = os; h.ldc = bs;
         h.alpha = {2.0, 0.0}; h.weight = dL_dT + e0; h.batch = ne;
         return s.gemm64(h);
       };
@@ -704,7 +759,8 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
           g.B = V; g.sB = s1; g.ldb = bN;
         }
         g.batch = ne;
-        if (sigma_E_stride == 0) {   // per-energy products, then their weighted sum times -2i
+        const int64_t os = ostride(side);
+        if (os == 0) {   // per-energy products, then their weighted sum times -2i
           g.C = p->DH_ws; g.sC = p->bmax2; g.ldc = bs;
           NEGF_TRY(s.gemm64(g));
           NEGF_TRY(s.misc([&] {
@@ -712,20 +768,20 @@ negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma
                                          {0.0, -2.0}, first ? 0 : 1, 0, p->stream);
           }));
         } else {   // per energy, onto the M-path part written above
-          double2* out = (double2*)dS + (int64_t)e0 * sigma_E_stride;
+          double2* out = (double2*)dS + (int64_t)e0 * os;
           g.alpha = {0.0, -2.0};
           g.weight = dL_dT + e0;
-          g.C = out; g.sC = sigma_E_stride; g.ldc = bs;
-          g.C1 = out; g.sC1 = sigma_E_stride; g.ldc1 = bs; g.beta1 = {1.0, 0.0};
+          g.C = out; g.sC = os; g.ldc = bs;
+          g.C1 = out; g.sC1 = os; g.ldc1 = bs; g.beta1 = {1.0, 0.0};
           NEGF_TRY(s.gemm64(g));
         }
       }
     }
-    if (sigma_E_stride == 0) {   // add the M-path parts dH_00 / dH_NN once, after all chunks
+    {   // summed outputs: add the M-path parts dH_00 / dH_NN once, after all chunks
       Sweep s{p, p->stream, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, info, 0, 1};
       for (int side = 0; side < 2; ++side) {
         negf_c128* dS = side == 0 ? dSigma_L : dSigma_R;
-        if (!dS) continue;
+        if (!dS || ostride(side) != 0) continue;
         const int layer = side == 0 ? 0 : N - 1, bs = p->b[layer];
         ZGemm g;
         g.m = bs; g.n = bs; g.k = 0;
@@ -749,10 +805,43 @@ extern "C" {
 // buffers the plan owns, the captured solve, outputs copied back, all on the
 // plan's stream; returns after the outputs are in host memory (with
 // negf_sync's status).
+namespace {
+
+bool host_pinned(const void* ptr) {
+  if (!ptr) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// Copy streams and events of negf_solve_host's overlapped copies.
+cudaError_t ensure_copy_streams(negf_plan_s* p) {
+  const int G = (int)p->side.size() + 1;
+  while ((int)p->cstream.size() < G) {
+    cudaStream_t c = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    NEGF_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+    p->cstream.push_back(c);
+    NEGF_TRY(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    p->cready.push_back(a);
+    NEGF_TRY(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    p->cdone.push_back(b);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+// negf_solve from host memory to host memory: inputs copied to device
+// buffers the plan owns, the captured solve, outputs copied back, all on the
+// plan's stream; returns after the outputs are in host memory (with
+// negf_sync's status).  With page-locked outputs on a plain RGF plan the
+// band's copy back overlaps the solve (piecewise, per energy group).
 negf_status negf_solve_host(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
                             const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                             negf_c128* G_band, negf_c128* G_1N, int32_t* info) {
   if (!p || !H || !E || !info || bad_sigma_stride(p, sigma_E_stride) || (!G_band && !G_1N)) return NEGF_ERR_ARG;
+  if (p->ck_k > 0 && G_band) return NEGF_ERR_UNSUPPORTED;
   const int64_t nE = p->nE, b0 = p->b[0], bN = p->b[p->N - 1];
   const int64_t nsig_L = sigma_E_stride ? (nE - 1) * sigma_E_stride + b0 * b0 : b0 * b0;
   const int64_t nsig_R = sigma_E_stride ? (nE - 1) * sigma_E_stride + bN * bN : bN * bN;
@@ -761,6 +850,7 @@ negf_status negf_solve_host(negf_plan_t* p, const negf_c128* H, const negf_c128*
                oG = oE + al(nE), o1 = oG + al(nE * p->band_elems), oI = o1 + al(nE * b0 * bN),
                need = oI + al(nE);
   if (!p->host_io || p->host_io_bytes < need) {
+    drop_graph(p);   // a captured host-copy schedule refers to the old buffers
     if (p->host_io) cudaFree(p->host_io);
     p->host_io = nullptr;
     p->host_io_bytes = 0;
@@ -783,10 +873,25 @@ negf_status negf_solve_host(negf_plan_t* p, const negf_c128* H, const negf_c128*
   if (e == cudaSuccess && dR) e = cudaMemcpyAsync(dR, sigma_R, (size_t)nsig_R * z, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dE, E, (size_t)nE * z, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e);
-  negf_status s = negf_solve(p, dH, dL, dR, sigma_E_stride, dE, dG, d1, dI);
-  if (s != NEGF_OK) return s;
-  if (G_band) e = cudaMemcpyAsync(G_band, dG, (size_t)(nE * p->band_elems) * z, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && G_1N) e = cudaMemcpyAsync(G_1N, d1, (size_t)(nE * b0 * bN) * z, cudaMemcpyDeviceToHost, st);
+  const bool overlap = p->n_domains == 1 && host_pinned(G_band) && host_pinned(G_1N);
+  if (overlap) {
+    e = ensure_copy_streams(p);
+    if (e != cudaSuccess) return cuda_status(e);
+    CallKey key{};
+    key.kind = CALL_SOLVE_HOST;
+    key.stride = sigma_E_stride;
+    const void* ptrs[] = {G_band, G_1N, dL, dR};
+    std::memcpy(key.p, ptrs, sizeof(ptrs));
+    negf_status s = run_captured(p, key, [&]() -> cudaError_t {
+      return solve_body(p, dH, dL, dR, sigma_E_stride, dE, dG, d1, dI, G_band, G_1N);
+    });
+    if (s != NEGF_OK) return s;
+  } else {
+    negf_status s = negf_solve(p, dH, dL, dR, sigma_E_stride, dE, dG, d1, dI);
+    if (s != NEGF_OK) return s;
+    if (G_band) e = cudaMemcpyAsync(G_band, dG, (size_t)(nE * p->band_elems) * z, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && G_1N) e = cudaMemcpyAsync(G_1N, d1, (size_t)(nE * b0 * bN) * z, cudaMemcpyDeviceToHost, st);
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(info, dI, (size_t)nE * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_status(e);
   return negf_sync(p);

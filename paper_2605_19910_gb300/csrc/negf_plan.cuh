@@ -119,6 +119,11 @@ struct negf_plan_s {
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;   // [0] fork, [1..] joins
   std::vector<cudaEvent_t> stagger;   // group g -> g + 1 start dependency
+  // negf_solve_host with page-locked host outputs: each energy group copies
+  // its band back in layer pieces on its own copy stream as the downward pass
+  // completes them (created at the first such call)
+  std::vector<cudaStream_t> cstream;
+  std::vector<cudaEvent_t> cready, cdone;
   // DDRGF: the sub-domains of one energy group run concurrently, domain j of
   // group g on dstream[g * n_domains + j] (j = 0 on the group's own stream)
   std::vector<cudaStream_t> dstream;

@@ -39,6 +39,45 @@ struct Sweep {
   // those layers when upward() first forms them.
   const double2* xr = nullptr; int xr_f = -1, xr_ld = 0; int64_t xr_s = 0;
   const double2* xl = nullptr; int xl_f = -1, xl_ld = 0; int64_t xl_s = 0;
+  // Host copy of the band (negf_solve_host with page-locked outputs): the
+  // energy-major host band, the group's copy stream and event, the number of
+  // layer pieces and the last layer already copied.
+  double2* host_band = nullptr;
+  cudaStream_t cst = nullptr;
+  cudaEvent_t cready = nullptr;
+  int host_pieces = 4, host_done = -1;
+
+  // Copy to the host every band block (a, b) with max(a, b) <= i not copied
+  // yet: for each diagonal d a contiguous run of blocks per energy, one 2-D
+  // copy over the range's energies (pitch: one band), on the copy stream
+  // after this stream's work so far.
+  cudaError_t host_copy_upto(int i) {
+    const int N = p->N, w = p->w;
+    NEGF_TRY(cudaEventRecord(cready, st));
+    NEGF_TRY(cudaStreamWaitEvent(cst, cready, 0));
+    const size_t pitch = (size_t)p->band_elems * sizeof(double2);
+    for (int d = -w; d <= w; ++d) {
+      const int lo = std::max(std::max(0, -d), host_done - std::max(0, d) + 1);
+      const int hi = std::min(std::min(N - 1, N - 1 - d), i - std::max(0, d));
+      if (hi < lo) continue;
+      const int64_t o0 = p->band_off[(size_t)(d + w) * N + lo];
+      const int64_t o1 = p->band_off[(size_t)(d + w) * N + hi] + (int64_t)p->b[hi] * p->b[hi + d];
+      const size_t width = (size_t)(o1 - o0) * sizeof(double2);
+      NEGF_TRY(cudaMemcpy2DAsync(host_band + (int64_t)e0 * p->band_elems + o0, pitch,
+                                 Gband + (int64_t)(e0 - gb_e0) * p->band_elems + o0, pitch, width, (size_t)ne,
+                                 cudaMemcpyDeviceToHost, cst));
+    }
+    host_done = i;
+    return cudaSuccess;
+  }
+  // After layer i of a downward pass over [f, l]: copy at piece boundaries.
+  cudaError_t host_copy_after(int i, int f, int l) {
+    if (!host_band) return cudaSuccess;
+    const int n = l - f + 1, k = i - f + 1;
+    const bool boundary = i == l || (k * host_pieces) / n != ((k - 1) * host_pieces) / n;
+    return boundary ? host_copy_upto(i) : cudaSuccess;
+  }
+
   // Offset of layer a inside the w layers starting at layer a0.
   int off_from(int a0, int a) const {
     int o = 0;
@@ -247,6 +286,7 @@ struct Sweep {
     if (l < 0) l = N - 1;
     const int64_t sG = p->band_elems;
     NEGF_TRY(misc([&] { return negf::copy_blocks(Tblk(f), sq(p->b[f]), Gb(f, f), sG, sq(p->b[f]), C, st); }));
+    NEGF_TRY(host_copy_after(f, f, l));
     for (int i = f + 1; i <= l; ++i) {
       const int bi = p->b[i];
       const int lo = std::max(f, i - w);
@@ -285,6 +325,7 @@ struct Sweep {
         g.batch = C;
         NEGF_TRY(gemm(g));
       }
+      NEGF_TRY(host_copy_after(i, f, l));
     }
     return cudaSuccess;
   }

@@ -86,6 +86,34 @@ def test_grad_per_energy_sigma_variable_sizes(P):
     _check(P, prob, rng.normal(size=4), per_energy_sigma=True)
 
 
+def test_grad_one_lead_per_energy_the_other_shared(P):
+    """Sigma_L given per energy, Sigma_R once for all energies: the library
+    returns dSigma_L per energy and dSigma_R summed over energies itself
+    (negf_grad_strided's separate output strides)."""
+    import torch
+    rng = np.random.default_rng(4)
+    prob = make_problem(6, b=None, size_range=(3, 9), w=1, n_energies=4, eta=1e-3, seed=35)
+    b0, bN = prob.sizes[0], prob.sizes[-1]
+    sLs = np.stack([_random_sigma(rng, b0) for _ in range(4)])
+    sR1 = _random_sigma(rng, bN)
+    weights = rng.normal(size=4)
+    # oracle: every energy with its own Sigma_L and the shared Sigma_R
+    prob.sigma_L, prob.sigma_R = sLs, np.stack([sR1] * 4)
+    gH, gL, gR, Tref = _oracle_grad(prob, weights, per_energy_sigma=True)
+    Hp = torch.tensor(P.pack_band(prob.H, prob.sizes, 1), device="cuda")
+    E = torch.tensor(prob.energies, device="cuda")
+    plan = P.Plan(prob.sizes, 3, 4, outputs=P.NEGF_OUT_TRANSMISSION | P.NEGF_OUT_GRAD)
+    T, dH, dSL, dSR = plan.grad(Hp, torch.tensor(sLs, device="cuda"), torch.tensor(sR1, device="cuda"), E,
+                                torch.tensor(weights, device="cuda"))
+    plan.close()
+    assert tuple(dSL.shape) == (4, b0, b0) and tuple(dSR.shape) == (bN, bN)
+    assert rel_err(dSL.cpu().numpy(), gL) < FP64_TOL
+    assert rel_err(dSR.cpu().numpy(), gR.sum(0)) < FP64_TOL
+    assert rel_err(T.cpu().numpy(), Tref) < FP64_TOL
+    got = P.unpack_band(dH.cpu().numpy(), prob.sizes, 1)
+    assert max(rel_err(got[k], v) for k, v in gH.items()) < 1e-10
+
+
 def test_grad_single_layer(P):
     rng = np.random.default_rng(3)
     prob = make_problem(1, b=5, w=1, n_energies=3, eta=1e-2, seed=33)
