@@ -33,14 +33,6 @@ WORKLOAD = "batched64x64"
 METRIC = "selected-G^R energies x blocks / s"
 UNIT = "energy-blocks/s"
 
-# product width per workload on the mixed path: at eta = 1e-6 the 1024-layer
-# nanowire, the pentadiagonal chain and the 128 x 48 transmission chain have
-# near-singular layers (localised states) whose blocks need more than 32 bits
-# for 1e-5 (at 32 bits: 7e-4, 2e-4, 5e-5); 42 bits (7 slices of 6-7 bits, the
-# widest that keeps the 64-bit level combination for these blocks) gives
-# 1.4e-6, 1.4e-8, 4e-8; 64 x 64 x 512 meets the bar at 32 bits (2e-6)
-PRODUCT_BITS = {"wire1024": 42, "penta256x32": 42, "trans128x48": 42}
-
 # DRAM traffic per unit (one block inversion) of the dominant kernel from an
 # ncu capture of one 512-block launch, valid only while the kernel source is
 # the one captured (the summary and its command are under profiles/)
@@ -51,6 +43,11 @@ NCU_TRAFFIC = {
         "sha256": "822754194672a1cbd60c34eab0d70b7732c3e368ef01f55ae1df4212b2eaba73",
     },
 }
+
+# Largest per-energy deviation from a 56-bit solve that negf_tune_precision
+# accepts: a quarter of the mixed path's 1e-5 bar (the 56-bit solve is
+# accurate to ~1e-10 here, so the deviation is the error itself)
+TUNE_TOL = 2.5e-6
 
 # Nominal GB300 FP64 rate at the 2070 MHz maximum SM clock (context only: the
 # roofline of the FP64 kernels is taken against the rates negf_fp64_peak
@@ -75,7 +72,9 @@ def _args():
     ap.add_argument("--block-size", type=int, default=None, help="override the workload's block size")
     ap.add_argument("--product-bits", type=int, default=None,
                     help="bits of the tensor-core block products on the mixed path "
-                         "(default: 48 for the 1024-layer nanowire, 32 otherwise)")
+                         "(default: the library's default, narrowed by negf_tune_precision)")
+    ap.add_argument("--no-tune-precision", action="store_true",
+                    help="keep the plan's product width instead of negf_tune_precision's choice")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plan's default energy-group count instead of negf_autotune's choice")
     ap.add_argument("--no-grad-side", action="store_true",
@@ -290,8 +289,7 @@ def run_ours(a, rank, world, local_rank):
     Eh = torch.tensor(prob.energies).pin_memory()
     H, sL, sR, E = (x.to(dev) for x in (Hh, sLh, sRh, Eh))
     outputs = P.NEGF_OUT_BAND | P.NEGF_OUT_G1N | P.NEGF_OUT_TRANSMISSION
-    bits = a.product_bits if a.product_bits is not None else PRODUCT_BITS.get(a.workload, 0)
-    bits = bits if a.precision == "mixed" else 0
+    bits = a.product_bits if (a.product_bits is not None and a.precision == "mixed") else 0
     refine = a.refine_steps if a.precision == "mixed" else 0
     plan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision=a.precision, outputs=outputs, product_bits=bits,
                   refine_steps=refine)
@@ -301,6 +299,14 @@ def run_ours(a, rank, world, local_rank):
     def step():
         plan.solve(H, sL, sR, E, out_band=Gb, out_g1n=G1, sync=False)
 
+    # product width: the narrowest whose results stay within TUNE_TOL of a
+    # 56-bit solve of these inputs at every energy (negf_tune_precision; untimed)
+    prec_tune = None
+    if a.precision == "mixed" and a.product_bits is None and not a.no_tune_precision:
+        tb, tdev = plan.tune_precision(H, sL, sR, E, tol=TUNE_TOL)
+        prec_tune = {"product_bits": tb, "max_rel_deviation_from_56_bit": tdev, "tol": TUNE_TOL,
+                     "candidates": list(P.TUNE_BITS)}
+        bits = tb
     # energy-group autotuner on these inputs (untimed, before the warm-up)
     tune = None
     if not a.no_autotune:
@@ -466,7 +472,7 @@ def run_ours(a, rank, world, local_rank):
     from oracle.rgf import rgf_flops_paper
     flops_step = rgf_flops_paper(prob.sizes, prob.w) * nE
     ws_gb = P.negf_workspace_bytes(plan.handle) / 1e9
-    plan_bits = bits or 32
+    plan_bits = P.negf_plan_product_bits(plan.handle)
     plan.close()
 
     # side measurement: the plain FP64 path on the same inputs (for the
@@ -576,6 +582,7 @@ def run_ours(a, rank, world, local_rank):
                        "parallelism": f"replicas x{world} (energies)",
                        "energy_groups": groups},
             "autotune": tune,
+            "precision_tuning": prec_tune,
             "effective_tflops_paper_count": flops_step / (ms * 1e-3) / 1e12 * world,
             "rel_err_vs_oracle_sampled": rel,
             "band_residual": band_residual,

@@ -70,11 +70,10 @@ typedef enum {
  * NEGF_MIXED: block products on the tensor cores from exact BF16 slices
  *             (each operand cut into integer slices below a power-of-two
  *             scale per row / column, every slice product and FP32 sum exact;
- *             negf_desc.product_bits significant bits, 32 by default),
- *             per-block inverses in FP64; inputs and outputs stay complex128.
- *             DDRGF plans (n_domains > 1) keep the interface system (T_S, its
- *             RGF) in FP64.  Closed sub-domains at small eta amplify product
- *             rounding: there product_bits = 48..56 is the setting. */
+ *             negf_desc.product_bits significant bits,
+ *             NEGF_DEFAULT_PRODUCT_BITS by default), per-block inverses in
+ *             FP64; inputs and outputs stay complex128.  DDRGF plans
+ *             (n_domains > 1) keep the interface system in FP64. */
 typedef enum { NEGF_FP64 = 0, NEGF_MIXED = 1 } negf_precision;
 
 /* Output selection bits (negf_desc.outputs). */
@@ -120,15 +119,23 @@ typedef struct {
                                          NEGF_OUT_GRAD.  < 0: NEGF_ERR_ARG.     */
   int32_t product_bits;               /* NEGF_MIXED: significant bits of the
                                          tensor-core block products, 16..56
-                                         (0 = 32 for RGF, 56 for DDRGF plans);
-                                         more bits trade speed for accuracy on
-                                         ill-conditioned problems.  Products
+                                         (0 = NEGF_DEFAULT_PRODUCT_BITS, which
+                                         meets 1e-5 on chains with localised
+                                         states at eta = 1e-6;
+                                         negf_tune_precision narrows it where
+                                         the caller's inputs allow); more bits
+                                         trade speed for accuracy.  Products
                                          too long for exact slices at that
                                          width (K x slices beyond the FP32
-                                         sums) run as FP64 DMMA products.      */
+                                         sums) run as FP64 DMMA products.
+                                         DDRGF plans form the closed
+                                         sub-domains' corner blocks with
+                                         56-bit products whatever the width. */
 } negf_desc;
 
 #define NEGF_MAX_BLOCK 160
+#define NEGF_DEFAULT_PRODUCT_BITS 42
+#define NEGF_TUNE_BITS_CANDIDATES 3   /* widths negf_tune_precision tries: 32 42 48 */
 #define NEGF_MAX_GROUPS 8   /* energy groups (concurrent streams) per plan */
 #define NEGF_AUTOTUNE_CANDIDATES 6   /* group counts negf_autotune times: 1 2 3 4 6 8 */
 
@@ -299,6 +306,25 @@ negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* s
                           const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
                           negf_c128* G_band, negf_c128* G_1N, int32_t* info, int32_t reps,
                           int32_t* best_groups, double* ms);
+
+/* Precision tuner (mixed plans): solves the caller's inputs once with
+ * 56-bit products into G_band_ref / G_1N_ref (caller-owned device buffers of
+ * the outputs' sizes), then with 32, 42 and 48 bits into G_band / G_1N,
+ * and keeps for the plan's later calls the narrowest width whose band and
+ * G_1N lie within tol of the 56-bit reference at every energy (relative
+ * Frobenius norm per energy and output kind); 56 if none does.  The choice
+ * holds for inputs like the tuned ones: re-tune when H, Sigma or the
+ * energies change in kind.  bits_out / dev_out (nullable): the kept width
+ * and its largest deviation.  Allocates 4 n_energies doubles for the
+ * duration of the call; synchronises the plan's stream.
+ * NEGF_ERR_UNSUPPORTED for an FP64 plan. */
+negf_status negf_tune_precision(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                                const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                                negf_c128* G_band, negf_c128* G_1N, int32_t* info, negf_c128* G_band_ref,
+                                negf_c128* G_1N_ref, double tol, int32_t* bits_out, double* dev_out);
+
+/* The plan's product width in bits (0 for FP64 plans); -1 for NULL. */
+int32_t negf_plan_product_bits(const negf_plan_t* p);
 
 /* The plan's current number of energy groups; -1 for NULL. */
 int32_t negf_plan_groups(const negf_plan_t* p);

@@ -40,6 +40,8 @@ NEGF_OUT_GRAD = 8
 NEGF_OUT_LESSER = 16
 
 NEGF_MAX_BLOCK = 160
+NEGF_DEFAULT_PRODUCT_BITS = 42
+TUNE_BITS = (32, 42, 48)   # the candidates of negf_tune_precision, in its order
 
 NEGF_PROF_INV = 0
 NEGF_PROF_GEMM_F64 = 1
@@ -54,7 +56,8 @@ EXPORTED = [
     "negf_plan_set_groups", "negf_lesser", "negf_solve_host",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
-    "negf_fp64_peak", "negf_plan_set_wait_limit", "negf_grad_strided",
+    "negf_fp64_peak", "negf_plan_set_wait_limit", "negf_grad_strided", "negf_tune_precision",
+    "negf_plan_product_bits",
 ]
 
 NEGF_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -153,6 +156,11 @@ def _load():
     lib.negf_plan_set_wait_limit.restype = st
     lib.negf_grad_strided.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, i64, vp, i64, vp]
     lib.negf_grad_strided.restype = st
+    lib.negf_tune_precision.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, ctypes.c_double,
+                                        ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
+    lib.negf_tune_precision.restype = st
+    lib.negf_plan_product_bits.argtypes = [vp]
+    lib.negf_plan_product_bits.restype = i32
     return lib
 
 
@@ -278,6 +286,22 @@ def negf_autotune(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, in
     st = _lib.negf_autotune(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
                             _ptr(G_band), _ptr(G_1N), _ptr(info), int(reps), ctypes.byref(best), ms)
     return st, int(best.value), list(ms)
+
+
+def negf_tune_precision(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info, G_band_ref, G_1N_ref,
+                        tol):
+    """``negf_tune_precision`` of include/negf.h: returns ``(status, bits, deviation)``."""
+    bits = ctypes.c_int32(0)
+    dev = ctypes.c_double(0.0)
+    st = _lib.negf_tune_precision(plan, _ptr(H), _ptr(sigma_L), _ptr(sigma_R), int(sigma_E_stride), _ptr(E),
+                                  _ptr(G_band), _ptr(G_1N), _ptr(info), _ptr(G_band_ref), _ptr(G_1N_ref),
+                                  float(tol), ctypes.byref(bits), ctypes.byref(dev))
+    return st, int(bits.value), float(dev.value)
+
+
+def negf_plan_product_bits(plan):
+    """``negf_plan_product_bits`` of include/negf.h (argument marshalling only)."""
+    return int(_lib.negf_plan_product_bits(plan))
 
 
 def negf_plan_groups(plan):
@@ -626,6 +650,24 @@ class Plan:
         self._check(st, "negf_autotune")
         self.sync()
         return best, {g: t for g, t in zip(AUTOTUNE_GROUPS, ms) if t >= 0}
+
+    def tune_precision(self, H, sigma_L, sigma_R, E, tol=1e-6, band=True, g1n=True):
+        """Keeps the narrowest product width whose results stay within ``tol``
+        of a 56-bit solve of these inputs (negf_tune_precision).  Returns
+        ``(bits, deviation)``."""
+        torch = self.torch
+        nE = self.n_energies
+        b0, bN = self.sizes[0], self.sizes[-1]
+        mk = lambda *shape: torch.empty(*shape, dtype=torch.complex128, device="cuda")
+        Gb, Gr = (mk(nE, self.band_elems), mk(nE, self.band_elems)) if band else (None, None)
+        G1, G1r = (mk(nE, b0, bN), mk(nE, b0, bN)) if g1n else (None, None)
+        sigma_L, sigma_R, stride = self._sigmas(sigma_L, sigma_R)
+        self._enter()
+        st, bits, dev = negf_tune_precision(self.handle, H, sigma_L, sigma_R, stride, E, Gb, G1, self.info, Gr, G1r,
+                                            tol)
+        self._leave()
+        self._check(st, "negf_tune_precision")
+        return bits, dev
 
     def lesser(self, H, sigma_L, sigma_R, E, sigma_less_L=None, sigma_less_R=None, less_diag=None,
                out_band=None, out_less=None, sync=True):

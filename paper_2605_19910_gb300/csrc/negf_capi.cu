@@ -9,6 +9,7 @@
 // schedule of one call is captured once into a CUDA graph and replayed while
 // the caller's pointers stay the same.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -152,12 +153,9 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   p->N = d->n_blocks; p->w = w; p->nE = d->n_energies; p->n_domains = d->n_domains;
   p->precision = d->precision; p->refine = d->refine_steps; p->outputs = d->outputs;
   p->ckpt = d->checkpoint_every;
-  p->bits = d->product_bits;
-  // DDRGF sub-domains are closed systems (broadened by eta only): near their
-  // internal resonances the halo chains amplify product rounding by up to
-  // ~1e7 (measured on the pentadiagonal 256 x 32 workload at eta = 1e-6), so
-  // mixed DDRGF defaults to 56-bit products
-  if (p->n_domains > 1 && p->precision == NEGF_MIXED && p->bits == 0) p->bits = 56;
+  // mixed plans default to NEGF_DEFAULT_PRODUCT_BITS (negf_tune_precision
+  // can narrow it on the caller's inputs)
+  p->bits = d->product_bits ? d->product_bits : (d->precision == NEGF_MIXED ? NEGF_DEFAULT_PRODUCT_BITS : 0);
   p->b.assign(d->block_sizes, d->block_sizes + d->n_blocks);
   p->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&p->device);
@@ -1024,6 +1022,67 @@ negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* s
 }
 
 int32_t negf_plan_groups(const negf_plan_t* p) { return p ? p->groups : -1; }
+
+int32_t negf_plan_product_bits(const negf_plan_t* p) { return p ? p->bits : -1; }
+
+// Precision tuner: a reference solve at 56 bits, then the candidate widths
+// from the narrowest; the first whose band and G_1N stay within tol of the
+// reference at every energy (relative Frobenius norm per energy and output)
+// is kept for the plan's later calls.
+negf_status negf_tune_precision(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
+                                const negf_c128* sigma_R, int64_t sigma_E_stride, const negf_c128* E,
+                                negf_c128* G_band, negf_c128* G_1N, int32_t* info, negf_c128* G_band_ref,
+                                negf_c128* G_1N_ref, double tol, int32_t* bits_out, double* dev_out) {
+  if (!p || !H || !E || !info || !(tol > 0.0) || (!G_band && !G_1N)) return NEGF_ERR_ARG;
+  if ((G_band && !G_band_ref) || (G_1N && !G_1N_ref)) return NEGF_ERR_ARG;
+  if (p->precision != NEGF_MIXED) return NEGF_ERR_UNSUPPORTED;
+  const int cand[NEGF_TUNE_BITS_CANDIDATES] = {32, 42, 48};
+  const int nE = p->nE;
+  const int64_t s1 = (int64_t)p->b[0] * p->b[p->N - 1];
+  double* d = nullptr;   // per-energy squared norms: band diff, band ref, G_1N diff, G_1N ref
+  cudaError_t ce = cudaMalloc((void**)&d, sizeof(double) * 4 * (size_t)nE);
+  if (ce != cudaSuccess) { g_last_cuda = ce; cudaGetLastError(); return NEGF_ERR_NOMEM; }
+  std::vector<double> h(4 * (size_t)nE);
+  const int bits0 = p->bits;
+  auto solve_at = [&](int bits, negf_c128* gb, negf_c128* g1) -> negf_status {
+    if (p->bits != bits) { p->bits = bits; drop_graph(p); }
+    negf_status st = negf_solve(p, H, sigma_L, sigma_R, sigma_E_stride, E, gb, g1, info);
+    return st != NEGF_OK ? st : negf_sync(p);
+  };
+  negf_status st = solve_at(56, G_band_ref, G_1N_ref);
+  int best = 56;
+  double best_dev = 0.0;
+  for (int k = 0; k < NEGF_TUNE_BITS_CANDIDATES && st == NEGF_OK; ++k) {
+    st = solve_at(cand[k], G_band, G_1N);
+    if (st != NEGF_OK) break;
+    ce = cudaSuccess;
+    if (G_band) {
+      ce = negf::frob2_diff((const double2*)G_band, p->band_elems, (const double2*)G_band_ref, p->band_elems,
+                            p->band_elems, d, nE, p->stream);
+      if (ce == cudaSuccess)
+        ce = negf::frob2((const double2*)G_band_ref, p->band_elems, p->band_elems, d + nE, nE, 0, p->stream);
+    }
+    if (ce == cudaSuccess && G_1N) {
+      ce = negf::frob2_diff((const double2*)G_1N, s1, (const double2*)G_1N_ref, s1, s1, d + 2 * nE, nE, p->stream);
+      if (ce == cudaSuccess) ce = negf::frob2((const double2*)G_1N_ref, s1, s1, d + 3 * nE, nE, 0, p->stream);
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h.data(), d, sizeof(double) * 4 * nE, cudaMemcpyDeviceToHost, p->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(p->stream);
+    if (ce != cudaSuccess) { st = cuda_status(ce); break; }
+    double dev = 0.0;
+    for (int e = 0; e < nE; ++e) {
+      if (G_band) dev = std::max(dev, std::sqrt(h[e] / std::max(h[nE + e], 1e-300)));
+      if (G_1N) dev = std::max(dev, std::sqrt(h[2 * nE + e] / std::max(h[3 * nE + e], 1e-300)));
+    }
+    if (dev < tol) { best = cand[k]; best_dev = dev; break; }
+  }
+  cudaFree(d);
+  if (st != NEGF_OK) best = bits0;
+  if (p->bits != best) { p->bits = best; drop_graph(p); }
+  if (bits_out) *bits_out = best;
+  if (dev_out) *dev_out = best_dev;
+  return st;
+}
 
 negf_status negf_plan_set_groups(negf_plan_t* p, int32_t groups) {
   if (!p || groups < 1 || groups > (int)p->side.size() + 1) return NEGF_ERR_ARG;

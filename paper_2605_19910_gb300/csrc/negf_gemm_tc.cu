@@ -140,10 +140,6 @@ __device__ __forceinline__ uint32_t f32_of_field(uint32_t lo, uint32_t hi, int s
 __device__ __forceinline__ uint32_t pack_bf16x2(uint32_t f0, uint32_t f1, uint32_t signs) {
   return __byte_perm(f0, f1, 0x7632u) | signs;
 }
-// BF16 sign bits of elements 2h, 2h+1 of an 8-element sign mask.
-__device__ __forceinline__ uint32_t pair_signs(uint32_t smask8, int h) {
-  return (((smask8 >> (2 * h)) & 1u) << 15) | (((smask8 >> (2 * h + 1)) & 1u) << 31);
-}
 
 // T += (-1)^neg * x exactly on the integer grid of unit 2^E (x: FP64 bits),
 // truncating the bits of x below 2^E (below the product's own resolution).
@@ -326,7 +322,7 @@ __device__ __forceinline__ long long acc_int(uint32_t bits) {
 template <bool S8>
 struct Digits8 {
   uint32_t lo[8], hi[8];
-  uint32_t sgn = 0;
+  uint32_t sw[4];   // BF16 sign bits of each pair of values (bits 15 and 31)
   __device__ __forceinline__ void load(const u64* v, int e_scale, int frac) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -338,8 +334,10 @@ struct Digits8 {
         lo[j] = (uint32_t)f;
         hi[j] = (uint32_t)(f >> 32);
       }
-      sgn |= (uint32_t)(v[j] >> 63) << j;
     }
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+      sw[h] = ((uint32_t)(v[2 * h] >> 48) & 0x8000u) | ((uint32_t)(v[2 * h + 1] >> 32) & 0x80000000u);
   }
   // digit l (0 = most significant) of all 8 values as 4 packed words
   __device__ __forceinline__ void slice(int l, int s, int L, uint32_t smask, uint32_t* out) const {
@@ -354,7 +352,7 @@ struct Digits8 {
         f0 = f32_of_field(lo[2 * h], hi[2 * h], sh, smask);
         f1 = f32_of_field(lo[2 * h + 1], hi[2 * h + 1], sh, smask);
       }
-      out[h] = pack_bf16x2(f0, f1, pair_signs(sgn, h));
+      out[h] = pack_bf16x2(f0, f1, sw[h]);
     }
   }
 };
@@ -413,14 +411,24 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
       for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
       if (lane == 0) e_row[r] = mx < -50000 ? ZERO_EXP : mx;
     }
-  } else {
-    for (int idx = tid - 128; idx < g.k * nt; idx += TC_THREADS - 128) {   // coalesced over columns
-      const int k = idx / nt, c = idx - k * nt;
-      // op(B)(k, c) at B + k sbk + c sbc (op(B) = B^H: the strides swap; the
-      // sign of the imaginary part does not matter here)
-      const ulonglong2 v = ld_bits(B + opb_off<BC>(g, k, n0 + c));
-      atomicMax(&e_col[c], max(exp_bound(v.x), exp_bound(v.y)));
-    }
+  } else if (nt > 0) {
+    // columns of B: thread t scans column t % nt over every (128 / nt)-th K
+    // (coalesced over columns; columns t, t + 128, ... over all K when
+    // nt >= 128) and publishes one running maximum per column
+    const int t = tid - 128, per = nt >= 128 ? 1 : 128 / nt;
+    const int kk = nt >= 128 ? 0 : t / nt;
+    if (kk < per)
+      for (int c = nt >= 128 ? t : t % nt; c < nt; c += 128) {
+        int mx = -100000;
+        for (int k = kk; k < g.k; k += per) {
+          // op(B)(k, c) at B + k sbk + c sbc (op(B) = B^H: the strides swap;
+          // the sign of the imaginary part does not matter here)
+          const ulonglong2 v = ld_bits(B + opb_off<BC>(g, k, n0 + c));
+          mx = max(mx, max(exp_bound(v.x), exp_bound(v.y)));
+        }
+        atomicMax(&e_col[c], mx);
+        if (nt < 128) break;
+      }
   }
   __syncthreads();
   for (int c = tid; c < n_mma; c += TC_THREADS)

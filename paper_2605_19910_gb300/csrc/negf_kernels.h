@@ -108,6 +108,10 @@ cudaError_t reduce_energies(const double2* src, int64_t sSrc, int ldSrc, int nE,
 // out[e] (+)= sum |A[e]_k|^2 over n contiguous elements.
 cudaError_t frob2(const double2* A, int64_t sA, int64_t n, double* out, int batch, int accumulate, cudaStream_t st);
 
+// out[e] = sum |A[e]_k - B[e]_k|^2 over n contiguous elements.
+cudaError_t frob2_diff(const double2* A, int64_t sA, const double2* B, int64_t sB, int64_t n, double* out, int batch,
+                       cudaStream_t st);
+
 // out[e] = sqrt(out[e] * scale).
 cudaError_t sqrt_scale(double* out, int n, double scale, cudaStream_t st);
 

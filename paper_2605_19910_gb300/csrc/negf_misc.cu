@@ -112,12 +112,14 @@ __global__ void reduce_energies_kernel(const double2* __restrict__ src, int64_t 
 }
 
 __global__ void frob2_kernel(const double2* __restrict__ A, int64_t sA, int64_t n, double* __restrict__ out,
-                             int accumulate) {
+                             int accumulate, const double2* __restrict__ Bm = nullptr, int64_t sB = 0) {
   const int e = blockIdx.x;
   const double2* a = A + (int64_t)e * sA;
+  const double2* bb = Bm ? Bm + (int64_t)e * sB : nullptr;
   double acc = 0.0;
   for (int64_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const double2 v = a[idx];
+    double2 v = a[idx];
+    if (bb) { const double2 u = bb[idx]; v.x -= u.x; v.y -= u.y; }
     acc = fma(v.x, v.x, acc);
     acc = fma(v.y, v.y, acc);
   }
@@ -363,6 +365,13 @@ cudaError_t reduce_energies(const double2* src, int64_t sSrc, int ldSrc, int nE,
 cudaError_t frob2(const double2* A, int64_t sA, int64_t n, double* out, int batch, int accumulate, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   frob2_kernel<<<batch, 256, 0, st>>>(A, sA, n, out, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t frob2_diff(const double2* A, int64_t sA, const double2* B, int64_t sB, int64_t n, double* out, int batch,
+                       cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  frob2_kernel<<<batch, 256, 0, st>>>(A, sA, n, out, 0, B, sB);
   return cudaGetLastError();
 }
 

@@ -104,8 +104,8 @@ def test_refinement_recovers_fp64_level_g1n_and_transmission(P, torch, w, N, b):
 
 def test_mixed_wire1024_full_size_sampled(P, torch):
     """1024 blocks with sizes uniform in {96..160} (2-CTA cluster inversions
-    above 119), 128 energies, mixed precision, band + G_1N: two sampled
-    energies against the oracle.  This long disordered wire at eta = 1e-6 has
-    localized states (large |G|), so the products run with 48 bits."""
+    above 119), 128 energies, mixed precision at the default product width,
+    band + G_1N: two sampled energies against the oracle (this long
+    disordered wire at eta = 1e-6 has localized states, large |G|)."""
     prob = workload("wire1024")
-    run_and_compare(P, torch, prob, energies_idx=[5, 97], tol=MIXED_TOL, precision="mixed", product_bits=48)
+    run_and_compare(P, torch, prob, energies_idx=[5, 97], tol=MIXED_TOL, precision="mixed")
