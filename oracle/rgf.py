@@ -277,8 +277,8 @@ def ddrgf_layout(N, n_domains, w, first_blocks=None):
     return pairs
 
 
-def ddrgf_selected(M, sizes, w, n_domains, first_blocks=None, return_parts=False):
-    """``bndiag(M^{-1})`` by single-level DDRGF (Alg. 2).
+def ddrgf_selected(M, sizes, w, n_domains, first_blocks=None, return_parts=False, levels=()):
+    """``bndiag(M^{-1})`` by DDRGF (Alg. 2), single level or recursive.
 
     Reordering ``T_hat = R T R^T`` (Eq. T_hat_overall_structure) puts the
     separator layers (D1) first and the interior sub-domain layers (D2)
@@ -289,8 +289,12 @@ def ddrgf_selected(M, sizes, w, n_domains, first_blocks=None, return_parts=False
        ``w`` block rows and columns are used, Sec. 3 "Data dependencies");
     2. ``T_S = T_hat_11 - T_hat_12 T_hat_22^{-1} T_hat_21``
        (Eq. Schur_complement_in_parallel_DDRGF);
-    3. ``bndiag(T_S^{-1})`` by RGF on the separators grouped into super-layers
-       (block tridiagonal at the sub-domain level, Prop. 4);
+    3. ``bndiag(T_S^{-1})`` on the separators grouped into super-layers
+       (block tridiagonal at the sub-domain level, Prop. 4): by RGF, or, when
+       ``levels`` is not empty, by DDRGF itself (Alg. 2 step 3, "recursive
+       DDRGF"): the super-layer chain of ``T_S`` is cut into ``levels[0]``
+       pairs of one-super-layer separators (``s_1 = 1``) and the next level
+       uses ``levels[1:]``;
     4. the four parts of Eq. 2x2_explicit_inverse_parallel_DDRGF restricted
        to the band: ``G_11 = T_S^{-1}``, ``G_12 = -T_S^{-1} T_12 X``,
        ``G_21 = -X T_21 T_S^{-1}``, ``G_22 = X + X T_21 T_S^{-1} T_12 X``;
@@ -362,7 +366,10 @@ def ddrgf_selected(M, sizes, w, n_domains, first_blocks=None, return_parts=False
         for h in (g - 1, g + 1):
             if 0 <= h < len(seps) and (g, h) not in TSf:
                 TSf[(g, h)] = np.zeros((sp_sizes[g], sp_sizes[h]), np.complex128)
-    GS_f = rgf_selected(TSf, sp_sizes, 1)["band"]
+    if levels:
+        GS_f = ddrgf_selected(TSf, sp_sizes, 1, levels[0], levels=tuple(levels[1:]))["band"]
+    else:
+        GS_f = rgf_selected(TSf, sp_sizes, 1)["band"]
 
     def GS(s, s2):
         ga, oa = loc[s]

@@ -324,6 +324,32 @@ def test_ddrgf_equals_dense(w, N, nd):
     assert rel(Ginv[np.ix_(i1, i1)], inv(TS)) < 1e-11
 
 
+@pytest.mark.parametrize("w,N,nd,levels", [(1, 40, 10, (3,)), (1, 60, 15, (5, 2)), (2, 48, 8, (3,)),
+                                             (1, 64, 16, (4, 2)), (2, 60, 12, (4, 2))])
+def test_recursive_ddrgf_equals_dense(w, N, nd, levels):
+    """Alg. 2 step 3 by DDRGF itself on the separators' chain (2 and 3
+    levels, one-super-layer separators below the first level) gives the
+    dense band."""
+    rng = np.random.default_rng(N + 7)
+    sizes = [int(x) for x in rng.integers(2, 5, size=N)]
+    M = random_band_matrix(sizes, w, seed=N + 11, diag_shift=3.0)
+    d = O.dense_selected(M, sizes, w)
+    r = O.ddrgf_selected(M, sizes, w, nd, levels=levels)
+    for k in d["band"]:
+        assert rel(r["band"][k], d["band"][k]) < 1e-11, k
+    # a recursion that cuts the separators' chain differently gives the same band
+    r2 = O.ddrgf_selected(M, sizes, w, nd, levels=(2,))
+    for k in d["band"]:
+        assert rel(r2["band"][k], d["band"][k]) < 1e-11, k
+
+
+def test_recursive_ddrgf_rejects_a_level_too_fine_for_its_chain():
+    sizes = [3] * 20
+    M = random_band_matrix(sizes, 1, seed=3, diag_shift=3.0)
+    with pytest.raises(ValueError):
+        O.ddrgf_selected(M, sizes, 1, 5, levels=(4,))   # 5 separators cannot hold 4 pairs of >= 2
+
+
 def test_ddrgf_interface_couplings_cannot_be_dropped():
     # the "orange" next-separator couplings (Sec. 3, after Prop. 4) matter
     sizes = [3] * 16
