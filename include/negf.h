@@ -90,9 +90,11 @@ typedef struct {
   const int32_t* block_sizes;         /* host array of N sizes b_i, 1 <= b_i <= NEGF_MAX_BLOCK */
   int32_t band_n;                     /* n = 3 or 5 (w = (n-1)/2)              */
   int32_t n_energies;                 /* >= 1                                  */
-  int32_t n_domains;                  /* 1 = plain RGF, >1 = single-level DDRGF,
-                                         0 = chosen by negf_auto_domains (plain
-                                         RGF for plans with NEGF_OUT_GRAD)
+  int32_t n_domains;                  /* 1 = plain RGF, >1 = DDRGF pairs,
+                                         0 = chosen with the interface levels
+                                         by negf_ddrgf_model from a measured
+                                         r_inv (plain RGF for plans with
+                                         NEGF_OUT_GRAD)
                                          (Alg. 2): sub-domain sweeps in the
                                          plan's precision, interface Schur
                                          system and its RGF in FP64            */
@@ -131,6 +133,18 @@ typedef struct {
                                          DDRGF plans form the closed
                                          sub-domains' corner blocks with
                                          56-bit products whatever the width. */
+  int32_t n_levels;                   /* DDRGF plans: levels of the interface
+                                         recursion below the first (0 = the
+                                         separators' chain by sequential
+                                         sweeps, Alg. 2 step 3 "via RGF")    */
+  const int32_t* level_domains;       /* host, n_levels entries or NULL:
+                                         level k + 2 cuts the previous level's
+                                         chain of separators into
+                                         level_domains[k] pairs (a group of
+                                         separators, then one separator; at
+                                         least 2 per pair), balanced by count
+                                         (Alg. 2 step 3 "recursive DDRGF",
+                                         s_1 = 1 below the first level)       */
 } negf_desc;
 
 #define NEGF_MAX_BLOCK 160
@@ -157,6 +171,44 @@ size_t negf_workspace_bytes(const negf_plan_t* p);
 
 /* The plan's number of DDRGF (D2, D1) pairs (1 = plain RGF); -1 for NULL. */
 int32_t negf_plan_n_domains(const negf_plan_t* p);
+
+/* The plan's interface levels below the first (their count, or -1 for NULL);
+ * up to cap pair counts into level_domains (nullable). */
+int32_t negf_plan_levels(const negf_plan_t* p, int32_t* level_domains, int32_t cap);
+
+/* The paper's DDRGF cost model (Sec. 3, Eq. cost_model_DDRGF with Eq.
+ * cost_model_RGF) evaluated for a GPU; pure host arithmetic.  Costs are in
+ * units of one batched block product: r_RGF(l) = l (4 + r_LU + 3 r_GETRS) -
+ * (4 + 2 r_GETRS) with r_LU = r_inv (the measured ratio of a batched block
+ * inversion to a batched block product, negf_measure_r_inv) and r_GETRS = 1
+ * (products with explicit inverses are products); the paper's
+ * n_tasks / n_threads becomes the wave factor
+ * max(1, n_tasks n_E / slots, n_tasks / 128) (slots: inversion CTAs resident
+ * on sm_count SMs for the largest block; concurrent tasks are graph branches,
+ * of which at most ~128 kernels run at once).
+ * Level 1 pairs have s2 in {2, 3, 4, 6, ..., 128} w layers and s1 = w
+ * separator layers and at most 128 pairs (one graph branch per pair);
+ * deeper levels s2 in {1, 2, 3, 4}, s1 = 1 (the paper's
+ * auto-tuner table), up to max_levels levels below the first, each level's
+ * Schur complement holding l_S = n_tasks s1 nodes, n_tasks = floor(l /
+ * (s1 + s2)) (the paper rounds up; here every pair holds a whole group and
+ * its separator).  Returns the pair count
+ * of the cheapest choice (1 = plain RGF); level_domains (nullable, up to
+ * max_levels entries) / n_levels receive the deeper levels' pair counts;
+ * cost_rgf / cost_ddrgf (nullable): the two model costs.  1 for invalid
+ * arguments. */
+int32_t negf_ddrgf_model(int32_t n_blocks, const int32_t* block_sizes, int32_t band_n, int32_t n_energies,
+                         int32_t sm_count, double r_inv, int32_t max_levels, int32_t* level_domains,
+                         int32_t* n_levels, double* cost_rgf, double* cost_ddrgf);
+
+/* Measures r_inv for b x b blocks on the current device with the library's
+ * own kernels: the CUDA-event time of a batched FP64 inversion of `batch`
+ * blocks over that of a batched block product of the same blocks in the
+ * given precision (NEGF_MIXED: tensor-core products at the default width),
+ * 10 repetitions each after 3 warm-ups.  The result is also cached for
+ * negf_plan's n_domains = 0 choice.  Allocates and frees its operands;
+ * synchronous on cuda_stream (NULL = legacy default stream). */
+negf_status negf_measure_r_inv(int32_t b, int32_t batch, int32_t precision, double* r_inv, void* cuda_stream);
 
 /* RGF / DDRGF choice made for n_domains = 0 (pure host arithmetic, no device
  * call).  Cost model: a layer step over x independent block problems costs

@@ -57,7 +57,7 @@ EXPORTED = [
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
     "negf_fp64_peak", "negf_plan_set_wait_limit", "negf_grad_strided", "negf_tune_precision",
-    "negf_plan_product_bits",
+    "negf_plan_product_bits", "negf_plan_levels", "negf_ddrgf_model", "negf_measure_r_inv",
 ]
 
 NEGF_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -93,6 +93,8 @@ class negf_desc(ctypes.Structure):
         ("outputs", ctypes.c_int32),
         ("checkpoint_every", ctypes.c_int32),
         ("product_bits", ctypes.c_int32),
+        ("n_levels", ctypes.c_int32),
+        ("level_domains", ctypes.POINTER(ctypes.c_int32)),
     ]
 
 
@@ -161,6 +163,14 @@ def _load():
     lib.negf_tune_precision.restype = st
     lib.negf_plan_product_bits.argtypes = [vp]
     lib.negf_plan_product_bits.restype = i32
+    lib.negf_plan_levels.argtypes = [vp, ctypes.POINTER(i32), i32]
+    lib.negf_plan_levels.restype = i32
+    lib.negf_ddrgf_model.argtypes = [i32, ctypes.POINTER(i32), i32, i32, i32, ctypes.c_double, i32,
+                                     ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
+    lib.negf_ddrgf_model.restype = i32
+    lib.negf_measure_r_inv.argtypes = [i32, i32, i32, ctypes.POINTER(ctypes.c_double), vp]
+    lib.negf_measure_r_inv.restype = st
     return lib
 
 
@@ -190,8 +200,10 @@ def _ptr(x):
 
 def negf_plan(block_sizes, band_n=3, n_energies=1, n_domains=1, domain_first_block=None,
               precision=NEGF_FP64, refine_steps=0, outputs=NEGF_OUT_BAND | NEGF_OUT_G1N,
-              checkpoint_every=0, stream=None, product_bits=0):
-    """Create a plan; returns an opaque handle (int).  Raises NegfError."""
+              checkpoint_every=0, stream=None, product_bits=0, interface_levels=()):
+    """Create a plan; returns an opaque handle (int).  Raises NegfError.
+    ``interface_levels``: the pair counts of the recursive interface levels
+    (negf_desc.level_domains)."""
     sizes = (ctypes.c_int32 * len(block_sizes))(*[int(b) for b in block_sizes])
     d = negf_desc()
     d.n_blocks = len(block_sizes)
@@ -207,6 +219,10 @@ def negf_plan(block_sizes, band_n=3, n_energies=1, n_domains=1, domain_first_blo
     d.outputs = outputs
     d.checkpoint_every = checkpoint_every
     d.product_bits = product_bits
+    if interface_levels:
+        lv = (ctypes.c_int32 * len(interface_levels))(*[int(x) for x in interface_levels])
+        d.n_levels = len(interface_levels)
+        d.level_domains = lv
     h = ctypes.c_void_p()
     s = _lib.negf_plan(ctypes.byref(h), ctypes.byref(d), stream)
     if s != NEGF_OK:
@@ -302,6 +318,34 @@ def negf_tune_precision(plan, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_
 def negf_plan_product_bits(plan):
     """``negf_plan_product_bits`` of include/negf.h (argument marshalling only)."""
     return int(_lib.negf_plan_product_bits(plan))
+
+
+def negf_plan_levels(plan):
+    """``negf_plan_levels`` of include/negf.h: the interface levels' pair counts (list)."""
+    buf = (ctypes.c_int32 * 16)()
+    n = int(_lib.negf_plan_levels(plan, buf, 16))
+    return [int(buf[k]) for k in range(max(0, n))]
+
+
+def negf_ddrgf_model(block_sizes, band_n, n_energies, sm_count, r_inv, max_levels=4):
+    """``negf_ddrgf_model`` of include/negf.h: returns ``(n_domains, levels, cost_rgf, cost_ddrgf)``."""
+    sizes = (ctypes.c_int32 * len(block_sizes))(*[int(b) for b in block_sizes])
+    lv = (ctypes.c_int32 * max(1, max_levels))()
+    nl = ctypes.c_int32(0)
+    cr, cd = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    nd = int(_lib.negf_ddrgf_model(len(block_sizes), sizes, int(band_n), int(n_energies), int(sm_count),
+                                   float(r_inv), int(max_levels), lv, ctypes.byref(nl), ctypes.byref(cr),
+                                   ctypes.byref(cd)))
+    return nd, [int(lv[k]) for k in range(nl.value)], cr.value, cd.value
+
+
+def negf_measure_r_inv(b, batch, precision=NEGF_FP64, stream=None):
+    """``negf_measure_r_inv`` of include/negf.h: returns r_inv; raises NegfError."""
+    r = ctypes.c_double(0.0)
+    s = _lib.negf_measure_r_inv(int(b), int(batch), int(precision), ctypes.byref(r), stream)
+    if s != NEGF_OK:
+        raise NegfError(s, "negf_measure_r_inv")
+    return r.value
 
 
 def negf_plan_groups(plan):
@@ -531,7 +575,7 @@ class Plan:
 
     def __init__(self, sizes, band_n=3, n_energies=1, n_domains=1, domain_first_block=None,
                  precision="fp64", refine_steps=0, outputs=NEGF_OUT_BAND | NEGF_OUT_G1N,
-                 checkpoint_every=0, stream=None, product_bits=0):
+                 checkpoint_every=0, stream=None, product_bits=0, interface_levels=()):
         import torch
         self.torch = torch
         self.sizes = [int(b) for b in sizes]
@@ -544,7 +588,8 @@ class Plan:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         prec = {"fp64": NEGF_FP64, "mixed": NEGF_MIXED}[precision] if isinstance(precision, str) else precision
         self.handle = negf_plan(self.sizes, band_n, self.n_energies, n_domains, domain_first_block, prec,
-                                refine_steps, outputs, checkpoint_every, self.stream.cuda_stream, product_bits)
+                                refine_steps, outputs, checkpoint_every, self.stream.cuda_stream, product_bits,
+                                interface_levels)
         self.band_elems = negf_band_elems(self.handle)
         self.n_domains = negf_plan_n_domains(self.handle)   # the choice made for n_domains = 0
         self.info = torch.zeros(self.n_energies, dtype=torch.int32, device="cuda")

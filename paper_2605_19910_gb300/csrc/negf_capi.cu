@@ -14,7 +14,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/negf.h"
@@ -58,6 +60,9 @@ negf_status validate(const negf_desc* d) {
     return NEGF_ERR_ARG;
   if (d->checkpoint_every < 0) return NEGF_ERR_ARG;
   if (d->product_bits != 0 && (d->product_bits < 16 || d->product_bits > 56)) return NEGF_ERR_ARG;
+  if (d->n_levels < 0 || (d->n_levels > 0 && !d->level_domains)) return NEGF_ERR_ARG;
+  for (int k = 0; k < d->n_levels; ++k)
+    if (d->level_domains[k] < 1) return NEGF_ERR_ARG;
   for (int i = 0; i < d->n_blocks; ++i)
     if (d->block_sizes[i] < 1 || d->block_sizes[i] > NEGF_MAX_BLOCK) return NEGF_ERR_ARG;
   return NEGF_OK;
@@ -118,6 +123,176 @@ int32_t negf_auto_domains(int32_t n_blocks, const int32_t* block_sizes, int32_t 
 
 int32_t negf_plan_n_domains(const negf_plan_t* p) { return p ? p->n_domains : -1; }
 
+int32_t negf_plan_levels(const negf_plan_t* p, int32_t* level_domains, int32_t cap) {
+  if (!p) return -1;
+  const int n = (int)p->lvl.size();
+  for (int k = 0; k < n && k < cap && level_domains; ++k) level_domains[k] = p->lvl[k];
+  return n;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Eq. cost_model_RGF in units of one block GEMM with explicit inverses: the
+// paper's LU is the inversion (ratio r_inv to a GEMM) and each GETRS is a
+// GEMM with the inverse (r_GETRS = 1):
+//   r_RGF(l) = l (4 + r_LU + 3 r_GETRS) - (4 + 2 r_GETRS).
+double model_rgf(double l, double r_inv) { return l * (7.0 + r_inv) - 6.0; }
+// r_RGF^extra(s2): the paper's values for s2 <= 4; beyond, the first and last
+// rows and columns of the sub-domain inverse by chains of one GEMM per layer.
+double model_extra(int s2) { return s2 <= 2 ? 0.0 : (s2 == 3 ? 2.0 : (s2 == 4 ? 6.0 : 4.0 * (s2 - 1))); }
+
+struct ModelChoice {
+  double cost = 1e300;
+  std::vector<int> s2;    // per level
+};
+
+// Cost of DDRGF from level k on with l layers (nodes) of relative block cube
+// scale `cube`, given the s2 candidates; returns the best and its s2 sequence.
+void model_levels(double l, int s1, double cube, double r_inv, double nE, double slots, int depth, int max_levels,
+                  const std::vector<int>& s2c, ModelChoice& best, std::vector<int>& seq) {
+  // concurrent tasks are graph branches: at most ~128 kernels run at once
+  auto wave = [&](double tasks) { return std::max(std::max(1.0, tasks * nE / slots), tasks / 128.0); };
+  // this level solved by RGF
+  {
+    const double c = wave(1.0) * model_rgf(l, r_inv) * cube;
+    if (c < best.cost && depth > 0) { best.cost = c; best.s2 = seq; }
+  }
+  if (depth >= max_levels) return;
+  for (int s2 : s2c) {
+    if (s2 + s1 > l / 2) continue;                    // at least two pairs
+    // pairs that each hold at least s2 + s1 layers (the paper rounds up; a
+    // pair here must hold its whole group and separator)
+    const double nt = std::floor(l / (double)(s2 + s1));
+    if (nt > 128.0) continue;                          // one graph branch per pair, at most ~128 at once
+    const double lvl = wave(nt) * cube *
+                       (model_rgf(s2, r_inv) + model_extra(s2) + 4.0 * s2 + 4.0 + (4.0 * s2 + 4.0) +
+                        (4.0 * (s2 - 1) + 2.0 * s2));
+    // the next level: l_S = n_tasks s1 layers of super-blocks s1 times larger
+    ModelChoice sub;
+    std::vector<int> seq2 = seq;
+    seq2.push_back(s2);
+    const double cube2 = cube * (double)s1 * s1 * s1;
+    model_levels(nt * s1, 1, cube2, r_inv, nE, slots, depth + 1, max_levels, {1, 2, 3, 4}, sub, seq2);
+    if (lvl + sub.cost < best.cost) { best.cost = lvl + sub.cost; best.s2 = sub.s2; }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// The paper's DDRGF cost model (Eq. cost_model_DDRGF with Eq. cost_model_RGF)
+// evaluated for the GPU: see include/negf.h.
+int32_t negf_ddrgf_model(int32_t n_blocks, const int32_t* block_sizes, int32_t band_n, int32_t n_energies,
+                         int32_t sm_count, double r_inv, int32_t max_levels, int32_t* level_domains,
+                         int32_t* n_levels, double* cost_rgf, double* cost_ddrgf) {
+  if (n_levels) *n_levels = 0;
+  if (n_blocks < 1 || !block_sizes || band_n < 3 || n_energies < 1 || sm_count < 1 || !(r_inv > 0.0)) return 1;
+  const int w = (band_n - 1) / 2;
+  int bmax = 1;
+  for (int i = 0; i < n_blocks; ++i) bmax = std::max(bmax, (int)block_sizes[i]);
+  const double per_cta = (double)bmax * (bmax + 1) * 16.0 + 1024.0;
+  const double slots = bmax <= 119 ? (double)sm_count * std::min(5.0, std::max(1.0, std::floor(233472.0 / per_cta)))
+                                   : std::max(1.0, std::floor(sm_count / 2.0));
+  const double nE = n_energies;
+  const double rgf = std::max(1.0, nE / slots) * model_rgf(n_blocks, r_inv);
+  if (cost_rgf) *cost_rgf = rgf;
+  ModelChoice best;
+  best.cost = rgf;
+  std::vector<int> s2c, seq;
+  for (int m : {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128}) s2c.push_back(m * w);
+  model_levels(n_blocks, w, 1.0, r_inv, nE, slots, 0, std::max(1, (int)max_levels + 1), s2c, best, seq);
+  if (cost_ddrgf) *cost_ddrgf = best.cost;
+  if (best.s2.empty()) return 1;                      // plain RGF
+  // level 1: pairs of s2 + w layers; deeper levels: pairs of s2 + 1 nodes
+  double l = n_blocks;
+  int nd = 1;
+  for (size_t k = 0; k < best.s2.size(); ++k) {
+    const int s1 = k == 0 ? w : 1;
+    const int pairs = (int)std::floor(l / (double)(best.s2[k] + s1));
+    if (k == 0) nd = pairs;
+    else if (level_domains && (int)k - 1 < max_levels) level_domains[k - 1] = pairs;
+    l = pairs;
+  }
+  if (n_levels) *n_levels = (int)best.s2.size() - 1;
+  return nd;
+}
+
+}  // extern "C"
+
+namespace {
+std::mutex g_ratio_mu;
+std::map<std::tuple<int, int, int>, double> g_ratio_cache;   // (device, b, precision) -> r_inv
+}  // namespace
+
+extern "C" {
+
+negf_status negf_measure_r_inv(int32_t b, int32_t batch, int32_t precision, double* r_inv, void* cuda_stream) {
+  if (b < 1 || b > NEGF_MAX_BLOCK || batch < 1 || !r_inv || (precision != NEGF_FP64 && precision != NEGF_MIXED))
+    return NEGF_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NEGF_ERR_CUDA;
+  cudaError_t e = negf::kernels_init();
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t elems = (size_t)batch * b * b;
+  double2 *A = nullptr, *B = nullptr, *Cm = nullptr;
+  int32_t* info = nullptr;
+  int* err = nullptr;
+  e = cudaMalloc((void**)&A, elems * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&B, elems * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&Cm, elems * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&info, sizeof(int32_t) * batch + sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(A); cudaFree(B); cudaFree(Cm); cudaFree(info);
+    g_last_cuda = e; cudaGetLastError();
+    return NEGF_ERR_NOMEM;
+  }
+  err = reinterpret_cast<int*>(info + batch);
+  cudaEvent_t a = nullptr, z = nullptr;
+  float t_inv = 0.f, t_mm = 0.f;
+  e = cudaMemsetAsync(info, 0, sizeof(int32_t) * batch + sizeof(int), st);
+  if (e == cudaSuccess) e = negf::set_identity(A, (int64_t)b * b, b, batch, st);   // regular operands
+  if (e == cudaSuccess) e = negf::set_identity(B, (int64_t)b * b, b, batch, st);
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&z);
+  ZGemm g;
+  g.m = b; g.n = b; g.k = b;
+  g.A = A; g.sA = (int64_t)b * b; g.lda = b;
+  g.B = B; g.sB = (int64_t)b * b; g.ldb = b;
+  g.C = Cm; g.sC = (int64_t)b * b; g.ldc = b;
+  g.errword = err;
+  g.bits = NEGF_DEFAULT_PRODUCT_BITS;
+  g.batch = batch;
+  auto prod = [&]() { return precision == NEGF_MIXED ? negf::zgemm_tc(g, st) : negf::zgemm_f64(g, st); };
+  const int reps = 10;
+  for (int r = 0; r < 3 && e == cudaSuccess; ++r) {   // warm-up
+    e = negf::zinv_f64(A, (int64_t)b * b, Cm, (int64_t)b * b, b, batch, info, 1, err, st);
+    if (e == cudaSuccess) e = prod();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(a, st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r)
+    e = negf::zinv_f64(A, (int64_t)b * b, Cm, (int64_t)b * b, b, batch, info, 1, err, st);
+  if (e == cudaSuccess) e = cudaEventRecord(z, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(z);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t_inv, a, z);
+  if (e == cudaSuccess) e = cudaEventRecord(a, st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = prod();
+  if (e == cudaSuccess) e = cudaEventRecord(z, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(z);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t_mm, a, z);
+  if (a) cudaEventDestroy(a);
+  if (z) cudaEventDestroy(z);
+  cudaFree(A); cudaFree(B); cudaFree(Cm); cudaFree(info);
+  if (e != cudaSuccess) return cuda_status(e);
+  *r_inv = t_mm > 0.f ? (double)t_inv / (double)t_mm : 1.0;
+  std::lock_guard<std::mutex> lk(g_ratio_mu);
+  g_ratio_cache[std::make_tuple(dev, (int)b, (int)precision)] = *r_inv;
+  return NEGF_OK;
+}
+
 negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream) {
   if (!out) return NEGF_ERR_ARG;
   *out = nullptr;
@@ -125,15 +300,37 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   if (v != NEGF_OK) return v;
   negf_desc dd_auto = *din;
   const negf_desc* d = &dd_auto;
+  std::vector<int32_t> auto_levels(8, 0);
   if (dd_auto.n_domains == 0) {
+    // the paper's cost model (Eq. cost_model_DDRGF) with this GPU's measured
+    // ratio of a batched block inversion to a batched block product picks
+    // plain RGF or DDRGF, its pair count and the interface levels
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
       cudaGetLastError();
       sms = 152;
     }
-    dd_auto.n_domains = (din->outputs & NEGF_OUT_GRAD)
-                            ? 1
-                            : negf_auto_domains(din->n_blocks, din->block_sizes, din->band_n, din->n_energies, sms);
+    if (din->outputs & NEGF_OUT_GRAD) {
+      dd_auto.n_domains = 1;
+    } else {
+      int bmax = 1;
+      for (int i = 0; i < din->n_blocks; ++i) bmax = std::max(bmax, (int)din->block_sizes[i]);
+      double r = 0.0;
+      {
+        std::lock_guard<std::mutex> lk(g_ratio_mu);
+        auto it = g_ratio_cache.find(std::make_tuple(dev, bmax, (int)din->precision));
+        if (it != g_ratio_cache.end()) r = it->second;
+      }
+      if (r <= 0.0) {
+        const negf_status ms = negf_measure_r_inv(bmax, std::min(din->n_energies, 512), din->precision, &r, nullptr);
+        if (ms != NEGF_OK) return ms;
+      }
+      int32_t nl = 0;
+      dd_auto.n_domains = negf_ddrgf_model(din->n_blocks, din->block_sizes, din->band_n, din->n_energies, sms, r,
+                                           (int32_t)auto_levels.size(), auto_levels.data(), &nl, nullptr, nullptr);
+      dd_auto.n_levels = dd_auto.n_domains > 1 ? nl : 0;
+      dd_auto.level_domains = dd_auto.n_levels ? auto_levels.data() : nullptr;
+    }
   }
   const int w = (d->band_n - 1) / 2;
   if (d->n_domains > 1 && (d->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_UNSUPPORTED;
@@ -205,7 +402,10 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
       p->dom_f[j] = lo;
       p->dom_l[j] = hi - w - 1;
     }
-    if (!dd_layout(p, negf::zinv_max_block())) { delete p; return NEGF_ERR_UNSUPPORTED; }
+    p->lvl.assign(d->level_domains ? d->level_domains : nullptr,
+                  d->level_domains ? d->level_domains + d->n_levels : nullptr);
+    const int lay = dd_layout(p, negf::zinv_max_block());
+    if (lay != 0) { delete p; return lay < 0 ? NEGF_ERR_ARG : NEGF_ERR_UNSUPPORTED; }
     dd_e = p->dd_e + p->band_elems;
   }
 

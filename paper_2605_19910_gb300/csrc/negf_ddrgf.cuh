@@ -20,9 +20,11 @@ namespace {
 // keeps the closed sub-domains' corners accurate near their resonances.
 // ---------------------------------------------------------------------------
 
-// Fills the DDRGF part of the plan (domain layout already in dom_f / dom_l)
-// and returns false if a super-block exceeds the inversion kernel's limit.
-inline bool dd_layout(negf_plan_s* p, int max_block) {
+// Fills the DDRGF part of the plan (domain layout already in dom_f / dom_l,
+// interface levels in lvl).  Returns 0, -1 for interface levels that cut a
+// chain into pairs of fewer than two nodes, 1 if a super-block exceeds the
+// inversion kernel's limit.
+inline int dd_layout(negf_plan_s* p, int max_block) {
   const int N = p->N, w = p->w, nd = p->n_domains;
   p->dom_of.assign(N, -1); p->sep_of.assign(N, -1); p->off_in.assign(N, 0);
   p->Fsz.assign(nd, 0); p->Lsz.assign(nd, 0); p->Psz.assign(nd, 0);
@@ -79,7 +81,7 @@ inline bool dd_layout(negf_plan_s* p, int max_block) {
       }
     }
   }
-  if (p->Bmax > max_block || p->Pmax > max_block || p->FLmax > max_block) return false;
+  if (p->Bmax > max_block || p->Pmax > max_block || p->FLmax > max_block) return 1;
   const int64_t B2 = sq(p->Bmax);
   p->r_xll.resize(nd); p->r_xfl.resize(nd); p->r_xlf.resize(nd);
   p->r_lsS.resize(nd); p->r_lsG.resize(nd); p->r_lsY.resize(nd); p->r_row.resize(nd); p->r_col.resize(nd);
@@ -104,17 +106,78 @@ inline bool dd_layout(negf_plan_s* p, int max_block) {
     p->r_tmp[j] = reg((int64_t)p->Pmax * p->FLmax);
   }
   p->r_A.resize(nd); p->r_cL.resize(nd); p->r_cR.resize(nd); p->r_base.resize(nd); p->r_LL.resize(nd);
-  p->r_RR.resize(nd); p->r_gLin.resize(nd); p->r_gLs.resize(nd); p->r_gRin.resize(nd); p->r_gRs.resize(nd);
+  p->r_RR.resize(nd); p->r_gLs.resize(nd); p->r_gRin.resize(nd); p->r_gRs.resize(nd);
   p->r_Gpp.resize(nd); p->r_Tu.resize(nd); p->r_Tl.resize(nd);
   for (int k = 0; k < nd; ++k) {
     const int64_t P2 = sq(p->Psz[k]), PP = k + 1 < nd ? (int64_t)p->Psz[k] * p->Psz[k + 1] : 0;
     p->r_A[k] = reg(P2); p->r_cL[k] = reg(P2); p->r_cR[k] = reg(P2); p->r_base[k] = reg(P2);
-    p->r_LL[k] = reg(P2); p->r_RR[k] = reg(P2); p->r_gLin[k] = reg(P2); p->r_gLs[k] = reg(P2);
+    p->r_LL[k] = reg(P2); p->r_RR[k] = reg(P2); p->r_gLs[k] = reg(P2);
     p->r_gRin[k] = reg(P2); p->r_gRs[k] = reg(P2); p->r_Gpp[k] = reg(P2);
     p->r_Tu[k] = reg(PP); p->r_Tl[k] = reg(PP);
   }
-  p->r_itL = reg(sq(p->Pmax));
-  p->r_itR = reg(sq(p->Pmax));
+  // interface levels: chain 0 is the separators' chain (T_S); a level with a
+  // pair count in lvl is cut into pairs and its separators form the next chain
+  p->chains.assign(1, DDChain());
+  {
+    DDChain& c0 = p->chains[0];
+    c0.n = nd;
+    c0.sz = p->Psz;
+    c0.D = p->r_base;
+    c0.U.assign(p->r_Tu.begin(), p->r_Tu.end() - 1);
+    c0.L.assign(p->r_Tl.begin(), p->r_Tl.end() - 1);
+    c0.LL = p->r_LL;
+    c0.RR = p->r_RR;
+  }
+  const int64_t PM2 = sq(p->Pmax);
+  for (size_t k = 0; k < p->chains.size(); ++k) {
+    const int n = p->chains[k].n;
+    std::vector<int> sz = p->chains[k].sz;
+    std::vector<negf_plan_s::Reg> t(n), X(n), Y(n), tmp(n);
+    for (int i = 0; i < n; ++i) {
+      t[i] = reg(sq(sz[i]));
+      tmp[i] = reg(PM2);
+      if (i > 0) { X[i] = reg((int64_t)sz[i] * sz[i - 1]); Y[i] = reg((int64_t)sz[i - 1] * sz[i]); }
+    }
+    p->chains[k].t = t; p->chains[k].X = X; p->chains[k].Y = Y; p->chains[k].tmp = tmp;
+    if (k >= p->lvl.size()) continue;              // the deepest level: sequential sweeps
+    const int np = p->lvl[k];
+    std::vector<int> f(np), l(np), nsz(np);
+    for (int J = 0; J < np; ++J) {
+      const int lo = (int)((int64_t)J * n / np), hi = (int)((int64_t)(J + 1) * n / np);   // pair = [lo, hi)
+      if (hi - lo < 2) return -1;
+      f[J] = lo; l[J] = hi - 2;
+      nsz[J] = sz[hi - 1];
+    }
+    std::vector<negf_plan_s::Reg> row(np), col(np), xll(np), s1(np), s2(np), cL(n), cR(n);
+    for (int J = 0; J < np; ++J) {
+      row[J] = reg(2 * (int64_t)sz[f[J]] * p->Pmax);
+      col[J] = reg(2 * (int64_t)p->Pmax * sz[f[J]]);
+      xll[J] = reg(sq(sz[l[J]]));
+      s1[J] = reg(PM2);
+      s2[J] = reg(PM2);
+      const int q = l[J] + 1;
+      cL[q] = reg(sq(sz[q]));
+      cR[q] = reg(sq(sz[q]));
+    }
+    DDChain h;
+    h.n = np;
+    h.sz = nsz;
+    for (int q = 0; q < np; ++q) {
+      h.D.push_back(reg(sq(nsz[q])));
+      h.LL.push_back(reg(sq(nsz[q])));
+      h.RR.push_back(reg(sq(nsz[q])));
+      if (q + 1 < np) {
+        h.U.push_back(reg((int64_t)nsz[q] * nsz[q + 1]));
+        h.L.push_back(reg((int64_t)nsz[q + 1] * nsz[q]));
+      }
+    }
+    DDChain& c = p->chains[k];
+    c.np = np; c.f = f; c.l = l;
+    c.row = row; c.col = col; c.xll = xll; c.s1 = s1; c.s2 = s2; c.cL = cL; c.cR = cR;
+    c.child = (int)p->chains.size();
+    p->chains.push_back(h);                        // may reallocate: no reference kept across
+  }
+  if ((int)p->chains.size() != (int)p->lvl.size() + 1) return -1;
   p->r_g1 = reg(2 * (int64_t)p->b[0] * p->Pmax);
   p->r_g1t = reg((int64_t)p->b[0] * p->Pmax);
   // energy-independent M super-blocks between F / L and the separators
@@ -126,7 +189,7 @@ inline bool dd_layout(negf_plan_s* p, int max_block) {
     p->mlq_off[j] = hreg((int64_t)p->Lsz[j] * p->Psz[j]);
     p->mql_off[j] = hreg((int64_t)p->Psz[j] * p->Lsz[j]);
   }
-  return true;
+  return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -393,51 +456,214 @@ struct DD {
       NEGF_TRY(comb(p->r_base[k], P2, &p->r_A[k], 1.0, &p->r_cL[k], -1.0, k + 1 < nd ? &p->r_cR[k] : nullptr, -1.0,
                     nullptr, 0.0));
     }
-    // left-connected sweep over the separators
+    // left / right self-energies of every separator on T_S's chain (by
+    // sequential sweeps or the recursion), then the connected Green's
+    // functions step 4 needs
+    NEGF_TRY(chain_solve(0));
     for (int k = 0; k < nd; ++k) {
-      const int P = p->Psz[k];
-      const int64_t P2 = sq(P);
-      const negf_plan_s::Reg* LLk = nullptr;
-      if (k > 0) {   // LL_k = T_S[k,k-1] gLin_{k-1} T_S[k-1,k]
-        const int Pm = p->Psz[k - 1];
-        double2* T = R(p->r_itL);
-        NEGF_TRY(mm(0, P, Pm, Pm, R(p->r_Tl[k - 1]), p->r_Tl[k - 1].sz, Pm, R(p->r_gLin[k - 1]), p->r_gLin[k - 1].sz, Pm,
-                    T, p->r_itL.sz, Pm, 1.0));
-        NEGF_TRY(mm(0, P, P, Pm, T, p->r_itL.sz, Pm, R(p->r_Tu[k - 1]), p->r_Tu[k - 1].sz, P, R(p->r_LL[k]),
-                    p->r_LL[k].sz, P, 1.0));
-        LLk = &p->r_LL[k];
-      }
-      if (k + 1 < nd) {
-        NEGF_TRY(comb(p->r_gLin[k], P2, &p->r_base[k], 1.0, LLk, -1.0, nullptr, 0.0, nullptr, 0.0));
-        NEGF_TRY(inv_reg(p->r_gLin[k], k));
+      const int64_t P2 = sq(p->Psz[k]);
+      const negf_plan_s::Reg* LLk = k > 0 ? &p->r_LL[k] : nullptr;
+      const negf_plan_s::Reg* RRk = k + 1 < nd ? &p->r_RR[k] : nullptr;
+      if (k + 1 < nd) {   // gL at separator k without sub-domain k + 1
         NEGF_TRY(comb(p->r_gLs[k], P2, &p->r_A[k], 1.0, &p->r_cL[k], -1.0, LLk, -1.0, nullptr, 0.0));
         NEGF_TRY(inv_reg(p->r_gLs[k], k));
       }
-    }
-    // right-connected sweep over the separators, and the diagonals of T_S^{-1}
-    for (int k = nd - 1; k >= 0; --k) {
-      const int P = p->Psz[k];
-      const int64_t P2 = sq(P);
-      const negf_plan_s::Reg* RRk = nullptr;
-      if (k + 1 < nd) {   // RR_k = T_S[k,k+1] gRin_{k+1} T_S[k+1,k]
-        const int Pn = p->Psz[k + 1];
-        double2* T = R(p->r_itR);
-        NEGF_TRY(mm(0, P, Pn, Pn, R(p->r_Tu[k]), p->r_Tu[k].sz, Pn, R(p->r_gRin[k + 1]), p->r_gRin[k + 1].sz, Pn, T,
-                    p->r_itR.sz, Pn, 1.0));
-        NEGF_TRY(mm(0, P, P, Pn, T, p->r_itR.sz, Pn, R(p->r_Tl[k]), p->r_Tl[k].sz, P, R(p->r_RR[k]), p->r_RR[k].sz, P,
-                    1.0));
-        RRk = &p->r_RR[k];
-      }
-      if (k > 0) {
+      if (k > 0) {        // gR at separator k including sub-domain k (the G_1N chain)
         NEGF_TRY(comb(p->r_gRin[k], P2, &p->r_base[k], 1.0, RRk, -1.0, nullptr, 0.0, nullptr, 0.0));
         NEGF_TRY(inv_reg(p->r_gRin[k], k));
       }
       NEGF_TRY(comb(p->r_gRs[k], P2, &p->r_A[k], 1.0, k + 1 < nd ? &p->r_cR[k] : nullptr, -1.0, RRk, -1.0, nullptr, 0.0));
       NEGF_TRY(inv_reg(p->r_gRs[k], k));
-      NEGF_TRY(comb(p->r_Gpp[k], P2, &p->r_base[k], 1.0, k > 0 ? &p->r_LL[k] : nullptr, -1.0, RRk, -1.0, nullptr, 0.0));
+      NEGF_TRY(comb(p->r_Gpp[k], P2, &p->r_base[k], 1.0, LLk, -1.0, RRk, -1.0, nullptr, 0.0));
       NEGF_TRY(inv_reg(p->r_Gpp[k], k));
     }
     return cudaSuccess;
+  }
+
+  // ---- the interface's chains (Alg. 2 step 3) ----------------------------
+  // Chain c: nodes 0..n-1 with diagonal D_k, couplings U_k (k, k+1) and L_k
+  // (k+1, k); LL_k = L_{k-1} gL_{k-1} U_{k-1} and RR_k = U_k gR_{k+1} L_k are
+  // the node's left / right self-energies, gL / gR the left- / right-connected
+  // Green's functions (LL_0 and RR_{n-1} are absent).
+  const negf_plan_s::Reg* opt(const std::vector<negf_plan_s::Reg>& v, int k, bool present) const {
+    return present ? &v[k] : nullptr;
+  }
+
+  // C = alpha A B on node-sized per-energy regions (FP64).
+  cudaError_t mmr(int m, int n, int k, const negf_plan_s::Reg& A, const negf_plan_s::Reg& B,
+                  const negf_plan_s::Reg& Cr, double alpha, const negf_plan_s::Reg* C1 = nullptr, double beta1 = 1.0) {
+    return mm(0, m, n, k, R(A), A.sz, k, R(B), B.sz, n, R(Cr), Cr.sz, n, alpha, false, C1 ? R(*C1) : nullptr,
+              C1 ? C1->sz : 0, n, beta1);
+  }
+  cudaError_t inv_chain(const negf_plan_s::Reg& src, const negf_plan_s::Reg& dst, int P) {
+    return s.inv(R(src), src.sz, R(dst), dst.sz, P, C, 0);
+  }
+
+  // Sequential sweeps over chain c (the deepest level).
+  cudaError_t chain_sweeps(DDChain& c) {
+    const int n = c.n;
+    // left: gL_0 = D_0^{-1}; LL_k = L_{k-1} gL_{k-1} U_{k-1}, gL_k = (D_k - LL_k)^{-1}
+    NEGF_TRY(inv_chain(c.D[0], c.t[0], c.sz[0]));
+    for (int k = 1; k < n; ++k) {
+      NEGF_TRY(mmr(c.sz[k], c.sz[k - 1], c.sz[k - 1], c.L[k - 1], c.t[k - 1], c.tmp[k], 1.0));
+      NEGF_TRY(mmr(c.sz[k], c.sz[k], c.sz[k - 1], c.tmp[k], c.U[k - 1], c.LL[k], 1.0));
+      if (k + 1 < n) {
+        NEGF_TRY(comb(c.t[k], sq(c.sz[k]), &c.D[k], 1.0, &c.LL[k], -1.0, nullptr, 0.0, nullptr, 0.0));
+        NEGF_TRY(inv_chain(c.t[k], c.t[k], c.sz[k]));
+      }
+    }
+    // right: gR_{n-1} = D_{n-1}^{-1}; RR_k = U_k gR_{k+1} L_k, gR_k = (D_k - RR_k)^{-1}
+    NEGF_TRY(inv_chain(c.D[n - 1], c.t[n - 1], c.sz[n - 1]));
+    for (int k = n - 2; k >= 0; --k) {
+      NEGF_TRY(mmr(c.sz[k], c.sz[k + 1], c.sz[k + 1], c.U[k], c.t[k + 1], c.tmp[k], 1.0));
+      NEGF_TRY(mmr(c.sz[k], c.sz[k], c.sz[k + 1], c.tmp[k], c.L[k], c.RR[k], 1.0));
+      if (k > 0) {
+        NEGF_TRY(comb(c.t[k], sq(c.sz[k]), &c.D[k], 1.0, &c.RR[k], -1.0, nullptr, 0.0, nullptr, 0.0));
+        NEGF_TRY(inv_chain(c.t[k], c.t[k], c.sz[k]));
+      }
+    }
+    return cudaSuccess;
+  }
+
+  // Step 1 on chain c, pair J: corners of the closed group [f, l]: X_FF = t_f
+  // of the right-connected sweep, X_FL / X_LF from its first row / column,
+  // X_LL from the left-connected sweep.
+  double2* ring(const negf_plan_s::Reg& r, int slot, int64_t slot_elems) const { return R(r) + slot * slot_elems; }
+  cudaError_t chain_corners(DDChain& c, int J) {
+    const int f = c.f[J], l = c.l[J], Ff = c.sz[f];
+    NEGF_TRY(cp(R(c.D[l]), c.D[l].sz, c.sz[l], R(c.s1[J]), c.s1[J].sz, c.sz[l], c.sz[l], c.sz[l], 1.0, 0, C));
+    for (int k = l; k >= f; --k) {
+      NEGF_TRY(inv_chain(c.s1[J], c.t[k], c.sz[k]));
+      if (k == f) break;
+      const int Bp = c.sz[k - 1], B = c.sz[k];
+      NEGF_TRY(mmr(Bp, B, B, c.U[k - 1], c.t[k], c.Y[k], 1.0));      // Y_k = U_{k-1} t_k
+      NEGF_TRY(mmr(B, Bp, B, c.t[k], c.L[k - 1], c.X[k], 1.0));      // X_k = t_k L_{k-1}
+      NEGF_TRY(mm(0, Bp, Bp, B, R(c.Y[k]), c.Y[k].sz, B, R(c.L[k - 1]), c.L[k - 1].sz, Bp, R(c.s1[J]), c.s1[J].sz, Bp,
+                  -1.0, false, R(c.D[k - 1]), c.D[k - 1].sz, Bp, 1.0));   // S_{k-1} = D_{k-1} - Y_k L_{k-1}
+    }
+    const int64_t sr = (int64_t)Ff * p->Pmax;
+    for (int k = f + 1; k <= l; ++k) {   // X_{F,k} = -X_{F,k-1} Y_k, X_{k,F} = -X_k X_{k-1,F}
+      const int B = c.sz[k], Bp = c.sz[k - 1];
+      const double2* rp = k - 1 == f ? R(c.t[f]) : ring(c.row[J], (k - 1) & 1, sr);
+      const int64_t srp = k - 1 == f ? c.t[f].sz : c.row[J].sz;
+      NEGF_TRY(mm(0, Ff, B, Bp, rp, srp, Bp, R(c.Y[k]), c.Y[k].sz, B, ring(c.row[J], k & 1, sr), c.row[J].sz, B, -1.0));
+      const double2* cpv = k - 1 == f ? R(c.t[f]) : ring(c.col[J], (k - 1) & 1, sr);
+      const int64_t scp = k - 1 == f ? c.t[f].sz : c.col[J].sz;
+      NEGF_TRY(mm(0, B, Ff, Bp, R(c.X[k]), c.X[k].sz, Bp, cpv, scp, Ff, ring(c.col[J], k & 1, sr), c.col[J].sz, Ff, -1.0));
+    }
+    // left-connected sweep: X_LL
+    NEGF_TRY(cp(R(c.D[f]), c.D[f].sz, Ff, R(c.s1[J]), c.s1[J].sz, Ff, Ff, Ff, 1.0, 0, C));
+    for (int k = f; k <= l; ++k) {
+      if (k == l) return inv_chain(c.s1[J], c.xll[J], c.sz[k]);
+      NEGF_TRY(inv_chain(c.s1[J], c.s2[J], c.sz[k]));
+      const int B = c.sz[k], Bn = c.sz[k + 1];
+      NEGF_TRY(mm(0, Bn, B, B, R(c.L[k]), c.L[k].sz, B, R(c.s2[J]), c.s2[J].sz, B, R(c.tmp[k]), c.tmp[k].sz, B, 1.0));
+      NEGF_TRY(mm(0, Bn, Bn, B, R(c.tmp[k]), c.tmp[k].sz, B, R(c.U[k]), c.U[k].sz, Bn, R(c.s1[J]), c.s1[J].sz, Bn, -1.0,
+                  false, R(c.D[k + 1]), c.D[k + 1].sz, Bn, 1.0));
+    }
+    return cudaSuccess;
+  }
+  // corners of pair J's group as (pointer, per-energy stride)
+  const double2* cXFF(DDChain& c, int J, int64_t* st) { *st = c.t[c.f[J]].sz; return R(c.t[c.f[J]]); }
+  const double2* cXFL(DDChain& c, int J, int64_t* st) {
+    const int f = c.f[J], l = c.l[J];
+    if (l == f) { *st = c.t[f].sz; return R(c.t[f]); }
+    *st = c.row[J].sz;
+    return ring(c.row[J], l & 1, (int64_t)c.sz[f] * p->Pmax);
+  }
+  const double2* cXLF(DDChain& c, int J, int64_t* st) {
+    const int f = c.f[J], l = c.l[J];
+    if (l == f) { *st = c.t[f].sz; return R(c.t[f]); }
+    *st = c.col[J].sz;
+    return ring(c.col[J], l & 1, (int64_t)c.sz[f] * p->Pmax);
+  }
+
+  // Step 4 on chain c, pair J: the group's left / right self-energies from
+  // the separators' (open sweeps with the boundary self-energies).
+  cudaError_t chain_open(DDChain& c, int J) {
+    const int f = c.f[J], l = c.l[J], q = l + 1;
+    if (J > 0) {   // LL_f = L_{f-1} (D_p - LL_p)^{-1} U_{f-1}, p = f - 1
+      const int pn = f - 1, P = c.sz[pn];
+      NEGF_TRY(comb(c.s2[J], sq(P), &c.D[pn], 1.0, &c.LL[pn], -1.0, nullptr, 0.0, nullptr, 0.0));
+      NEGF_TRY(inv_chain(c.s2[J], c.s2[J], P));
+      NEGF_TRY(mmr(c.sz[f], P, P, c.L[pn], c.s2[J], c.tmp[f], 1.0));
+      NEGF_TRY(mmr(c.sz[f], c.sz[f], P, c.tmp[f], c.U[pn], c.LL[f], 1.0));
+    }
+    for (int k = f; k <= l; ++k) {   // open left sweep
+      if (k > f) {
+        NEGF_TRY(mmr(c.sz[k], c.sz[k - 1], c.sz[k - 1], c.L[k - 1], c.s1[J], c.tmp[k], 1.0));
+        NEGF_TRY(mmr(c.sz[k], c.sz[k], c.sz[k - 1], c.tmp[k], c.U[k - 1], c.LL[k], 1.0));
+      }
+      if (k == l) break;
+      NEGF_TRY(comb(c.s1[J], sq(c.sz[k]), &c.D[k], 1.0, opt(c.LL, k, k > 0), -1.0, nullptr, 0.0, nullptr, 0.0));
+      NEGF_TRY(inv_chain(c.s1[J], c.s1[J], c.sz[k]));
+    }
+    {   // RR_l = U_l (D_q - RR_q)^{-1} L_l
+      const int P = c.sz[q];
+      NEGF_TRY(comb(c.s2[J], sq(P), &c.D[q], 1.0, opt(c.RR, q, q + 1 < c.n), -1.0, nullptr, 0.0, nullptr, 0.0));
+      NEGF_TRY(inv_chain(c.s2[J], c.s2[J], P));
+      NEGF_TRY(mmr(c.sz[l], P, P, c.U[l], c.s2[J], c.tmp[l], 1.0));
+      NEGF_TRY(mmr(c.sz[l], c.sz[l], P, c.tmp[l], c.L[l], c.RR[l], 1.0));
+    }
+    for (int k = l; k >= f; --k) {   // open right sweep
+      if (k < l) {
+        NEGF_TRY(mmr(c.sz[k], c.sz[k + 1], c.sz[k + 1], c.U[k], c.s1[J], c.tmp[k], 1.0));
+        NEGF_TRY(mmr(c.sz[k], c.sz[k], c.sz[k + 1], c.tmp[k], c.L[k], c.RR[k], 1.0));
+      }
+      if (k == f) break;
+      NEGF_TRY(comb(c.s1[J], sq(c.sz[k]), &c.D[k], 1.0, &c.RR[k], -1.0, nullptr, 0.0, nullptr, 0.0));
+      NEGF_TRY(inv_chain(c.s1[J], c.s1[J], c.sz[k]));
+    }
+    return cudaSuccess;
+  }
+
+  // Left / right self-energies of every node of chain ci.
+  cudaError_t chain_solve(int ci) {
+    if (p->chains[ci].child < 0) return chain_sweeps(p->chains[ci]);
+    const int np = p->chains[ci].np;
+    NEGF_TRY(for_count(np, [&](DD& d, int J) { return d.chain_corners(d.p->chains[ci], J); }));
+    {   // the next level's chain over this level's separators
+      DDChain& c = p->chains[ci];
+      DDChain& h = p->chains[c.child];
+      for (int J = 0; J < np; ++J) {
+        const int q = c.l[J] + 1, P = c.sz[q], lq = c.l[J], Pl = c.sz[lq];
+        // cL_q = L_{l} X_LL U_{l} (the group left of q)
+        NEGF_TRY(mmr(P, Pl, Pl, c.L[lq], c.xll[J], c.tmp[q], 1.0));
+        NEGF_TRY(mmr(P, P, Pl, c.tmp[q], c.U[lq], c.cL[q], 1.0));
+        const negf_plan_s::Reg* cRq = nullptr;
+        if (J + 1 < np) {   // the group right of q: cR_q, and the couplings to the next separator
+          const int f1 = c.f[J + 1], l1 = c.l[J + 1], F = c.sz[f1], Ln = c.sz[l1], q1 = l1 + 1, P1 = c.sz[q1];
+          int64_t sff = 0, sfl = 0, slf = 0;
+          const double2* xff = cXFF(c, J + 1, &sff);
+          const double2* xfl = cXFL(c, J + 1, &sfl);
+          const double2* xlf = cXLF(c, J + 1, &slf);
+          NEGF_TRY(mm(0, P, F, F, R(c.U[q]), c.U[q].sz, F, xff, sff, F, R(c.tmp[q]), c.tmp[q].sz, F, 1.0));
+          NEGF_TRY(mm(0, P, P, F, R(c.tmp[q]), c.tmp[q].sz, F, R(c.L[q]), c.L[q].sz, P, R(c.cR[q]), c.cR[q].sz, P, 1.0));
+          cRq = &c.cR[q];
+          // U'_J = -U_q X_FL U_{l1},  L'_J = -L_{l1} X_LF L_q
+          NEGF_TRY(mm(0, P, Ln, F, R(c.U[q]), c.U[q].sz, F, xfl, sfl, Ln, R(c.tmp[q]), c.tmp[q].sz, Ln, 1.0));
+          NEGF_TRY(mm(0, P, P1, Ln, R(c.tmp[q]), c.tmp[q].sz, Ln, R(c.U[l1]), c.U[l1].sz, P1, R(h.U[J]), h.U[J].sz, P1,
+                      -1.0));
+          NEGF_TRY(mm(0, P1, F, Ln, R(c.L[l1]), c.L[l1].sz, Ln, xlf, slf, F, R(c.tmp[q1]), c.tmp[q1].sz, F, 1.0));
+          NEGF_TRY(mm(0, P1, P, F, R(c.tmp[q1]), c.tmp[q1].sz, F, R(c.L[q]), c.L[q].sz, P, R(h.L[J]), h.L[J].sz, P,
+                      -1.0));
+        }
+        NEGF_TRY(comb(h.D[J], sq(P), &c.D[q], 1.0, &c.cL[q], -1.0, cRq, -1.0, nullptr, 0.0));
+      }
+    }
+    NEGF_TRY(chain_solve(p->chains[ci].child));
+    {   // the separators' self-energies: the adjacent groups plus the next level's
+      DDChain& c = p->chains[ci];
+      DDChain& h = p->chains[c.child];
+      for (int J = 0; J < np; ++J) {
+        const int q = c.l[J] + 1;
+        const int64_t P2 = sq(c.sz[q]);
+        NEGF_TRY(comb(c.LL[q], P2, &c.cL[q], 1.0, J > 0 ? &h.LL[J] : nullptr, 1.0, nullptr, 0.0, nullptr, 0.0));
+        if (J + 1 < np)
+          NEGF_TRY(comb(c.RR[q], P2, &c.cR[q], 1.0, &h.RR[J], 1.0, nullptr, 0.0, nullptr, 0.0));
+      }
+    }
+    return for_count(np, [&](DD& d, int J) { return d.chain_open(d.p->chains[ci], J); });
   }
 
   // Step 4 for domain j: boundary self-energies, the open sub-domain's RGF
@@ -553,11 +779,16 @@ struct DD {
   // Each domain sweeps in its own Schur-window slots; everything else a
   // domain writes is disjoint from the other domains'.
   template <class F>
-  cudaError_t for_domains(F f) {
+  cudaError_t for_domains(F f) { return for_count(nd, f); }
+
+  // Runs f(dd_j, j) for j < cnt (cnt <= n_domains) on the group's domain
+  // streams, concurrently, joined back afterwards.
+  template <class F>
+  cudaError_t for_count(int cnt, F f) {
     const int g = s.grp;
     NEGF_TRY(cudaEventRecord(p->dfork[g], s.st));
-    for (int j = 1; j < nd; ++j) NEGF_TRY(cudaStreamWaitEvent(p->dstream[(size_t)g * nd + j], p->dfork[g], 0));
-    for (int j = 0; j < nd; ++j) {
+    for (int j = 1; j < cnt; ++j) NEGF_TRY(cudaStreamWaitEvent(p->dstream[(size_t)g * nd + j], p->dfork[g], 0));
+    for (int j = 0; j < cnt; ++j) {
       Sweep sj = s;
       sj.sdom = j;
       if (j > 0) {
@@ -568,7 +799,7 @@ struct DD {
       NEGF_TRY(f(dj, j));
       if (j == 0) s.after_first_inv = sj.after_first_inv;
     }
-    for (int j = 1; j < nd; ++j) {
+    for (int j = 1; j < cnt; ++j) {
       NEGF_TRY(cudaEventRecord(p->djoin[(size_t)g * nd + j], p->dstream[(size_t)g * nd + j]));
       NEGF_TRY(cudaStreamWaitEvent(s.st, p->djoin[(size_t)g * nd + j], 0));
     }

@@ -43,6 +43,24 @@ struct DDGroups {
   std::vector<DDReg> t, x, y;
 };
 
+// One level of the DDRGF interface: a block tridiagonal chain of n nodes
+// (the separators of the level above) with per-energy diagonal blocks D,
+// couplings U (node k to k + 1) and L (k + 1 to k), whose left / right
+// self-energies LL / RR every node needs.  A level that recurses is cut into
+// np pairs: a group of nodes [f[J], l[J]] then the separator node l[J] + 1.
+struct DDChain {
+  int n = 0;
+  std::vector<int> sz;                        // node sizes (elements)
+  std::vector<DDReg> D, U, L, LL, RR;         // U / L: n - 1 entries
+  int np = 0, child = -1;                     // pairs, index of the next level (-1: sequential sweeps)
+  std::vector<int> f, l;                      // node range of each pair's group
+  std::vector<DDReg> t, X, Y;                 // closed right sweep per node: t, t L_{k-1}, U_{k-1} t
+  std::vector<DDReg> row, col;                // per pair: rings of the first row / column (2 slots)
+  std::vector<DDReg> xll, s1, s2;             // per pair: X_LL, two node-sized temporaries
+  std::vector<DDReg> cL, cR;                  // per separator node of a recursing level: group contributions
+  std::vector<DDReg> tmp;                     // per node: a sweep temporary
+};
+
 struct negf_plan_s {
   int N = 0, w = 1, nE = 0, n_domains = 1, precision = 0, refine = 0, outputs = 0, ckpt = 0, bits = 0;
   long long wait_limit = -1;       // tensor-core MMA-completion wait polls (< 0: the kernel's default)
@@ -104,10 +122,12 @@ struct negf_plan_s {
   int Pmax = 0, FLmax = 0, Bmax = 0;
   using Reg = DDReg;
   std::vector<DDGroups> grR, grL;               // step-1 groups (fused sweeps) per domain
+  std::vector<int> lvl;                          // pair counts of the recursive interface levels
+  std::vector<DDChain> chains;                   // interface levels: [0] the separators' chain
   std::vector<Reg> r_xll, r_xfl, r_xlf, r_lsS, r_lsG, r_lsY, r_row, r_col;   // per domain, step 1
   std::vector<Reg> r_wr, r_vr, r_sr, r_wl, r_vl, r_sl, r_tmp;                // per domain, step 4
-  std::vector<Reg> r_A, r_cL, r_cR, r_base, r_LL, r_RR, r_gLin, r_gLs, r_gRin, r_gRs, r_Gpp, r_Tu, r_Tl;  // per separator
-  Reg r_itL, r_itR, r_g1, r_g1t;
+  std::vector<Reg> r_A, r_cL, r_cR, r_base, r_LL, r_RR, r_gLs, r_gRin, r_gRs, r_Gpp, r_Tu, r_Tl;  // per separator
+  Reg r_g1, r_g1t;
   int64_t dd_e = 0, hf_e = 0;
   std::vector<int64_t> mfp_off, mpf_off, mlq_off, mql_off;   // M super-blocks (offsets in Hf)
   double2* DDW = nullptr;       // per-energy DDRGF regions

@@ -29,12 +29,14 @@ def P():
     return P
 
 
-def run_dd(P, prob, n_domains, first=None, idx=None, tol=FP64_TOL, precision="fp64", check_ddrgf_oracle=False):
+def run_dd(P, prob, n_domains, first=None, idx=None, tol=FP64_TOL, precision="fp64", check_ddrgf_oracle=False,
+           levels=()):
     import torch
     Hp, sL, sR, E = to_dev(prob, torch)
     nE = len(prob.energies)
     plan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, n_domains=n_domains, domain_first_block=first,
-                  precision=precision, outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_G1N | P.NEGF_OUT_TRANSMISSION)
+                  precision=precision, outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_G1N | P.NEGF_OUT_TRANSMISSION,
+                  interface_levels=levels)
     Gb, G1 = plan.solve(Hp, sL, sR, E)
     T = plan.transmission(Hp, sL, sR, E)
     assert not plan.info.cpu().numpy().any()
@@ -48,7 +50,7 @@ def run_dd(P, prob, n_domains, first=None, idx=None, tol=FP64_TOL, precision="fp
         Tref = O.transmission(ref["G1N"], prob.sigma_L, prob.sigma_R)
         assert abs(T[e] - Tref) < tol * max(1.0, abs(Tref)), (e, T[e], Tref)
         if check_ddrgf_oracle:
-            dd = O.ddrgf_selected(M, prob.sizes, prob.w, n_domains, first)
+            dd = O.ddrgf_selected(M, prob.sizes, prob.w, n_domains, first, levels=levels)
             assert band_rel_err(Gb[e], dd["band"], prob.sizes, prob.w) < tol, e
 
 
@@ -59,6 +61,29 @@ DOM = 4.0   # diagonal shift: layer blocks well conditioned for E < 2 (E = 2 tou
 def test_ddrgf_uniform(P, w, N, nd):
     prob = make_problem(N, b=8, w=w, n_energies=3, eta=1e-3, seed=40 + N, diag_shift=DOM)
     run_dd(P, prob, nd, check_ddrgf_oracle=True)
+
+
+@pytest.mark.parametrize("w,N,nd,levels", [(1, 48, 12, (3,)), (1, 64, 16, (4, 2)), (2, 60, 10, (3,)),
+                                             (1, 40, 10, (5,)), (2, 72, 12, (3, 1))])
+def test_ddrgf_recursive_interface(P, w, N, nd, levels):
+    """Alg. 2 step 3 by DDRGF itself on the separators' chain (2 and 3
+    levels; pairs of one node group and one separator, single-node groups
+    included): parity with RGF at the FP64 bar and with the oracle's
+    recursive DDRGF."""
+    prob = make_problem(N, b=8, w=w, n_energies=3, eta=1e-3, seed=60 + N, diag_shift=DOM)
+    run_dd(P, prob, nd, check_ddrgf_oracle=True, levels=levels)
+
+
+def test_ddrgf_recursive_interface_mixed_and_uneven_sizes(P):
+    prob = make_problem(50, b=None, size_range=(4, 24), w=1, n_energies=4, eta=1e-3, seed=71, diag_shift=DOM)
+    run_dd(P, prob, 10, levels=(3,))
+    run_dd(P, prob, 10, levels=(3,), precision="mixed", tol=MIXED_TOL)
+
+
+def test_ddrgf_recursive_interface_rejects_too_fine_levels(P):
+    with pytest.raises(P.NegfError) as ei:
+        P.Plan([8] * 40, 3, 2, n_domains=10, interface_levels=(6,))   # 10 separators, 6 pairs of >= 2: no
+    assert ei.value.status == P.NEGF_ERR_ARG
 
 
 def test_ddrgf_variable_sizes_and_explicit_split(P):
@@ -158,14 +183,20 @@ def test_ddrgf_wire1024_32_domains_mixed_defaults(P):
 
 
 def test_auto_domains_plans_follow_the_cost_model(P):
+    """n_domains = 0: the paper's cost model (negf_ddrgf_model) with this
+    GPU's measured inversion-to-product ratio picks the pairs and the
+    interface levels; the chosen plan matches the oracle."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    # one energy on a long chain: DDRGF; parity as for an explicit split
-    prob = make_problem(64, b=16, w=1, n_energies=1, eta=1e-3, seed=77, diag_shift=DOM)
-    d = P.negf_auto_domains(prob.sizes, 3, 1, sms)
-    assert d > 1
+    r = P.negf_measure_r_inv(16, 1)
+    assert r > 0
+    # one energy on a long chain: DDRGF with interface levels; parity as for an explicit split
+    prob = make_problem(96, b=16, w=1, n_energies=1, eta=1e-3, seed=77, diag_shift=DOM)
+    nd, levels, crgf, cdd = P.negf_ddrgf_model(prob.sizes, 3, 1, sms, r)
+    assert nd > 1 and cdd < crgf
     plan = P.Plan(prob.sizes, 3, 1, n_domains=0)
-    assert plan.n_domains == d
+    assert plan.n_domains == nd
+    assert P.negf_plan_levels(plan.handle) == levels
     plan.close()
     run_dd(P, prob, 0)
     # many energies: plain RGF
