@@ -83,6 +83,8 @@ def _args():
                     help="skip the side measurement of the Keldysh (G^<) path")
     ap.add_argument("--refine-steps", type=int, default=1,
                     help="refinement steps of the mixed plan's G_1N (the benchmark configuration has one)")
+    ap.add_argument("--no-ddrgf-side", action="store_true",
+                    help="skip the side measurement of DDRGF levels on a few-energy long chain")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -271,7 +273,7 @@ def run_ours(a, rank, world, local_rank):
     import __graft_entry__ as g
     g.build()
     import paper_2605_19910_gb300 as P
-    from workloads import workload
+    from workloads import make_problem, workload
 
     torch.cuda.set_device(local_rank)
     dist = None
@@ -558,6 +560,45 @@ def run_ours(a, rank, world, local_rank):
             grad_side["checkpoint_every_%d" % ck] = {"ms_per_step": gms, "value": job_throughput(world, nE, N, gms),
                                                      "workspace_gb": gws, "steps": k3}
 
+    # side measurement: one energy on a long chain (1024 x 64, diagonally
+    # dominant, eta = 1e-3), where the GPU is not filled by energies: plain
+    # RGF, single-level DDRGF with the cost model's pair count, and the cost
+    # model's recursive choice (negf_ddrgf_model with the measured r_inv)
+    ddrgf_side = None
+    if not a.no_ddrgf_side and rank == 0:
+        dprob = make_problem(1024, b=64, w=1, n_energies=1, eta=1e-3, seed=3, diag_shift=4.0)
+        dH = torch.tensor(P.pack_band(dprob.H, dprob.sizes, 1), device=dev)
+        dsL, dsR = torch.tensor(dprob.sigma_L, device=dev), torch.tensor(dprob.sigma_R, device=dev)
+        dE = torch.tensor(dprob.energies, device=dev)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        r_inv = P.negf_measure_r_inv(64, 1)
+        nd, levels, c_rgf, c_dd = P.negf_ddrgf_model(dprob.sizes, 3, 1, sms, r_inv)
+        ref_band = None
+        ddrgf_side = {"chain": "1024 x 64, 1 energy, eta 1e-3, diagonally dominant", "r_inv": r_inv,
+                      "model": {"n_domains": nd, "levels": levels, "cost_rgf": c_rgf, "cost_ddrgf": c_dd}}
+        for label, kw in (("rgf", dict(n_domains=1)), ("ddrgf_1_level", dict(n_domains=max(nd, 2))),
+                          ("ddrgf_model", dict(n_domains=max(nd, 2), interface_levels=tuple(levels)))):
+            dplan = P.Plan(dprob.sizes, 3, 1, outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_G1N, **kw)
+            db, _ = dplan.solve(dH, dsL, dsR, dE)
+            for _ in range(2):
+                dplan.solve(dH, dsL, dsR, dE, out_band=db, sync=False)
+            dplan.sync()
+            d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            d0.record(stream)
+            for _ in range(5):
+                dplan.solve(dH, dsL, dsR, dE, out_band=db, sync=False)
+            d1.record(stream)
+            torch.cuda.synchronize()
+            dplan.sync()
+            dplan.close()
+            if ref_band is None:
+                ref_band = db.clone()
+                dev_ = 0.0
+            else:
+                dev_ = float(torch.linalg.norm(db - ref_band) / torch.linalg.norm(ref_band))
+            ddrgf_side[label] = {"ms": d0.elapsed_time(d1) / 5, "rel_dev_from_rgf": dev_}
+        del dH, ref_band
+
     cpu = None
     if pool is not None:
         cpu, _ = oracle_sample(a.workload, a.cpu_energies, pool, cores)
@@ -592,6 +633,7 @@ def run_ours(a, rank, world, local_rank):
             "fp64_path": fp64_side,
             "lesser_path": lesser_side,
             "grad_path": grad_side,
+            "ddrgf_levels": ddrgf_side,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

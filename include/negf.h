@@ -148,7 +148,7 @@ typedef struct {
 } negf_desc;
 
 #define NEGF_MAX_BLOCK 160
-#define NEGF_DEFAULT_PRODUCT_BITS 42
+#define NEGF_DEFAULT_PRODUCT_BITS 48
 #define NEGF_TUNE_BITS_CANDIDATES 3   /* widths negf_tune_precision tries: 32 42 48 */
 #define NEGF_MAX_GROUPS 8   /* energy groups (concurrent streams) per plan */
 #define NEGF_AUTOTUNE_CANDIDATES 6   /* group counts negf_autotune times: 1 2 3 4 6 8 */

