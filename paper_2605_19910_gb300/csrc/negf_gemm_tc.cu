@@ -71,6 +71,7 @@ struct TcCfg {
   int L;        // slices (= accumulator levels)
   int n_mma;    // MMA N (complex columns per tile)
   int tmem_cols;
+  int ep;       // epilogue pass width (columns)
 };
 
 __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -386,11 +387,6 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
   const double2* A = g.A + (int64_t)e * g.sA;
   const double2* B = g.B + (int64_t)e * g.sB;
 
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_base_s)), "r"(cfg.tmem_cols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -433,10 +429,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
   __syncthreads();
   for (int c = tid; c < n_mma; c += TC_THREADS)
     if (e_col[c] < -50000) e_col[c] = ZERO_EXP;
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem_d = tmem_base_s;
+  uint32_t tmem_d = 0;
   const uint32_t mb = smem_u32(&mbar);
   const uint32_t idesc = make_idesc(128, n_mma);
   const int frac = s * L;
@@ -509,7 +503,23 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (ch == 0) {
+      // Tensor memory is taken only now (the scales and the first chunk's
+      // slices need none) and given back before the FP64 stores: with more
+      // than 256 accumulator columns a CTA holds all of an SM's tensor
+      // memory, and other CTAs on the SM wait in tcgen05.alloc meanwhile.
+      if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_base_s)), "r"(cfg.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
     __syncthreads();
+    if (ch == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      tmem_d = tmem_base_s;
+    }
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
@@ -536,16 +546,18 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-  // Epilogue in passes of EP columns (keeps the staging buffer small so that
-  // this kernel can share an SM with the FP64 inversion kernel).  Epilogue 1
-  // combines each real row's level accumulators into one integer T on the
-  // grid of unit 2^E, E = e_row + e_col - s (L + 1); epilogue 2 adds
-  // alpha / beta1 C1 / beta2 C2 / gamma dshift I on that grid and converts
-  // once to FP64 (falling back to rounded FP64 additions on integer bit
-  // patterns where a term is too large for the grid).
-  constexpr int EP = 32;
+  // Epilogue in passes of EP columns (64 where the operands' shared memory
+  // holds that staging, else 32).  Epilogue 1 combines each real row's level
+  // accumulators into one integer T on the grid of unit 2^E,
+  // E = e_row + e_col - s (L + 1); tensor memory is freed after the last
+  // pass's epilogue 1; epilogue 2 adds alpha / beta1 C1 / beta2 C2 / gamma
+  // dshift I on that grid and converts once to FP64 (falling back to rounded
+  // FP64 additions on integer bit patterns where a term is too large for the
+  // grid).
+  const int EP = cfg.ep;
   Acc* stage = reinterpret_cast<Acc*>(smem);   // 128 x (EP + 1) integers (operands are dead)
-  constexpr int lds = EP + 1;                   // padded rows: conflict-free per-lane row writes
+  const int lds = EP + 1;                       // padded rows: conflict-free per-lane row writes
+  bool tmem_live = true;
   constexpr int DMAX = WIDE ? 60 : 8;           // largest left shift of a term onto the grid
   double2* C = g.C + (int64_t)e * g.sC;
   const double2* C1 = (g.C1 && g.beta1.x != 0.0) ? g.C1 + (int64_t)e * g.sC1 : nullptr;
@@ -558,11 +570,11 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
     const int q = warp & 3, half = warp >> 2;   // warp w reads TMEM lanes 32 (w % 4) .. + 31
     const int R = q * 32 + lane;
     for (int p0 = 0; p0 < n_mma; p0 += EP) {
-      // Epilogue 1: combine the levels of this lane's real row for 16 columns, 8 at a time
-      const int c0 = p0 + 16 * half;
-      if (c0 < n_mma) {
+      // Epilogue 1: combine the levels of this lane's real row for EP / 2 columns, 8 at a time
+      const int c0 = p0 + (EP / 2) * half;
+      {
 #pragma unroll 1
-        for (int h8 = 0; h8 < 16; h8 += 8) {
+        for (int h8 = 0; h8 < EP / 2 && c0 + h8 < n_mma; h8 += 8) {
           Acc T[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) T[i] = 0;
@@ -575,10 +587,17 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
             for (int i = 0; i < 8; ++i) T[i] += (Acc)acc_int(v[i]) << sh;
           }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) stage[R * lds + 16 * half + h8 + i] = T[i];
+          for (int i = 0; i < 8; ++i) stage[R * lds + (EP / 2) * half + h8 + i] = T[i];
         }
       }
+      const bool last = p0 + EP >= n_mma;
+      if (last) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
+      if (last) {
+        if (warp == 0)
+          asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_d), "r"(cfg.tmem_cols));
+        tmem_live = false;
+      }
       // Epilogue 2: the linear terms on the grid, one conversion, FP64 store.
       const int pc = min(EP, nt - p0);
       for (int idx = tid; idx < mt * pc; idx += TC_THREADS) {
@@ -619,10 +638,12 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
     mbar_wait(mb, last_parity);       // drain: bounded wait (default limit) for MMAs still in flight
     if (tid == 0 && g.errword) atomicOr(g.errword, ERRBIT_TIMEOUT);
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_d), "r"(cfg.tmem_cols));
+  if (tmem_live) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_d), "r"(cfg.tmem_cols));
+    }
   }
 }
 
@@ -653,6 +674,11 @@ TcCfg tc_config(int n, int k, int bits) {
   int tc = 32;
   while (tc < c.L * nm) tc <<= 1;
   c.tmem_cols = tc;
+  // one 64-column epilogue pass where its integer staging fits the operands' shared memory
+  const int kr_c = Chunk<16>::KR;
+  const size_t op = (size_t)c.L * 128 * kr_c * 2 + (size_t)c.L * c.n_mma * kr_c * 2;
+  const bool wide = c.s * (c.L - 1) > 36;
+  c.ep = (c.n_mma >= 64 && (size_t)128 * 65 * (wide ? 16 : 8) <= op) ? 64 : 32;
   return c;
 }
 
