@@ -471,6 +471,17 @@ def run_ours(a, rank, world, local_rank):
                                "bf16_tflops": bf16, "source": "FP64: negf_fp64_peak in this run; "
                                                              "bf16: MEASURED_PEAKS sustained"}}
 
+    # every kernel of the single-group profiled step: time, launches, share
+    # and useful flops per second (the method's count)
+    tot_ms = sum(v[0] for v in prof.values())
+    kernels = {k: {"ms": v[0], "launches": int(v[2]), "share": v[0] / tot_ms if tot_ms > 0 else 0.0,
+                   "tflops": (v[1] / (v[0] * 1e-3) / 1e12) if v[0] > 0 else 0.0}
+               for k, v in prof.items() if v[2] > 0}
+    if "zinv_gj_kernel" in kernels:
+        kernels["zinv_gj_kernel"]["of_measured_dfma"] = kernels["zinv_gj_kernel"]["tflops"] / dfma_peak
+    if "zgemm_f64_kernel" in kernels:
+        kernels["zgemm_f64_kernel"]["of_measured_dmma"] = kernels["zgemm_f64_kernel"]["tflops"] / dmma_peak
+
     from oracle.rgf import rgf_flops_paper
     flops_step = rgf_flops_paper(prob.sizes, prob.w) * nE
     ws_gb = P.negf_workspace_bytes(plan.handle) / 1e9
@@ -629,6 +640,7 @@ def run_ours(a, rank, world, local_rank):
             "band_residual": band_residual,
             "roofline": roof,
             "composite_roofline": composite,
+            "kernels_single_group_step": kernels,
             "fp64_peaks_measured": fp64,
             "fp64_path": fp64_side,
             "lesser_path": lesser_side,

@@ -359,10 +359,11 @@ struct Digits8 {
 };
 
 // S8: 8-bit slices of products up to 32 bits.  WIDE: products longer than
-// the 64-bit level combination allows.  Every build is held to 64 registers
-// so that four CTAs fit an SM.  BC: op(B) = B^H.
+// the 64-bit level combination allows.  BC: op(B) = B^H.  Register caps
+// follow the CTAs per SM that the operands' shared memory allows anyway:
+// four for S8 (4 slices), three for 5-6 slices, two for WIDE (7-8).
 template <bool S8, bool WIDE, bool BC>
-__global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
+__global__ void __launch_bounds__(TC_THREADS, S8 ? 4 : (WIDE ? 2 : 3)) zgemm_tc_kernel(ZGemm g, int tiles_n, TcCfg cfg) {
   using CK = Chunk<16>;
   using Acc = typename std::conditional<WIDE, __int128, long long>::type;
   constexpr int KC = CK::KC, KG = CK::KG, KR = CK::KR, A_SLICE_BYTES = CK::A_SLICE_BYTES;
@@ -393,20 +394,29 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
   }
 
   // Pass 1: power-of-two scales of the rows of A (warps 0-3) and of the
-  // columns of B (warps 4-7), concurrently.
+  // columns of B (warps 4-7), concurrently, with eight loads in flight per
+  // thread (the scan is bound by load latency, not by its arithmetic).
   for (int c = tid; c < n_mma; c += TC_THREADS) e_col[c] = -100000;
   __syncthreads();
   if (warp < 4) {
-    for (int r = warp; r < MC; r += 4) {
-      int mx = -100000;
-      if (m0 + r < g.m)
-        for (int k = lane; k < g.k; k += 32) {
-          const ulonglong2 v = ld_bits(A + (int64_t)(m0 + r) * g.lda + k);
-          mx = max(mx, max(exp_bound(v.x), exp_bound(v.y)));
+    // row tid / 2 of A, every other K from tid % 2 (two threads per row)
+    const int r = tid >> 1, hh = tid & 1;
+    int mx = -100000;
+    if (m0 + r < g.m) {
+      const double2* row = A + (int64_t)(m0 + r) * g.lda;
+      for (int k0 = hh; k0 < g.k; k0 += 16) {
+        ulonglong2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k = k0 + 2 * u;
+          v[u] = k < g.k ? ld_bits(row + k) : make_ulonglong2(0ull, 0ull);
         }
-      for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-      if (lane == 0) e_row[r] = mx < -50000 ? ZERO_EXP : mx;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mx = max(mx, max(exp_bound(v[u].x), exp_bound(v[u].y)));
+      }
     }
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    if (hh == 0) e_row[r] = mx < -50000 ? ZERO_EXP : mx;
   } else if (nt > 0) {
     // columns of B: thread t scans column t % nt over every (128 / nt)-th K
     // (coalesced over columns; columns t, t + 128, ... over all K when
@@ -416,11 +426,17 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
     if (kk < per)
       for (int c = nt >= 128 ? t : t % nt; c < nt; c += 128) {
         int mx = -100000;
-        for (int k = kk; k < g.k; k += per) {
+        for (int k0 = kk; k0 < g.k; k0 += 8 * per) {
           // op(B)(k, c) at B + k sbk + c sbc (op(B) = B^H: the strides swap;
           // the sign of the imaginary part does not matter here)
-          const ulonglong2 v = ld_bits(B + opb_off<BC>(g, k, n0 + c));
-          mx = max(mx, max(exp_bound(v.x), exp_bound(v.y)));
+          ulonglong2 v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u * per;
+            v[u] = k < g.k ? ld_bits(B + opb_off<BC>(g, k, n0 + c)) : make_ulonglong2(0ull, 0ull);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) mx = max(mx, max(exp_bound(v[u].x), exp_bound(v[u].y)));
         }
         atomicMax(&e_col[c], mx);
         if (nt < 128) break;
@@ -522,7 +538,9 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
     }
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      // descriptors advance in 16-byte units in their start-address field
+      // (shared-memory addresses stay below 256 KB, the field's range)
+      const uint64_t ad0 = make_desc<CK>(smem_u32(sA)), bd0 = make_desc<CK>(smem_u32(sB));
 #pragma unroll 1
       for (int st = 0; st < KR / 16; ++st) {
         const uint32_t koff = (uint32_t)st * 2 * LBO;       // 16 BF16 of K = two core columns
@@ -533,8 +551,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
           for (int l = 0; l <= d; ++l) {
             const int m = d - l;
             const uint32_t acc = (ch > 0 || st > 0 || l > 0) ? 1u : 0u;
-            mma_bf16(tm, make_desc<CK>(a0 + (uint32_t)l * A_SLICE_BYTES + koff),
-                     make_desc<CK>(b0 + (uint32_t)m * b_slice_bytes + koff), idesc, acc);
+            mma_bf16(tm, ad0 + (((uint32_t)l * A_SLICE_BYTES + koff) >> 4),
+                     bd0 + (((uint32_t)m * b_slice_bytes + koff) >> 4), idesc, acc);
           }
         }
       }
@@ -598,9 +616,28 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
           asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_d), "r"(cfg.tmem_cols));
         tmem_live = false;
       }
-      // Epilogue 2: the linear terms on the grid, one conversion, FP64 store.
+      // Epilogue 2: the linear terms on the grid, one conversion, FP64 store;
+      // EU items per thread at a time with their C1 / C2 loads issued first.
       const int pc = min(EP, nt - p0);
-      for (int idx = tid; idx < mt * pc; idx += TC_THREADS) {
+      const int items = mt * pc;
+      constexpr int EU = S8 ? 1 : (WIDE ? 4 : 2);
+      for (int idx0 = tid; idx0 < items; idx0 += EU * TC_THREADS) {
+        ulonglong2 x1v[EU], x2v[EU];
+#pragma unroll
+        for (int u = 0; u < EU; ++u) {
+          const int idx = idx0 + u * TC_THREADS;
+          x1v[u] = make_ulonglong2(0ull, 0ull);
+          x2v[u] = make_ulonglong2(0ull, 0ull);
+          if (idx < items) {
+            const int gr = m0 + idx / pc, gc = n0 + p0 + idx % pc;
+            if (C1) x1v[u] = ld_bits(C1 + (int64_t)gr * g.ldc1 + gc);
+            if (C2) x2v[u] = ld_bits(C2 + (int64_t)gr * g.ldc2 + gc);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < EU; ++u) {
+        const int idx = idx0 + u * TC_THREADS;
+        if (idx >= items) break;
         const int r = idx / pc, cl = idx % pc;
         const int gr = m0 + r, gc = n0 + p0 + cl;
         const int E = e_row[r] + e_col[p0 + cl] - s * (L + 1);
@@ -608,15 +645,9 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
         if (na) { tre = -tre; tim = -tim; }
         Acc xre = tre, xim = tim;
         bool grid = true;
-        ulonglong2 x1 = make_ulonglong2(0ull, 0ull), x2 = make_ulonglong2(0ull, 0ull);
-        if (C1) {
-          x1 = ld_bits(C1 + (int64_t)gr * g.ldc1 + gc);
-          grid = grid_add<Acc, DMAX>(xre, x1.x, n1, E) && grid_add<Acc, DMAX>(xim, x1.y, n1, E);
-        }
-        if (C2) {
-          x2 = ld_bits(C2 + (int64_t)gr * g.ldc2 + gc);
-          grid = grid && grid_add<Acc, DMAX>(xre, x2.x, n2, E) && grid_add<Acc, DMAX>(xim, x2.y, n2, E);
-        }
+        const ulonglong2 x1 = x1v[u], x2 = x2v[u];
+        if (C1) grid = grid_add<Acc, DMAX>(xre, x1.x, n1, E) && grid_add<Acc, DMAX>(xim, x1.y, n1, E);
+        if (C2) grid = grid && grid_add<Acc, DMAX>(xre, x2.x, n2, E) && grid_add<Acc, DMAX>(xim, x2.y, n2, E);
         const bool diag = has_d && gr == gc;
         if (diag) grid = grid && grid_add<Acc, DMAX>(xre, dsh.x, ng, E) && grid_add<Acc, DMAX>(xim, dsh.y, ng, E);
         u64 re, im;
@@ -631,6 +662,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) zgemm_tc_kernel(ZGemm g, int ti
           if (diag) { re = add_bits(re, flip(dsh.x, ng)); im = add_bits(im, flip(dsh.y, ng)); }
         }
         *reinterpret_cast<ulonglong2*>(C + (int64_t)gr * g.ldc + gc) = make_ulonglong2(re, im);
+        }
       }
       __syncthreads();
     }
