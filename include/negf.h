@@ -183,9 +183,10 @@ int32_t negf_plan_levels(const negf_plan_t* p, int32_t* level_domains, int32_t c
  * inversion to a batched block product, negf_measure_r_inv) and r_GETRS = 1
  * (products with explicit inverses are products); the paper's
  * n_tasks / n_threads becomes the wave factor
- * max(1, n_tasks n_E / slots, n_tasks / 128) (slots: inversion CTAs resident
- * on sm_count SMs for the largest block; concurrent tasks are graph branches,
- * of which at most ~128 kernels run at once).
+ * max(1, n_tasks n_E / slots, n_tasks / 16) (slots: inversion CTAs resident
+ * on sm_count SMs for the largest block; concurrent tasks are graph branches
+ * of latency-bound launches, of which about 16 progress at once on GB300,
+ * measured).
  * Level 1 pairs have s2 in {2, 3, 4, 6, ..., 128} w layers and s1 = w
  * separator layers and at most 128 pairs (one graph branch per pair);
  * deeper levels s2 in {1, 2, 3, 4}, s1 = 1 (the paper's

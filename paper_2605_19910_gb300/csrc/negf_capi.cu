@@ -152,8 +152,12 @@ struct ModelChoice {
 // scale `cube`, given the s2 candidates; returns the best and its s2 sequence.
 void model_levels(double l, int s1, double cube, double r_inv, double nE, double slots, int depth, int max_levels,
                   const std::vector<int>& s2c, ModelChoice& best, std::vector<int>& seq) {
-  // concurrent tasks are graph branches: at most ~128 kernels run at once
-  auto wave = [&](double tasks) { return std::max(std::max(1.0, tasks * nE / slots), tasks / 128.0); };
+  // Concurrent tasks are graph branches of latency-bound launches.  Measured
+  // on GB300 (1024 x 64 chain, one energy, FP64): 16 and 32 pairs take 234
+  // and 217 ms, 113 pairs 482 ms, although every pair's step holds only a few
+  // CTAs, so about 16 branches progress at once, not the ~128 concurrent
+  // kernels the hardware admits: n_threads of the paper's model = 16.
+  auto wave = [&](double tasks) { return std::max(std::max(1.0, tasks * nE / slots), tasks / 16.0); };
   // this level solved by RGF
   {
     const double c = wave(1.0) * model_rgf(l, r_inv) * cube;
