@@ -107,11 +107,6 @@ __device__ __forceinline__ u64 fixed_abs(u64 u, int e_scale, int frac_bits) {
   return m >> (-sh);
 }
 
-// BF16 bits of the small integer v (< 256): exact through FP32 (2^23 + v), sign added after
-__device__ __forceinline__ uint32_t bf16_of_small(uint32_t v) {
-  return __float_as_uint(__uint_as_float(0x4B000000u | v) - 8388608.0f) >> 16;
-}
-
 // |x| * 2^(frac_bits - e_scale) truncated, for frac_bits <= 32: the result
 // fits 32 bits.  With |x| < 2^e_scale the right shift of the 53-bit mantissa
 // is k = 1075 - be - frac_bits + e_scale >= 21.
@@ -448,24 +443,24 @@ __global__ void __launch_bounds__(TC_THREADS, S8 ? 4 : (WIDE ? 2 : 3)) zgemm_tc_
   __syncthreads();
   uint32_t tmem_d = 0;
   const uint32_t mb = smem_u32(&mbar);
-  const uint32_t idesc = make_idesc(128, n_mma);
   const int frac = s * L;
   const uint32_t smask = (1u << s) - 1u;
   bool ok = true;
   uint32_t last_parity = 0;
 
   const int nchunks = (g.k + KC - 1) / KC;
-  for (int ch = 0; ch < nchunks && ok; ++ch) {
-    const int k0 = ch * KC;
-    // Pass 2: slices of A and of B^T, 8 consecutive K per thread item, one
-    // 16-byte core-matrix row per store; A and B concurrently on the two
-    // halves of the CTA.
-    const int half_t = TC_THREADS / 2;   // threads 0-127 slice A, 128-255 slice B
-    if (tid < half_t) for (int item = tid; item < MC * KG; item += half_t) {
-      // A: row r holds [Re A | -Im A], row 64 + r holds [Im A | Re A].
-      const int r = item / KG, kg = item % KG;
-      const int gr = m0 + r;
-      u64 vre[8], vim[8];
+  // Pass 2: slices of A and of B^T, 8 consecutive K per thread item, one
+  // 16-byte core-matrix row per store; A and B concurrently on the two
+  // halves of the CTA (threads 0-127 slice A, 128-255 slice B).
+  const int half_t = TC_THREADS / 2;
+  const bool isA = tid < half_t;
+  const int item0 = isA ? tid : tid - half_t;
+  const int n_items = isA ? MC * KG : n_mma * KG;
+  // the raw values of an item: A row r (real and imaginary parts of 8
+  // consecutive K), or column c of op(B)
+  auto load_item = [&](int item, int k0, u64* vre, u64* vim) {
+    if (isA) {
+      const int r = item / KG, kg = item % KG, gr = m0 + r;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int gk = k0 + kg * 8 + j;
@@ -474,27 +469,8 @@ __global__ void __launch_bounds__(TC_THREADS, S8 ? 4 : (WIDE ? 2 : 3)) zgemm_tc_
         vre[j] = v.x;
         vim[j] = v.y;
       }
-      Digits8<S8> dre, dim;
-      dre.load(vre, e_row[r], frac);
-      dim.load(vim, e_row[r], frac);
-      for (int l = 0; l < L; ++l) {
-        uint32_t pr[4], pi[4];
-        dre.slice(l, s, L, smask, pr);
-        dim.slice(l, s, L, smask, pi);
-        unsigned char* base = sA + (size_t)l * A_SLICE_BYTES;
-        const uint4 vr = make_uint4(pr[0], pr[1], pr[2], pr[3]);
-        const uint4 vi = make_uint4(pi[0], pi[1], pi[2], pi[3]);
-        const uint4 vn = make_uint4(pi[0] ^ 0x80008000u, pi[1] ^ 0x80008000u, pi[2] ^ 0x80008000u,
-                                    pi[3] ^ 0x80008000u);
-        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(r, kg * 8)) = vr;
-        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(r, KC + kg * 8)) = vn;
-        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(MC + r, kg * 8)) = vi;
-        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(MC + r, KC + kg * 8)) = vr;
-      }
-    } else for (int item = tid - half_t; item < n_mma * KG; item += half_t) {
-      // B^T (K-major): row c holds [Re B(:, c) | Im B(:, c)].
+    } else {
       const int c = item % n_mma, kg = item / n_mma;
-      u64 vre[8], vim[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int gk = k0 + kg * 8 + j;
@@ -506,6 +482,32 @@ __global__ void __launch_bounds__(TC_THREADS, S8 ? 4 : (WIDE ? 2 : 3)) zgemm_tc_
         vre[j] = v.x;
         vim[j] = v.y;
       }
+    }
+  };
+  auto slice_item = [&](int item, const u64* vre, const u64* vim, unsigned char* dst) {
+    if (isA) {
+      // A: row r holds [Re A | -Im A], row 64 + r holds [Im A | Re A].
+      const int r = item / KG, kg = item % KG;
+      Digits8<S8> dre, dim;
+      dre.load(vre, e_row[r], frac);
+      dim.load(vim, e_row[r], frac);
+      for (int l = 0; l < L; ++l) {
+        uint32_t pr[4], pi[4];
+        dre.slice(l, s, L, smask, pr);
+        dim.slice(l, s, L, smask, pi);
+        unsigned char* base = dst + (size_t)l * A_SLICE_BYTES;
+        const uint4 vr = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+        const uint4 vi = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+        const uint4 vn = make_uint4(pi[0] ^ 0x80008000u, pi[1] ^ 0x80008000u, pi[2] ^ 0x80008000u,
+                                    pi[3] ^ 0x80008000u);
+        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(r, kg * 8)) = vr;
+        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(r, KC + kg * 8)) = vn;
+        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(MC + r, kg * 8)) = vi;
+        *reinterpret_cast<uint4*>(base + kmaj_off<CK>(MC + r, KC + kg * 8)) = vr;
+      }
+    } else {
+      // B^T (K-major): row c holds [Re B(:, c) | Im B(:, c)].
+      const int c = item % n_mma, kg = item / n_mma;
       Digits8<S8> dre, dim;
       dre.load(vre, e_col[c], frac);
       dim.load(vim, e_col[c], frac);
@@ -513,11 +515,31 @@ __global__ void __launch_bounds__(TC_THREADS, S8 ? 4 : (WIDE ? 2 : 3)) zgemm_tc_
         uint32_t pr[4], pi[4];
         dre.slice(l, s, L, smask, pr);
         dim.slice(l, s, L, smask, pi);
-        unsigned char* base = sB + (size_t)l * b_slice_bytes;
+        unsigned char* base = dst + (size_t)L * A_SLICE_BYTES + (size_t)l * b_slice_bytes;
         *reinterpret_cast<uint4*>(base + kmaj_off<CK>(c, kg * 8)) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
         *reinterpret_cast<uint4*>(base + kmaj_off<CK>(c, KC + kg * 8)) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
       }
     }
+  };
+  // The wide variants (two CTAs per SM, registers to spare) keep the first
+  // item of the next chunk in flight during this chunk's MMAs (its loads are
+  // issued before the barrier that hands the slices to the tensor core);
+  // in the narrower variants the extra registers cost more than the latency
+  // they hide.
+  constexpr bool PREFETCH = WIDE;
+  u64 pre_re[8], pre_im[8];
+  for (int ch = 0; ch < nchunks && ok; ++ch) {
+    const int k0 = ch * KC;
+    for (int item = item0; item < n_items; item += half_t) {
+      if (PREFETCH && item == item0 && ch > 0) {
+        slice_item(item, pre_re, pre_im, smem);
+      } else {
+        u64 vre[8], vim[8];
+        load_item(item, k0, vre, vim);
+        slice_item(item, vre, vim, smem);
+      }
+    }
+    if (PREFETCH && ch + 1 < nchunks && item0 < n_items) load_item(item0, k0 + KC, pre_re, pre_im);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (ch == 0) {
       // Tensor memory is taken only now (the scales and the first chunk's
@@ -538,21 +560,28 @@ __global__ void __launch_bounds__(TC_THREADS, S8 ? 4 : (WIDE ? 2 : 3)) zgemm_tc_
     }
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // descriptors advance in 16-byte units in their start-address field
-      // (shared-memory addresses stay below 256 KB, the field's range)
+      // Descriptors advance in 16-byte units in their start-address field
+      // (shared-memory addresses stay below 256 KB, the field's range).  One
+      // MMA per A slice l and group of B slices m stacked along N: the
+      // slices of B are consecutive rows of one K-major operand and the level
+      // accumulators d = l + m consecutive TMEM columns, so up to 256 / n_mma
+      // slice products go into one instruction (fewer, larger MMAs issue
+      // faster from the single issuing thread).
       const uint64_t ad0 = make_desc<CK>(smem_u32(sA)), bd0 = make_desc<CK>(smem_u32(sB));
+      const int per = 256 / n_mma;
 #pragma unroll 1
       for (int st = 0; st < KR / 16; ++st) {
         const uint32_t koff = (uint32_t)st * 2 * LBO;       // 16 BF16 of K = two core columns
 #pragma unroll 1
-        for (int d = 0; d < L; ++d) {
-          const uint32_t tm = tmem_d + (uint32_t)(d * n_mma);
+        for (int l = 0; l < L; ++l) {
 #pragma unroll 1
-          for (int l = 0; l <= d; ++l) {
-            const int m = d - l;
+          for (int mg = 0; mg < L - l; mg += per) {
+            const int nm = min(per, L - l - mg);
+            const uint32_t tm = tmem_d + (uint32_t)((l + mg) * n_mma);
+            // the l = 0 products write every level first (d = m): overwrite at the first K step
             const uint32_t acc = (ch > 0 || st > 0 || l > 0) ? 1u : 0u;
             mma_bf16(tm, ad0 + (((uint32_t)l * A_SLICE_BYTES + koff) >> 4),
-                     bd0 + (((uint32_t)m * b_slice_bytes + koff) >> 4), idesc, acc);
+                     bd0 + (((uint32_t)mg * b_slice_bytes + koff) >> 4), make_idesc(128, nm * n_mma), acc);
           }
         }
       }
@@ -617,22 +646,18 @@ __global__ void __launch_bounds__(TC_THREADS, S8 ? 4 : (WIDE ? 2 : 3)) zgemm_tc_
         tmem_live = false;
       }
       // Epilogue 2: the linear terms on the grid, one conversion, FP64 store;
-      // EU items per thread at a time with their C1 / C2 loads issued first.
+      // EU items per thread at a time with their C1 loads issued first (the
+      // phase is bound by the latency of those loads).
       const int pc = min(EP, nt - p0);
       const int items = mt * pc;
-      constexpr int EU = S8 ? 1 : (WIDE ? 4 : 2);
+      constexpr int EU = S8 ? 2 : (WIDE ? 4 : 5);
       for (int idx0 = tid; idx0 < items; idx0 += EU * TC_THREADS) {
-        ulonglong2 x1v[EU], x2v[EU];
+        ulonglong2 x1v[EU];
 #pragma unroll
         for (int u = 0; u < EU; ++u) {
           const int idx = idx0 + u * TC_THREADS;
           x1v[u] = make_ulonglong2(0ull, 0ull);
-          x2v[u] = make_ulonglong2(0ull, 0ull);
-          if (idx < items) {
-            const int gr = m0 + idx / pc, gc = n0 + p0 + idx % pc;
-            if (C1) x1v[u] = ld_bits(C1 + (int64_t)gr * g.ldc1 + gc);
-            if (C2) x2v[u] = ld_bits(C2 + (int64_t)gr * g.ldc2 + gc);
-          }
+          if (C1 && idx < items) x1v[u] = ld_bits(C1 + (int64_t)(m0 + idx / pc) * g.ldc1 + n0 + p0 + idx % pc);
         }
 #pragma unroll
         for (int u = 0; u < EU; ++u) {
@@ -645,7 +670,8 @@ __global__ void __launch_bounds__(TC_THREADS, S8 ? 4 : (WIDE ? 2 : 3)) zgemm_tc_
         if (na) { tre = -tre; tim = -tim; }
         Acc xre = tre, xim = tim;
         bool grid = true;
-        const ulonglong2 x1 = x1v[u], x2 = x2v[u];
+        const ulonglong2 x1 = x1v[u];
+        const ulonglong2 x2 = C2 ? ld_bits(C2 + (int64_t)gr * g.ldc2 + gc) : make_ulonglong2(0ull, 0ull);
         if (C1) grid = grid_add<Acc, DMAX>(xre, x1.x, n1, E) && grid_add<Acc, DMAX>(xim, x1.y, n1, E);
         if (C2) grid = grid && grid_add<Acc, DMAX>(xre, x2.x, n2, E) && grid_add<Acc, DMAX>(xim, x2.y, n2, E);
         const bool diag = has_d && gr == gc;
