@@ -149,7 +149,7 @@ typedef struct {
 
 #define NEGF_MAX_BLOCK 160
 #define NEGF_DEFAULT_PRODUCT_BITS 48
-#define NEGF_TUNE_BITS_CANDIDATES 3   /* widths negf_tune_precision tries: 32 42 48 */
+#define NEGF_TUNE_BITS_CANDIDATES 4   /* widths negf_tune_precision tries: 32 35 42 48 */
 #define NEGF_MAX_GROUPS 8   /* energy groups (concurrent streams) per plan */
 #define NEGF_AUTOTUNE_CANDIDATES 6   /* group counts negf_autotune times: 1 2 3 4 6 8 */
 
@@ -362,7 +362,7 @@ negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* s
 
 /* Precision tuner (mixed plans): solves the caller's inputs once with
  * 56-bit products into G_band_ref / G_1N_ref (caller-owned device buffers of
- * the outputs' sizes), then with 32, 42 and 48 bits into G_band / G_1N,
+ * the outputs' sizes), then with 32, 35, 42 and 48 bits (4 to 7 slices) into G_band / G_1N,
  * and keeps for the plan's later calls the narrowest width whose band and
  * G_1N lie within tol of the 56-bit reference at every energy (relative
  * Frobenius norm per energy and output kind); 56 if none does.  The choice

@@ -41,7 +41,7 @@ NEGF_OUT_LESSER = 16
 
 NEGF_MAX_BLOCK = 160
 NEGF_DEFAULT_PRODUCT_BITS = 48
-TUNE_BITS = (32, 42, 48)   # the candidates of negf_tune_precision, in its order
+TUNE_BITS = (32, 35, 42, 48)   # the candidates of negf_tune_precision, in its order
 
 NEGF_PROF_INV = 0
 NEGF_PROF_GEMM_F64 = 1

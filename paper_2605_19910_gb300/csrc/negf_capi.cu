@@ -1240,7 +1240,7 @@ negf_status negf_tune_precision(negf_plan_t* p, const negf_c128* H, const negf_c
   if (!p || !H || !E || !info || !(tol > 0.0) || (!G_band && !G_1N)) return NEGF_ERR_ARG;
   if ((G_band && !G_band_ref) || (G_1N && !G_1N_ref)) return NEGF_ERR_ARG;
   if (p->precision != NEGF_MIXED) return NEGF_ERR_UNSUPPORTED;
-  const int cand[NEGF_TUNE_BITS_CANDIDATES] = {32, 42, 48};
+  const int cand[NEGF_TUNE_BITS_CANDIDATES] = {32, 35, 42, 48};   // 4, 5, 6 and 7 slices
   const int nE = p->nE;
   const int64_t s1 = (int64_t)p->b[0] * p->b[p->N - 1];
   double* d = nullptr;   // per-energy squared norms: band diff, band ref, G_1N diff, G_1N ref

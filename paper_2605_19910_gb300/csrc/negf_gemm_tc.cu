@@ -732,11 +732,14 @@ TcCfg tc_config(int n, int k, int bits) {
   int tc = 32;
   while (tc < c.L * nm) tc <<= 1;
   c.tmem_cols = tc;
-  // one 64-column epilogue pass where its integer staging fits the operands' shared memory
-  const int kr_c = Chunk<16>::KR;
-  const size_t op = (size_t)c.L * 128 * kr_c * 2 + (size_t)c.L * c.n_mma * kr_c * 2;
+  // One 64-column epilogue pass (all of epilogue 2 after the tensor memory
+  // is freed) for the 5-6 slice products, whose shared memory is raised to
+  // the staging's 66.5 KB where the operands need less (three CTAs per SM
+  // either way); 32-column passes for the 4-slice products (four CTAs per
+  // SM) and the wide ones (128-bit staging).
   const bool wide = c.s * (c.L - 1) > 36;
-  c.ep = (c.n_mma >= 64 && (size_t)128 * 65 * (wide ? 16 : 8) <= op) ? 64 : 32;
+  const bool s8 = c.s == 8 && c.s * c.L <= 32;
+  c.ep = (c.n_mma >= 64 && !wide && !s8) ? 64 : 32;
   return c;
 }
 
@@ -747,7 +750,7 @@ bool tc_wide(const TcCfg& c);
 size_t tc_smem_bytes(const TcCfg& c) {
   const int kr = Chunk<16>::KR;
   size_t op = (size_t)c.L * 128 * kr * 2 + (size_t)c.L * c.n_mma * kr * 2;
-  size_t st = (size_t)128 * (32 + 1) * (tc_wide(c) ? 16 : 8);   // integer staging of one epilogue pass
+  size_t st = (size_t)128 * (c.ep + 1) * (tc_wide(c) ? 16 : 8);   // integer staging of one epilogue pass
   return op > st ? op : st;
 }
 
