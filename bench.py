@@ -33,14 +33,23 @@ WORKLOAD = "batched64x64"
 METRIC = "selected-G^R energies x blocks / s"
 UNIT = "energy-blocks/s"
 
-# DRAM traffic per unit (one block inversion) of the dominant kernel from an
-# ncu capture of one 512-block launch, valid only while the kernel source is
-# the one captured (the summary and its command are under profiles/)
+# DRAM traffic per unit (one block inversion, one block product) of the
+# dominant kernel from ncu captures, valid only while the kernel source is the
+# one captured (the summaries and their commands are under profiles/)
 NCU_TRAFFIC = {
     ("zinv_gj_kernel", 64): {
         "bytes_per_unit": (33.590272e6 + 0.707584e6) / 512,
+        "unit": "inversion",
         "src": "paper_2605_19910_gb300/csrc/negf_inv.cu",
         "sha256": "822754194672a1cbd60c34eab0d70b7732c3e368ef01f55ae1df4212b2eaba73",
+    },
+    # two captured 2048-product launches at 35 bits (one with a shared
+    # coupling-block operand, one with two per-energy operands), averaged
+    ("zgemm_tc_kernel", 64): {
+        "bytes_per_unit": ((269.563904e6 + 98.436352e6) + (414.447104e6 + 105.942784e6)) / 2 / 2048,
+        "unit": "block product",
+        "src": "paper_2605_19910_gb300/csrc/negf_gemm_tc.cu",
+        "sha256": "ff6db95dd68af2efe39b9e4a48f9170bfaad900c9a09ddef194b6fafb8d69f84",
     },
 }
 
@@ -459,10 +468,15 @@ def run_ours(a, rank, world, local_rank):
         import hashlib
         with open(os.path.join(ROOT, t["src"]), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() == t["sha256"]:
-                traffic = t["bytes_per_unit"] * (N * nE / dln)
+                # units per launch: one per energy of the single-group step's
+                # launches (a layer's inversions, or one block product)
+                traffic = t["bytes_per_unit"] * (N * nE / dln if t["unit"] == "inversion" else nE)
     roof = {"kernel": name, "bound": bound,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": psrc,
+            "traffic_note": "ncu dram bytes read + written per launch (captured launches, scaled per unit) against "
+                            "the algorithmic 2 x 16 b^2 bytes per inversion / up to 4 x 16 b^2 per block product "
+                            "(A, B, C1 in, C out; a shared coupling-block operand is read once per launch)",
             "flop_count": "the method's 8 m n k per complex product / 8 b^3 per inversion",
             "kernel_share": dms / sum(v[0] for v in prof.values()),
             "launches_per_step": int(dln), "nominal_fp64_tflops": FP64_NOMINAL_TFLOPS}
