@@ -305,8 +305,15 @@ negf_status negf_solve_host(negf_plan_t* p, const negf_c128* H, const negf_c128*
                             negf_c128* G_band, negf_c128* G_1N, int32_t* info);
 
 /* Selected blocks of the Keldysh equation G^< = G^R Sigma^< G^A (Sec. 1; the
- * paper leaves its recursive solution to future work, Sec. 5), block
- * tridiagonal plans (band_n = 3, n_domains = 1) with NEGF_OUT_LESSER.  Runs
+ * paper leaves its recursive solution to future work, Sec. 5), plain RGF
+ * plans (n_domains = 1) with NEGF_OUT_LESSER.  Block n-diagonal plans
+ * (band_n >= 5) run it on their fused block tridiagonal chain (Sec. 2.3:
+ * super-layers of w layers, which must stay within NEGF_MAX_BLOCK): the band
+ * of H and the leads are laid out on the super-blocks by block copies, the
+ * recursion below runs there (the plan keeps a sub-plan for that, with the
+ * plan's precision and product width at plan time, and device buffers for
+ * at most ~8 GiB of fused outputs per sub-call), and both bands are cut
+ * back; there info[e] is the first layer of the failing w-layer group.  Runs
  * the retarded sweep (written to G_band) and a recursion over the
  * factorisation M = U D L of its upward pass:
  *   upward   Q_i = Sigma^<_i + H_{i,i+1} g^<_{i+1} H_{i,i+1}^H,

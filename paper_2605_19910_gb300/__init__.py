@@ -525,41 +525,18 @@ def unfuse_band(fband, sizes, w):
 
 def lesser_ndiag(sizes, band_n, H, sigma_L, sigma_R, E, sigma_less_L=None, sigma_less_R=None, less_diag=None,
                  precision="fp64", product_bits=0):
-    """Keldysh ``G^<`` (and ``G^R``) bands of a block n-diagonal chain through
-    its fused block tridiagonal form: the band of ``H`` is re-laid out on
-    super-blocks of w layers, the lead terms are placed in the first and last
-    super-blocks, :meth:`Plan.lesser` runs on the fused chain, and the
-    original band is cut out of both results.  ``H``: band-packed torch CUDA
-    tensor; ``sigma_*``: one matrix each (shared by all energies).  Returns
-    ``(G_band, G_less)`` in the original band packing."""
-    torch = __import__("torch")
-    w = (band_n - 1) // 2
-    if w == 1:
-        plan = Plan(sizes, 3, len(E), precision=precision, outputs=NEGF_OUT_BAND | NEGF_OUT_LESSER,
-                    product_bits=product_bits)
-        try:
-            return plan.lesser(H, sigma_L, sigma_R, E, sigma_less_L, sigma_less_R, less_diag)
-        finally:
-            plan.close()
-    Hf, fs = fuse_band(H, sizes, w)
-    N, Nf = len(sizes), len(fs)
-    rl = sum(sizes[(Nf - 1) * w:N - 1])      # offset of layer N inside the last super-block
-
-    def pad(m, size, at):
-        if m is None:
-            return None
-        out = torch.zeros(size, size, dtype=m.dtype, device=m.device)
-        out[at:at + m.shape[0], at:at + m.shape[1]] = m
-        return out
-    sLf, sRf = pad(sigma_L, fs[0], 0), pad(sigma_R, fs[-1], rl)
-    slLf, slRf = pad(sigma_less_L, fs[0], 0), pad(sigma_less_R, fs[-1], rl)
-    plan = Plan(fs, 3, len(E), precision=precision, outputs=NEGF_OUT_BAND | NEGF_OUT_LESSER,
+    """Keldysh ``G^<`` (and ``G^R``) bands of a block n-diagonal chain:
+    ``negf_lesser`` on a plan of ``band_n`` diagonals, which for ``band_n >= 5``
+    runs through the fused block tridiagonal form inside the library
+    (``fuse_band`` / ``unfuse_band`` restate its layout in Python).  ``H``:
+    band-packed torch CUDA tensor; ``sigma_*``: one matrix each (shared by all
+    energies).  Returns ``(G_band, G_less)`` in the original band packing."""
+    plan = Plan(sizes, band_n, len(E), precision=precision, outputs=NEGF_OUT_BAND | NEGF_OUT_LESSER,
                 product_bits=product_bits)
     try:
-        Gbf, Glf = plan.lesser(Hf, sLf, sRf, E, slLf, slRf, less_diag)
+        return plan.lesser(H, sigma_L, sigma_R, E, sigma_less_L, sigma_less_R, less_diag)
     finally:
         plan.close()
-    return unfuse_band(Gbf, sizes, w), unfuse_band(Glf, sizes, w)
 
 
 # ---------------------------------------------------------------------------

@@ -297,6 +297,162 @@ negf_status negf_measure_r_inv(int32_t b, int32_t batch, int32_t precision, doub
   return NEGF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Keldysh on a block n-diagonal plan: the block tridiagonal sub-plan of its
+// fused chain (Sec. 2.3, block fusing: super-layer J holds layers
+// [J w, (J + 1) w), the last one possibly fewer), the block map between the
+// two band packings and the device buffers of one sub-call.  Energies run
+// fz_nE at a time so that the fused outputs stay within about 8 GiB.
+negf_status fused_lesser_setup(negf_plan_s* p, const negf_desc* d) {
+  const int N = p->N, w = p->w, Nf = (N + w - 1) / w;
+  std::vector<int32_t> fs(Nf, 0);
+  std::vector<int> start(N + 1, 0), fstart(Nf + 1, 0);
+  for (int i = 0; i < N; ++i) { fs[i / w] += p->b[i]; start[i + 1] = start[i] + p->b[i]; }
+  for (int J = 0; J < Nf; ++J) fstart[J + 1] = fstart[J] + fs[J];
+  // fused band offsets (block tridiagonal packing: diagonals -1, 0, +1, layers inner)
+  std::vector<int64_t> foff((size_t)3 * Nf, -1);
+  int64_t fe = 0;
+  for (int dd = -1; dd <= 1; ++dd)
+    for (int J = 0; J < Nf; ++J)
+      if (J + dd >= 0 && J + dd < Nf) { foff[(size_t)(dd + 1) * Nf + J] = fe; fe += (int64_t)fs[J] * fs[J + dd]; }
+  std::vector<int64_t> map;
+  for (int dd = -w; dd <= w; ++dd)
+    for (int a = 0; a < N; ++a) {
+      const int b = a + dd;
+      if (b < 0 || b >= N) continue;
+      const int J = a / w, K = b / w;
+      map.push_back(p->band_off[(size_t)(dd + w) * N + a]);
+      map.push_back(p->b[a]);
+      map.push_back(p->b[b]);
+      map.push_back(foff[(size_t)(K - J + 1) * Nf + J]);
+      map.push_back(fs[K]);
+      map.push_back(start[a] - fstart[J]);
+      map.push_back(start[b] - fstart[K]);
+    }
+  p->fz_nblk = (int)(map.size() / 7);
+  p->fz_elems = fe;
+  p->fz_rl = start[N - 1] - fstart[Nf - 1];
+  p->fz_pad0 = sq(fs[0]);
+  p->fz_padN = sq(fs[Nf - 1]);
+  const double per_e = 2.0 * (double)fe * sizeof(double2);
+  p->fz_nE = (int)std::max(1.0, std::min((double)p->nE, std::floor(8.0 * (1ull << 30) / per_e)));
+  negf_desc sd = *d;
+  sd.n_blocks = Nf;
+  sd.block_sizes = fs.data();
+  sd.band_n = 3;
+  sd.n_energies = p->fz_nE;
+  sd.product_bits = p->bits;
+  sd.refine_steps = 0;
+  sd.outputs = NEGF_OUT_BAND | NEGF_OUT_LESSER;
+  sd.checkpoint_every = 0;
+  sd.n_domains = 1;
+  sd.domain_first_block = nullptr;
+  sd.n_levels = 0;
+  sd.level_domains = nullptr;
+  negf_status st = negf_plan(&p->fz, &sd, p->stream);
+  if (st != NEGF_OK) return st;
+  const int64_t nEs = p->fz_nE;
+  const int64_t pad = std::max(p->fz_pad0, p->fz_padN);
+  const size_t elems = (size_t)(fe + nEs + 4 * nEs * pad + nEs + 2 * nEs * fe);
+  cudaError_t e = cudaMalloc((void**)&p->fz_buf, elems * sizeof(double2) + (size_t)nEs * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->fz_map, map.size() * sizeof(int64_t));
+  if (e != cudaSuccess) { g_last_cuda = e; cudaGetLastError(); return NEGF_ERR_NOMEM; }
+  double2* q = reinterpret_cast<double2*>(p->fz_buf);
+  p->fz_H = q; q += fe;
+  p->fz_E = q; q += nEs;
+  p->fz_sL = q; q += nEs * pad;
+  p->fz_sR = q; q += nEs * pad;
+  p->fz_lL = q; q += nEs * pad;
+  p->fz_lR = q; q += nEs * pad;
+  p->fz_ld = q; q += nEs;
+  p->fz_Gb = q; q += nEs * fe;
+  p->fz_Gl = q; q += nEs * fe;
+  p->fz_info = reinterpret_cast<int32_t*>(q);
+  e = cudaMemcpy(p->fz_map, map.data(), map.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  return cuda_status(e);
+}
+
+// b x b lead matrices padded into zeroed fsz x fsz blocks at (at, at): with
+// a per-energy stride, nEs blocks at dstride (the chunk's n energies, then
+// the last one repeated for a short last chunk); shared (stride 0): one.
+cudaError_t fused_pad(const double2* src, int64_t stride, int b, double2* dst, int64_t dstride, int fsz, int at,
+                      int n, int nEs, cudaStream_t st) {
+  const int cnt = stride ? nEs : 1;
+  const int64_t ds = stride ? dstride : (int64_t)fsz * fsz;
+  NEGF_TRY(cudaMemsetAsync(dst, 0, sizeof(double2) * (size_t)(cnt * ds), st));
+  double2* d0 = dst + (int64_t)at * fsz + at;
+  if (!stride) return negf::copy2d(src, 0, b, d0, ds, fsz, b, b, 1.0, 0, 1, st);
+  NEGF_TRY(negf::copy2d(src, stride, b, d0, ds, fsz, b, b, 1.0, 0, n, st));
+  if (n < nEs) NEGF_TRY(negf::copy2d(src + (int64_t)(n - 1) * stride, 0, b, d0 + (int64_t)n * ds, ds, fsz, b, b, 1.0, 0,
+                                     nEs - n, st));
+  return cudaSuccess;
+}
+
+// negf_lesser of a block n-diagonal plan through its fused chain.
+negf_status fused_lesser(negf_plan_s* p, const double2* H, const double2* sigma_L, const double2* sigma_R,
+                         int64_t sigma_E_stride, const double2* E, const double2* sigma_less_L,
+                         const double2* sigma_less_R, int64_t sless_stride, const double2* less_diag,
+                         double2* G_band, double2* G_less, int32_t* info) {
+  negf_plan_s* f = p->fz;
+  cudaStream_t st = p->stream;
+  const int N = p->N, Nf = f->N, nEs = p->fz_nE;
+  const int b0 = p->b[0], bN = p->b[N - 1], fs0 = f->b[0], fsN = f->b[Nf - 1];
+  NEGF_TRY_STATUS(cudaMemsetAsync(p->fz_H, 0, sizeof(double2) * (size_t)p->fz_elems, st));
+  NEGF_TRY_STATUS(negf::band_remap(H, 0, p->fz_H, 0, p->fz_map, p->fz_nblk, 1, 0, st));
+  for (int e0 = 0; e0 < p->nE; e0 += nEs) {
+    const int n = std::min(nEs, p->nE - e0);
+    // energies of this sub-call; a short last call repeats its last energy
+    NEGF_TRY_STATUS(cudaMemcpyAsync(p->fz_E, E + e0, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+    if (n < nEs) NEGF_TRY_STATUS(negf::copy2d(E + e0 + n - 1, 0, 1, p->fz_E + n, 1, 1, 1, 1, 1.0, 0, nEs - n, st));
+    // padded leads: per-energy ones at the larger end block's size squared
+    // (one layout for both ends), shared ones as one block (stride 0)
+    const int64_t pad = std::max(p->fz_pad0, p->fz_padN);
+    const int64_t ps = sigma_E_stride ? pad : 0, ls = sless_stride ? pad : 0;
+    const double2 *pL = nullptr, *pR = nullptr, *lL = nullptr, *lR = nullptr, *ld = nullptr;
+    if (sigma_L) {
+      NEGF_TRY_STATUS(fused_pad(sigma_L + e0 * sigma_E_stride, sigma_E_stride, b0, p->fz_sL, pad, fs0, 0, n, nEs, st));
+      pL = p->fz_sL;
+    }
+    if (sigma_R) {
+      NEGF_TRY_STATUS(fused_pad(sigma_R + e0 * sigma_E_stride, sigma_E_stride, bN, p->fz_sR, pad, fsN, p->fz_rl, n,
+                                nEs, st));
+      pR = p->fz_sR;
+    }
+    if (sigma_less_L) {
+      NEGF_TRY_STATUS(fused_pad(sigma_less_L + e0 * sless_stride, sless_stride, b0, p->fz_lL, pad, fs0, 0, n, nEs, st));
+      lL = p->fz_lL;
+    }
+    if (sigma_less_R) {
+      NEGF_TRY_STATUS(fused_pad(sigma_less_R + e0 * sless_stride, sless_stride, bN, p->fz_lR, pad, fsN, p->fz_rl, n,
+                                nEs, st));
+      lR = p->fz_lR;
+    }
+    if (less_diag) {
+      NEGF_TRY_STATUS(cudaMemsetAsync(p->fz_ld, 0, sizeof(double2) * nEs, st));
+      NEGF_TRY_STATUS(cudaMemcpyAsync(p->fz_ld, less_diag + e0, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+      ld = p->fz_ld;
+    }
+    auto c = [](const double2* x) { return reinterpret_cast<const negf_c128*>(x); };
+    negf_status s = negf_lesser(f, c(p->fz_H), c(pL), c(pR), ps, c(p->fz_E), c(lL), c(lR), ls, c(ld),
+                                reinterpret_cast<negf_c128*>(p->fz_Gb), reinterpret_cast<negf_c128*>(p->fz_Gl),
+                                p->fz_info);
+    if (s != NEGF_OK) return s;
+    NEGF_TRY_STATUS(negf::band_remap(p->fz_Gb, p->fz_elems, G_band + (int64_t)e0 * p->band_elems, p->band_elems,
+                                     p->fz_map, p->fz_nblk, n, 1, st));
+    NEGF_TRY_STATUS(negf::band_remap(p->fz_Gl, p->fz_elems, G_less + (int64_t)e0 * p->band_elems, p->band_elems,
+                                     p->fz_map, p->fz_nblk, n, 1, st));
+    NEGF_TRY_STATUS(negf::fold_fused_status(info + e0, p->fz_info, n, p->w, p->d_err, f->d_err, st));
+  }
+  return NEGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream) {
   if (!out) return NEGF_ERR_ARG;
   *out = nullptr;
@@ -340,8 +496,14 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   if (d->n_domains > 1 && (d->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_UNSUPPORTED;
   if (d->precision == NEGF_MIXED && !negf::zgemm_tc_available()) return NEGF_ERR_UNSUPPORTED;
   if ((d->outputs & NEGF_OUT_GRAD) && w != 1) return NEGF_ERR_UNSUPPORTED;
-  if ((d->outputs & NEGF_OUT_LESSER) && (w != 1 || d->n_domains > 1 || (d->checkpoint_every > 0 && (d->outputs & NEGF_OUT_GRAD))))
+  if ((d->outputs & NEGF_OUT_LESSER) && (d->n_domains > 1 || (d->checkpoint_every > 0 && (d->outputs & NEGF_OUT_GRAD))))
     return NEGF_ERR_UNSUPPORTED;
+  if ((d->outputs & NEGF_OUT_LESSER) && w > 1)   // the fused chain's super-blocks must invert
+    for (int i = 0; i < d->n_blocks; i += w) {
+      int64_t sz = 0;
+      for (int j = i; j < std::min(d->n_blocks, i + w); ++j) sz += d->block_sizes[j];
+      if (sz > negf::zinv_max_block()) return NEGF_ERR_UNSUPPORTED;
+    }
   {
     cudaError_t ie = negf::kernels_init();
     if (ie != cudaSuccess) { g_last_cuda = ie; return NEGF_ERR_CUDA; }
@@ -456,7 +618,7 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   // Gamma_L, Gamma_R, P, Q, G_1N, and two more b1 x bN temporaries (gradient)
   p->scr_elems = sq(b0) + sq(bN) + 5 * (int64_t)b0 * bN;
 
-  const int64_t lesser_e = (d->outputs & NEGF_OUT_LESSER) ? 2 * te : 0;
+  const int64_t lesser_e = ((d->outputs & NEGF_OUT_LESSER) && w == 1) ? 2 * te : 0;
   const int64_t dh_e = grad ? p->bmax2 : 0;
   int64_t per_e = dh_e + lesser_e + te + xe + ye + (int64_t)(w + 1) * (w + 1) * p->s_slot * std::max(1, p->n_domains) +
                   (p->full_row ? re : (int64_t)(w + 1) * b0 * bmax) + 2 * p->p_elems + ck_elems +
@@ -554,6 +716,10 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
       }
     }
   }
+  if ((d->outputs & NEGF_OUT_LESSER) && w > 1) {
+    const negf_status fs = fused_lesser_setup(p, d);
+    if (fs != NEGF_OK) { negf_destroy(p); return fs; }
+  }
   *out = p;
   return NEGF_OK;
 }
@@ -587,6 +753,9 @@ void negf_destroy(negf_plan_t* p) {
   cudaFree(p->ws);
   cudaFree(p->d_err);
   if (p->host_io) cudaFree(p->host_io);
+  if (p->fz) negf_destroy(p->fz);
+  if (p->fz_map) cudaFree(p->fz_map);
+  if (p->fz_buf) cudaFree(p->fz_buf);
   delete p;
 }
 
@@ -1108,6 +1277,11 @@ negf_status negf_lesser(negf_plan_t* p, const negf_c128* H, const negf_c128* sig
       bad_sigma_stride(p, sless_stride))
     return NEGF_ERR_ARG;
   if (!(p->outputs & NEGF_OUT_LESSER)) return NEGF_ERR_ARG;
+  if (p->w > 1)
+    return p->fz ? fused_lesser(p, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R, sigma_E_stride,
+                                (const double2*)E, (const double2*)sigma_less_L, (const double2*)sigma_less_R,
+                                sless_stride, (const double2*)less_diag, (double2*)G_band, (double2*)G_less, info)
+                 : NEGF_ERR_UNSUPPORTED;
   CallKey key{};
   key.kind = 4;
   key.stride = sigma_E_stride * 1000003 + sless_stride;

@@ -89,6 +89,17 @@ cudaError_t lincomb(double2* dst, int64_t sDst, int64_t n, int batch, const doub
                     const double2* x1, int64_t s1, double c1, const double2* x2, int64_t s2, double c2,
                     const double2* x3, int64_t s3, double c3, cudaStream_t st);
 
+// Block copies between a block n-diagonal band and the band of its fused
+// block tridiagonal form over a batch (map: 7 int64 per block, see
+// negf_misc.cu); dir 0: original -> fused, 1: fused -> original.
+cudaError_t band_remap(const double2* src, int64_t sSrc, double2* dst, int64_t sDst, const int64_t* map, int nblk,
+                       int batch, int dir, cudaStream_t st);
+
+// info[e] from a fused sub-plan's (super-layer -> its first layer) for e < n,
+// and the sub-plan's error word folded into err (and cleared).
+cudaError_t fold_fused_status(int32_t* info, const int32_t* sub_info, int n, int w, int* err, int* sub_err,
+                              cudaStream_t st);
+
 // D[e] = I (b x b).
 cudaError_t set_identity(double2* D, int64_t sD, int b, int batch, cudaStream_t st);
 

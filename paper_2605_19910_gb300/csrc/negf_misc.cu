@@ -281,6 +281,44 @@ cudaError_t copy_blocks(const double2* src, int64_t sSrc, double2* dst, int64_t 
   return cudaGetLastError();
 }
 
+// Block copies between the band of a block n-diagonal chain and the band of
+// its fused block tridiagonal form (Sec. 2.3, block fusing).  map holds 7
+// entries per block: offset in the original band, rows, columns, offset of
+// the super-block in the fused band, its leading dimension, and the block's
+// row / column inside it.  dir 0: original -> fused, dir 1: fused -> original.
+__global__ void band_remap_kernel(const double2* __restrict__ src, int64_t sSrc, double2* __restrict__ dst,
+                                  int64_t sDst, const int64_t* __restrict__ map, int dir) {
+  const int64_t* m = map + 7 * (int64_t)blockIdx.x;
+  const int64_t oo = m[0], fo = m[3];
+  const int r = (int)m[1], c = (int)m[2], fld = (int)m[4], r0 = (int)m[5], c0 = (int)m[6];
+  const double2* sp = src + (int64_t)blockIdx.y * sSrc;
+  double2* dp = dst + (int64_t)blockIdx.y * sDst;
+  for (int idx = threadIdx.x; idx < r * c; idx += blockDim.x) {
+    const int i = idx / c, j = idx - i * c;
+    const int64_t oi = oo + idx, fi = fo + (int64_t)(r0 + i) * fld + c0 + j;
+    if (dir == 0) dp[fi] = sp[oi];
+    else dp[oi] = sp[fi];
+  }
+}
+
+// info[e] = the first layer of the failing w-layer group (sub_info[e] is the
+// failing super-layer, 1-based; 0 = none), and the sub-plan's error word
+// folded into the plan's (and cleared).
+__global__ void fold_fused_status_kernel(int32_t* __restrict__ info, const int32_t* __restrict__ sub_info, int n,
+                                         int w, int* err, int* sub_err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int v = sub_info[i];
+    info[i] = v > 0 ? (v - 1) * w + 1 : 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int word = *sub_err;
+    if (word) {
+      atomicOr(err, word);
+      *sub_err = 0;
+    }
+  }
+}
+
 cudaError_t copy2d(const double2* src, int64_t sSrc, int ldSrc, double2* dst, int64_t sDst, int ldDst,
                    int rows, int cols, double scale, int acc, int batch, cudaStream_t st) {
   if (batch <= 0 || rows <= 0 || cols <= 0) return cudaSuccess;
@@ -378,6 +416,27 @@ cudaError_t frob2_diff(const double2* A, int64_t sA, const double2* B, int64_t s
 cudaError_t sqrt_scale(double* out, int n, double scale, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   sqrt_scale_kernel<<<(n + 255) / 256, 256, 0, st>>>(out, n, scale);
+  return cudaGetLastError();
+}
+
+
+cudaError_t band_remap(const double2* src, int64_t sSrc, double2* dst, int64_t sDst, const int64_t* map, int nblk,
+                       int batch, int dir, cudaStream_t st) {
+  if (nblk <= 0 || batch <= 0) return cudaSuccess;
+  for (int b0 = 0; b0 < batch; b0 += 65535) {   // grid.y limit
+    const int nb = batch - b0 < 65535 ? batch - b0 : 65535;
+    band_remap_kernel<<<dim3(nblk, nb), 256, 0, st>>>(src + (int64_t)b0 * sSrc, sSrc, dst + (int64_t)b0 * sDst, sDst,
+                                                     map, dir);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t fold_fused_status(int32_t* info, const int32_t* sub_info, int n, int w, int* err, int* sub_err,
+                              cudaStream_t st) {
+  const int blocks = n > 0 ? (n + 255) / 256 : 1;
+  fold_fused_status_kernel<<<blocks < 1024 ? blocks : 1024, 256, 0, st>>>(info, sub_info, n, w, err, sub_err);
   return cudaGetLastError();
 }
 

@@ -99,6 +99,19 @@ struct negf_plan_s {
   // (allocated at the first call, sized for the sigma stride of that call)
   char* host_io = nullptr;
   size_t host_io_bytes = 0;
+  // Keldysh on a block n-diagonal plan (w >= 2): a block tridiagonal
+  // sub-plan on the fused chain (super-layers of w layers) runs negf_lesser
+  // for fz_nE energies at a time; the band of H and the results move
+  // between the two packings by block copies (fz_map: 7 int64 per original
+  // band block), the lead terms are padded into the end super-blocks
+  negf_plan_s* fz = nullptr;
+  int fz_nE = 0, fz_nblk = 0, fz_rl = 0;       // energies per sub-call, blocks, layer N's offset in its super-block
+  int64_t fz_elems = 0, fz_pad0 = 0, fz_padN = 0;   // fused band elements; end super-block sizes^2
+  int64_t* fz_map = nullptr;                   // device map
+  char* fz_buf = nullptr;                      // device buffers of the sub-calls
+  double2 *fz_H = nullptr, *fz_E = nullptr, *fz_sL = nullptr, *fz_sR = nullptr, *fz_lL = nullptr, *fz_lR = nullptr,
+          *fz_ld = nullptr, *fz_Gb = nullptr, *fz_Gl = nullptr;
+  int32_t* fz_info = nullptr;
   double2* LW_ws = nullptr;     // Keldysh: W_i = Q_ii t_i^H per layer (t_i layout)
   double2* LG_ws = nullptr;     // Keldysh: right-connected g^<_i per layer
 

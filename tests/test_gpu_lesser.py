@@ -130,9 +130,11 @@ def test_lesser_plan_requirements(P):
         plan.lesser(Hp, sL, sR, E)
     assert ei.value.status == P.NEGF_ERR_ARG
     plan.close()
+    # n = 5 runs on the fused chain, whose super-blocks (two layers) must invert
     with pytest.raises(P.NegfError) as ei:
-        P.Plan([4] * 6, 5, 1, outputs=P.NEGF_OUT_LESSER)
+        P.Plan([100] * 6, 5, 1, outputs=P.NEGF_OUT_LESSER)
     assert ei.value.status == P.NEGF_ERR_UNSUPPORTED
+    P.Plan([4] * 6, 5, 1, outputs=P.NEGF_OUT_LESSER).close()
 
 
 @pytest.mark.parametrize("N", [6, 9])
@@ -154,3 +156,36 @@ def test_lesser_pentadiagonal_through_the_fused_chain(P, N):
         assert band_rel_err(Gl[e], ref, prob.sizes, 2) < FP64_TOL, e
         refR = O.dense_selected(M, prob.sizes, 2)["band"]
         assert band_rel_err(Gb[e], refR, prob.sizes, 2) < FP64_TOL, e
+
+
+@pytest.mark.parametrize("w,N,precision", [(2, 11, "fp64"), (3, 10, "fp64"), (2, 9, "mixed")])
+def test_lesser_ndiag_per_energy_leads_and_diagonal_term(P, w, N, precision):
+    """n = 5 and 7 through the C-ABI (negf_lesser on the plan's fused chain),
+    per-energy lead self-energies of both kinds and the per-energy diagonal
+    term, FP64 and mixed, against the oracle's dense Keldysh equation and
+    dense retarded band."""
+    import torch
+    rng = np.random.default_rng(140 + 10 * w + N)
+    nE = 3
+    prob = make_problem(N, b=None, size_range=(3, 8), w=w, n_energies=nE, eta=1e-3, seed=141 + N)
+    b0, bN = prob.sizes[0], prob.sizes[-1]
+    slL = np.stack([_sless(rng, b0) for _ in range(nE)])
+    slR = np.stack([_sless(rng, bN) for _ in range(nE)])
+    diag = 2e-3j * np.array([0.3, 0.5, 0.7])
+    Hp, sL, sR, E = to_dev(prob, torch, per_energy_sigma=True)
+    plan = P.Plan(prob.sizes, 2 * w + 1, nE, precision=precision, outputs=P.NEGF_OUT_BAND | P.NEGF_OUT_LESSER)
+    Gb, Gl = plan.lesser(Hp, sL, sR, E, torch.tensor(slL, device="cuda"), torch.tensor(slR, device="cuda"),
+                         torch.tensor(diag, device="cuda"))
+    assert not plan.info.cpu().numpy().any()
+    plan.close()
+    Gb, Gl = Gb.cpu().numpy(), Gl.cpu().numpy()
+    tol = FP64_TOL if precision == "fp64" else MIXED_TOL
+    for e in range(nE):
+        M = O.system_blocks(prob, prob.energies[e])
+        sl = {i: diag[e] * np.eye(prob.sizes[i]) for i in range(N)}
+        sl[0] = sl[0] + slL[e]
+        sl[N - 1] = sl[N - 1] + slR[e]
+        ref = O.lesser_dense(M, prob.sizes, w, sl)
+        assert band_rel_err(Gl[e], ref, prob.sizes, w) < tol, e
+        refR = O.dense_selected(M, prob.sizes, w)["band"]
+        assert band_rel_err(Gb[e], refR, prob.sizes, w) < tol, e
