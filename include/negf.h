@@ -266,7 +266,12 @@ negf_status negf_transmission(negf_plan_t* p, const negf_c128* H, const negf_c12
  *   dSigma_L: b_1 x b_1 per energy with stride sigma_E_stride (0 = summed
  *             over energies into one matrix); dSigma_R likewise.  Either may
  *             be NULL.
- * Requires a plan with NEGF_OUT_GRAD, n_domains == 1 and band_n == 3. */
+ * Requires a plan with NEGF_OUT_GRAD and n_domains == 1.  Block n-diagonal
+ * plans (band_n >= 5) run it on their fused block tridiagonal chain (a
+ * sub-plan on w-layer super-blocks, within NEGF_MAX_BLOCK; checkpoint_every
+ * applies there): the fused H is the band laid out on super-blocks, so each
+ * band block's gradient is its sub-block of the super-block's gradient, and
+ * info[e] is the first layer of a failing w-layer group. */
 negf_status negf_grad(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
                       const negf_c128* sigma_R, int64_t sigma_E_stride,
                       const negf_c128* E, const double* dL_dT, double* T,

@@ -301,12 +301,14 @@ negf_status negf_measure_r_inv(int32_t b, int32_t batch, int32_t precision, doub
 
 namespace {
 
-// Keldysh on a block n-diagonal plan: the block tridiagonal sub-plan of its
-// fused chain (Sec. 2.3, block fusing: super-layer J holds layers
-// [J w, (J + 1) w), the last one possibly fewer), the block map between the
-// two band packings and the device buffers of one sub-call.  Energies run
-// fz_nE at a time so that the fused outputs stay within about 8 GiB.
-negf_status fused_lesser_setup(negf_plan_s* p, const negf_desc* d) {
+// Keldysh and the adjoint on a block n-diagonal plan run on its fused
+// block tridiagonal chain (Sec. 2.3, block fusing: super-layer J holds layers
+// [J w, (J + 1) w), the last one possibly fewer): a sub-plan on the
+// super-blocks, the block map between the two band packings and the device
+// buffers of the sub-calls.  The Keldysh sub-calls take fz_nE energies at a
+// time so that the fused outputs stay within about 8 GiB; the adjoint's take
+// every energy (its fused outputs are one band and the leads' gradients).
+negf_status fused_setup(negf_plan_s* p, const negf_desc* d) {
   const int N = p->N, w = p->w, Nf = (N + w - 1) / w;
   std::vector<int32_t> fs(Nf, 0);
   std::vector<int> start(N + 1, 0), fstart(Nf + 1, 0);
@@ -337,42 +339,65 @@ negf_status fused_lesser_setup(negf_plan_s* p, const negf_desc* d) {
   p->fz_rl = start[N - 1] - fstart[Nf - 1];
   p->fz_pad0 = sq(fs[0]);
   p->fz_padN = sq(fs[Nf - 1]);
-  const double per_e = 2.0 * (double)fe * sizeof(double2);
-  p->fz_nE = (int)std::max(1.0, std::min((double)p->nE, std::floor(8.0 * (1ull << 30) / per_e)));
+  const int64_t pad = std::max(p->fz_pad0, p->fz_padN);
+  cudaError_t e = cudaMalloc((void**)&p->fz_map, map.size() * sizeof(int64_t));
+  if (e != cudaSuccess) { g_last_cuda = e; cudaGetLastError(); return NEGF_ERR_NOMEM; }
+  e = cudaMemcpy(p->fz_map, map.data(), map.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_status(e);
   negf_desc sd = *d;
   sd.n_blocks = Nf;
   sd.block_sizes = fs.data();
   sd.band_n = 3;
-  sd.n_energies = p->fz_nE;
   sd.product_bits = p->bits;
   sd.refine_steps = 0;
-  sd.outputs = NEGF_OUT_BAND | NEGF_OUT_LESSER;
-  sd.checkpoint_every = 0;
   sd.n_domains = 1;
   sd.domain_first_block = nullptr;
   sd.n_levels = 0;
   sd.level_domains = nullptr;
-  negf_status st = negf_plan(&p->fz, &sd, p->stream);
-  if (st != NEGF_OK) return st;
-  const int64_t nEs = p->fz_nE;
-  const int64_t pad = std::max(p->fz_pad0, p->fz_padN);
-  const size_t elems = (size_t)(fe + nEs + 4 * nEs * pad + nEs + 2 * nEs * fe);
-  cudaError_t e = cudaMalloc((void**)&p->fz_buf, elems * sizeof(double2) + (size_t)nEs * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&p->fz_map, map.size() * sizeof(int64_t));
-  if (e != cudaSuccess) { g_last_cuda = e; cudaGetLastError(); return NEGF_ERR_NOMEM; }
-  double2* q = reinterpret_cast<double2*>(p->fz_buf);
-  p->fz_H = q; q += fe;
-  p->fz_E = q; q += nEs;
-  p->fz_sL = q; q += nEs * pad;
-  p->fz_sR = q; q += nEs * pad;
-  p->fz_lL = q; q += nEs * pad;
-  p->fz_lR = q; q += nEs * pad;
-  p->fz_ld = q; q += nEs;
-  p->fz_Gb = q; q += nEs * fe;
-  p->fz_Gl = q; q += nEs * fe;
-  p->fz_info = reinterpret_cast<int32_t*>(q);
-  e = cudaMemcpy(p->fz_map, map.data(), map.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
-  return cuda_status(e);
+  if (d->outputs & NEGF_OUT_LESSER) {
+    const double per_e = 2.0 * (double)fe * sizeof(double2);
+    p->fz_nE = (int)std::max(1.0, std::min((double)p->nE, std::floor(8.0 * (1ull << 30) / per_e)));
+    negf_desc ld = sd;
+    ld.n_energies = p->fz_nE;
+    ld.outputs = NEGF_OUT_BAND | NEGF_OUT_LESSER;
+    ld.checkpoint_every = 0;
+    negf_status st = negf_plan(&p->fz, &ld, p->stream);
+    if (st != NEGF_OK) return st;
+    const int64_t nEs = p->fz_nE;
+    const size_t elems = (size_t)(fe + nEs + 4 * nEs * pad + nEs + 2 * nEs * fe);
+    e = cudaMalloc((void**)&p->fz_buf, elems * sizeof(double2) + (size_t)nEs * sizeof(int32_t));
+    if (e != cudaSuccess) { g_last_cuda = e; cudaGetLastError(); return NEGF_ERR_NOMEM; }
+    double2* q = reinterpret_cast<double2*>(p->fz_buf);
+    p->fz_H = q; q += fe;
+    p->fz_E = q; q += nEs;
+    p->fz_sL = q; q += nEs * pad;
+    p->fz_sR = q; q += nEs * pad;
+    p->fz_lL = q; q += nEs * pad;
+    p->fz_lR = q; q += nEs * pad;
+    p->fz_ld = q; q += nEs;
+    p->fz_Gb = q; q += nEs * fe;
+    p->fz_Gl = q; q += nEs * fe;
+    p->fz_info = reinterpret_cast<int32_t*>(q);
+  }
+  if (d->outputs & NEGF_OUT_GRAD) {
+    negf_desc gd = sd;
+    gd.outputs = NEGF_OUT_GRAD;   // checkpoint_every passes through
+    negf_status st = negf_plan(&p->fzg, &gd, p->stream);
+    if (st != NEGF_OK) return st;
+    const int64_t nE = p->nE;
+    const size_t elems = (size_t)(2 * fe + 4 * nE * pad);
+    e = cudaMalloc((void**)&p->fzg_buf, elems * sizeof(double2) + (size_t)nE * sizeof(int32_t));
+    if (e != cudaSuccess) { g_last_cuda = e; cudaGetLastError(); return NEGF_ERR_NOMEM; }
+    double2* q = reinterpret_cast<double2*>(p->fzg_buf);
+    p->fzg_H = q; q += fe;
+    p->fzg_dH = q; q += fe;
+    p->fzg_sL = q; q += nE * pad;
+    p->fzg_sR = q; q += nE * pad;
+    p->fzg_dL = q; q += nE * pad;
+    p->fzg_dR = q; q += nE * pad;
+    p->fzg_info = reinterpret_cast<int32_t*>(q);
+  }
+  return NEGF_OK;
 }
 
 // b x b lead matrices padded into zeroed fsz x fsz blocks at (at, at): with
@@ -449,6 +474,40 @@ negf_status fused_lesser(negf_plan_s* p, const double2* H, const double2* sigma_
   return NEGF_OK;
 }
 
+// negf_grad_strided of a block n-diagonal plan through its fused chain: the
+// fused H is the original band laid out on super-blocks (zeros elsewhere), so
+// each original block's gradient is its sub-block of the super-block's
+// gradient, and the leads' gradients are the sub-blocks where the leads
+// were padded in.
+negf_status fused_grad(negf_plan_s* p, const double2* H, const double2* sigma_L, const double2* sigma_R,
+                       int64_t sigma_E_stride, const double2* E, const double* dL_dT, double* T, double2* dH,
+                       double2* dSigma_L, int64_t dL_stride, double2* dSigma_R, int64_t dR_stride, int32_t* info) {
+  negf_plan_s* f = p->fzg;
+  cudaStream_t st = p->stream;
+  const int N = p->N, Nf = f->N, nE = p->nE;
+  const int b0 = p->b[0], bN = p->b[N - 1], fs0 = f->b[0], fsN = f->b[Nf - 1];
+  const int64_t pad = std::max(p->fz_pad0, p->fz_padN);
+  NEGF_TRY_STATUS(cudaMemsetAsync(p->fzg_H, 0, sizeof(double2) * (size_t)p->fz_elems, st));
+  NEGF_TRY_STATUS(negf::band_remap(H, 0, p->fzg_H, 0, p->fz_map, p->fz_nblk, 1, 0, st));
+  NEGF_TRY_STATUS(fused_pad(sigma_L, sigma_E_stride, b0, p->fzg_sL, pad, fs0, 0, nE, nE, st));
+  NEGF_TRY_STATUS(fused_pad(sigma_R, sigma_E_stride, bN, p->fzg_sR, pad, fsN, p->fz_rl, nE, nE, st));
+  const int64_t ps = sigma_E_stride ? pad : 0, pls = dL_stride ? pad : 0, prs = dR_stride ? pad : 0;
+  auto c = [](const double2* x) { return reinterpret_cast<const negf_c128*>(x); };
+  auto m = [](double2* x) { return reinterpret_cast<negf_c128*>(x); };
+  negf_status s = negf_grad_strided(f, c(p->fzg_H), c(p->fzg_sL), c(p->fzg_sR), ps, c(E), dL_dT, T, m(p->fzg_dH),
+                                    dSigma_L ? m(p->fzg_dL) : nullptr, pls, dSigma_R ? m(p->fzg_dR) : nullptr, prs,
+                                    p->fzg_info);
+  if (s != NEGF_OK) return s;
+  NEGF_TRY_STATUS(negf::band_remap(p->fzg_dH, 0, dH, 0, p->fz_map, p->fz_nblk, 1, 1, st));
+  if (dSigma_L)
+    NEGF_TRY_STATUS(negf::copy2d(p->fzg_dL, pls, fs0, dSigma_L, dL_stride, b0, b0, b0, 1.0, 0, dL_stride ? nE : 1, st));
+  if (dSigma_R)
+    NEGF_TRY_STATUS(negf::copy2d(p->fzg_dR + (int64_t)p->fz_rl * fsN + p->fz_rl, prs, fsN, dSigma_R, dR_stride, bN,
+                                 bN, bN, 1.0, 0, dR_stride ? nE : 1, st));
+  NEGF_TRY_STATUS(negf::fold_fused_status(info, p->fzg_info, nE, p->w, p->d_err, f->d_err, st));
+  return NEGF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -495,10 +554,9 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
   const int w = (d->band_n - 1) / 2;
   if (d->n_domains > 1 && (d->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_UNSUPPORTED;
   if (d->precision == NEGF_MIXED && !negf::zgemm_tc_available()) return NEGF_ERR_UNSUPPORTED;
-  if ((d->outputs & NEGF_OUT_GRAD) && w != 1) return NEGF_ERR_UNSUPPORTED;
   if ((d->outputs & NEGF_OUT_LESSER) && (d->n_domains > 1 || (d->checkpoint_every > 0 && (d->outputs & NEGF_OUT_GRAD))))
     return NEGF_ERR_UNSUPPORTED;
-  if ((d->outputs & NEGF_OUT_LESSER) && w > 1)   // the fused chain's super-blocks must invert
+  if ((d->outputs & (NEGF_OUT_LESSER | NEGF_OUT_GRAD)) && w > 1)   // the fused chain's super-blocks must invert
     for (int i = 0; i < d->n_blocks; i += w) {
       int64_t sz = 0;
       for (int j = i; j < std::min(d->n_blocks, i + w); ++j) sz += d->block_sizes[j];
@@ -587,7 +645,7 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
     }
   }
   p->s_slot = sq(bmax);
-  const bool grad = (d->outputs & NEGF_OUT_GRAD) != 0;
+  const bool grad = (d->outputs & NEGF_OUT_GRAD) != 0 && w == 1;   // w > 1: on the fused chain
   const int bN = p->b[N - 1], b0 = p->b[0];
   p->bmax2 = sq(bmax);
   p->bmaxN = (int64_t)bmax * bN;
@@ -716,8 +774,8 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
       }
     }
   }
-  if ((d->outputs & NEGF_OUT_LESSER) && w > 1) {
-    const negf_status fs = fused_lesser_setup(p, d);
+  if ((d->outputs & (NEGF_OUT_LESSER | NEGF_OUT_GRAD)) && w > 1) {
+    const negf_status fs = fused_setup(p, d);
     if (fs != NEGF_OK) { negf_destroy(p); return fs; }
   }
   *out = p;
@@ -754,8 +812,10 @@ void negf_destroy(negf_plan_t* p) {
   cudaFree(p->d_err);
   if (p->host_io) cudaFree(p->host_io);
   if (p->fz) negf_destroy(p->fz);
+  if (p->fzg) negf_destroy(p->fzg);
   if (p->fz_map) cudaFree(p->fz_map);
   if (p->fz_buf) cudaFree(p->fz_buf);
+  if (p->fzg_buf) cudaFree(p->fzg_buf);
   delete p;
 }
 
@@ -1001,6 +1061,11 @@ negf_status negf_grad_strided(negf_plan_t* p, const negf_c128* H, const negf_c12
     return NEGF_ERR_ARG;
   if (bad_sigma_stride(p, dSigma_L_stride) || bad_sigma_stride(p, dSigma_R_stride)) return NEGF_ERR_ARG;
   if (!(p->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
+  if (p->w > 1)
+    return p->fzg ? fused_grad(p, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R, sigma_E_stride,
+                               (const double2*)E, dL_dT, T, (double2*)dH, (double2*)dSigma_L, dSigma_L_stride,
+                               (double2*)dSigma_R, dSigma_R_stride, info)
+                  : NEGF_ERR_UNSUPPORTED;
   CallKey key{};
   key.kind = CALL_GRAD;
   key.stride = sigma_E_stride;

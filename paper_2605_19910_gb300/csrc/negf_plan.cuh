@@ -112,6 +112,11 @@ struct negf_plan_s {
   double2 *fz_H = nullptr, *fz_E = nullptr, *fz_sL = nullptr, *fz_sR = nullptr, *fz_lL = nullptr, *fz_lR = nullptr,
           *fz_ld = nullptr, *fz_Gb = nullptr, *fz_Gl = nullptr;
   int32_t* fz_info = nullptr;
+  negf_plan_s* fzg = nullptr;                  // the adjoint's sub-plan (every energy at once)
+  char* fzg_buf = nullptr;
+  double2 *fzg_H = nullptr, *fzg_dH = nullptr, *fzg_sL = nullptr, *fzg_sR = nullptr, *fzg_dL = nullptr,
+          *fzg_dR = nullptr;
+  int32_t* fzg_info = nullptr;
   double2* LW_ws = nullptr;     // Keldysh: W_i = Q_ii t_i^H per layer (t_i layout)
   double2* LG_ws = nullptr;     // Keldysh: right-connected g^<_i per layer
 

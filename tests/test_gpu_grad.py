@@ -192,3 +192,52 @@ def test_autograd_function(P):
     assert rel_err(sL.grad.cpu().numpy(), gL) < FP64_TOL
     assert rel_err(sR.grad.cpu().numpy(), gR) < FP64_TOL
     assert rel_err(T.detach().cpu().numpy(), Tref) < FP64_TOL
+
+
+def _oracle_grad_w(prob, weights, w):
+    N = prob.n_blocks
+    pairs = O.band_pairs(N, w)
+    gH = {k: np.zeros((prob.sizes[k[0]], prob.sizes[k[1]]), complex) for k in pairs}
+    gL, gR, T = [], [], []
+    for e, E in enumerate(prob.energies):
+        M = O.system_blocks(prob, E)
+        r = O.rgf_selected(M, prob.sizes, w, first_row=True)
+        lc = O.rgf_last_column(M, prob.sizes, w)
+        T.append(O.transmission(r["G1N"], prob.sigma_L, prob.sigma_R))
+        g, a, b = O.transmission_grad(r["first_row"], lc, pairs, prob.sigma_L, prob.sigma_R, N)
+        for k in pairs:
+            gH[k] += weights[e] * g[k]
+        gL.append(weights[e] * a)
+        gR.append(weights[e] * b)
+    return gH, np.stack(gL), np.stack(gR), np.array(T)
+
+
+@pytest.mark.parametrize("w,N,ck", [(2, 9, 0), (3, 10, 0), (2, 12, 2)])
+def test_grad_block_ndiagonal_through_the_fused_chain(P, w, N, ck):
+    """n = 5 and 7 (and n = 5 checkpointed on the fused chain): dH for every
+    band block |a - b| <= w and the energy-summed dSigma_L / dSigma_R, against
+    the oracle's gradient over the n-diagonal band."""
+    import torch
+    rng = np.random.default_rng(200 + 10 * w + N)
+    nE = 4
+    prob = make_problem(N, b=None, size_range=(3, 8), w=w, n_energies=nE, eta=1e-3, seed=201 + N)
+    prob.sigma_L = _random_sigma(rng, prob.sizes[0])
+    prob.sigma_R = _random_sigma(rng, prob.sizes[-1])
+    weights = rng.normal(size=nE)
+    Hp = torch.tensor(P.pack_band(prob.H, prob.sizes, w), device="cuda")
+    sL = torch.tensor(prob.sigma_L, device="cuda")
+    sR = torch.tensor(prob.sigma_R, device="cuda")
+    E = torch.tensor(prob.energies, device="cuda")
+    plan = P.Plan(prob.sizes, 2 * w + 1, nE, outputs=P.NEGF_OUT_TRANSMISSION | P.NEGF_OUT_GRAD,
+                  checkpoint_every=ck)
+    T, dH, dSL, dSR = plan.grad(Hp, sL, sR, E, torch.tensor(weights, device="cuda"))
+    assert not plan.info.cpu().numpy().any()
+    plan.close()
+    gH, gL, gR, Tref = _oracle_grad_w(prob, weights, w)
+    got = P.unpack_band(dH.cpu().numpy(), prob.sizes, w)
+    num = sum(np.linalg.norm(got[k] - v) ** 2 for k, v in gH.items())
+    den = sum(np.linalg.norm(v) ** 2 for v in gH.values())
+    assert np.sqrt(num / den) < FP64_TOL
+    assert rel_err(dSL.cpu().numpy(), gL.sum(0)) < FP64_TOL   # shared leads: energy-summed gradients
+    assert rel_err(dSR.cpu().numpy(), gR.sum(0)) < FP64_TOL
+    assert rel_err(T.cpu().numpy(), Tref) < FP64_TOL
