@@ -266,8 +266,10 @@ negf_status negf_transmission(negf_plan_t* p, const negf_c128* H, const negf_c12
  *   dSigma_L: b_1 x b_1 per energy with stride sigma_E_stride (0 = summed
  *             over energies into one matrix); dSigma_R likewise.  Either may
  *             be NULL.
- * Requires a plan with NEGF_OUT_GRAD and n_domains == 1.  Block n-diagonal
- * plans (band_n >= 5) run it on their fused block tridiagonal chain (a
+ * Requires a plan with NEGF_OUT_GRAD.  DDRGF plans (n_domains > 1) run it on
+ * a plain RGF sub-plan of the same chain (the gradient of T does not depend
+ * on the method that solved for it).  Block n-diagonal plans (band_n >= 5)
+ * run it on their fused block tridiagonal chain (a
  * sub-plan on w-layer super-blocks, within NEGF_MAX_BLOCK; checkpoint_every
  * applies there): the fused H is the band laid out on super-blocks, so each
  * band block's gradient is its sub-block of the super-block's gradient, and

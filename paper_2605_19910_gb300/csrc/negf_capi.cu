@@ -305,7 +305,8 @@ namespace {
 // block tridiagonal chain (Sec. 2.3, block fusing: super-layer J holds layers
 // [J w, (J + 1) w), the last one possibly fewer): a sub-plan on the
 // super-blocks, the block map between the two band packings and the device
-// buffers of the sub-calls.  The Keldysh sub-calls take fz_nE energies at a
+// buffers of the sub-calls.  The adjoint of a DDRGF plan runs the same way on
+// a plain RGF sub-plan of its chain (w = 1: the map is the identity layout).  The Keldysh sub-calls take fz_nE energies at a
 // time so that the fused outputs stay within about 8 GiB; the adjoint's take
 // every energy (its fused outputs are one band and the leads' gradients).
 negf_status fused_setup(negf_plan_s* p, const negf_desc* d) {
@@ -354,7 +355,7 @@ negf_status fused_setup(negf_plan_s* p, const negf_desc* d) {
   sd.domain_first_block = nullptr;
   sd.n_levels = 0;
   sd.level_domains = nullptr;
-  if (d->outputs & NEGF_OUT_LESSER) {
+  if ((d->outputs & NEGF_OUT_LESSER) && w > 1) {
     const double per_e = 2.0 * (double)fe * sizeof(double2);
     p->fz_nE = (int)std::max(1.0, std::min((double)p->nE, std::floor(8.0 * (1ull << 30) / per_e)));
     negf_desc ld = sd;
@@ -552,7 +553,6 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
     }
   }
   const int w = (d->band_n - 1) / 2;
-  if (d->n_domains > 1 && (d->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_UNSUPPORTED;
   if (d->precision == NEGF_MIXED && !negf::zgemm_tc_available()) return NEGF_ERR_UNSUPPORTED;
   if ((d->outputs & NEGF_OUT_LESSER) && (d->n_domains > 1 || (d->checkpoint_every > 0 && (d->outputs & NEGF_OUT_GRAD))))
     return NEGF_ERR_UNSUPPORTED;
@@ -645,7 +645,9 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
     }
   }
   p->s_slot = sq(bmax);
-  const bool grad = (d->outputs & NEGF_OUT_GRAD) != 0 && w == 1;   // w > 1: on the fused chain
+  // block n-diagonal and DDRGF plans run the adjoint on a sub-plan (the
+  // fused chain, or the same chain by plain RGF)
+  const bool grad = (d->outputs & NEGF_OUT_GRAD) != 0 && w == 1 && p->n_domains == 1;
   const int bN = p->b[N - 1], b0 = p->b[0];
   p->bmax2 = sq(bmax);
   p->bmaxN = (int64_t)bmax * bN;
@@ -774,7 +776,7 @@ negf_status negf_plan(negf_plan_t** out, const negf_desc* din, void* cuda_stream
       }
     }
   }
-  if ((d->outputs & (NEGF_OUT_LESSER | NEGF_OUT_GRAD)) && w > 1) {
+  if (((d->outputs & NEGF_OUT_LESSER) && w > 1) || ((d->outputs & NEGF_OUT_GRAD) && (w > 1 || p->n_domains > 1))) {
     const negf_status fs = fused_setup(p, d);
     if (fs != NEGF_OK) { negf_destroy(p); return fs; }
   }
@@ -1061,7 +1063,7 @@ negf_status negf_grad_strided(negf_plan_t* p, const negf_c128* H, const negf_c12
     return NEGF_ERR_ARG;
   if (bad_sigma_stride(p, dSigma_L_stride) || bad_sigma_stride(p, dSigma_R_stride)) return NEGF_ERR_ARG;
   if (!(p->outputs & NEGF_OUT_GRAD)) return NEGF_ERR_ARG;
-  if (p->w > 1)
+  if (p->w > 1 || p->n_domains > 1)
     return p->fzg ? fused_grad(p, (const double2*)H, (const double2*)sigma_L, (const double2*)sigma_R, sigma_E_stride,
                                (const double2*)E, dL_dT, T, (double2*)dH, (double2*)dSigma_L, dSigma_L_stride,
                                (double2*)dSigma_R, dSigma_R_stride, info)

@@ -212,11 +212,12 @@ def _oracle_grad_w(prob, weights, w):
     return gH, np.stack(gL), np.stack(gR), np.array(T)
 
 
-@pytest.mark.parametrize("w,N,ck", [(2, 9, 0), (3, 10, 0), (2, 12, 2)])
-def test_grad_block_ndiagonal_through_the_fused_chain(P, w, N, ck):
-    """n = 5 and 7 (and n = 5 checkpointed on the fused chain): dH for every
+@pytest.mark.parametrize("w,N,ck,nd", [(2, 9, 0, 1), (3, 10, 0, 1), (2, 12, 2, 1), (1, 14, 0, 3), (2, 18, 0, 2)])
+def test_grad_block_ndiagonal_through_the_fused_chain(P, w, N, ck, nd):
+    """n = 5 and 7 (and n = 5 checkpointed on the fused chain), and DDRGF plans
+    (n = 3 and 5, whose adjoint runs on a plain RGF sub-plan): dH for every
     band block |a - b| <= w and the energy-summed dSigma_L / dSigma_R, against
-    the oracle's gradient over the n-diagonal band."""
+    the oracle's gradient over the band."""
     import torch
     rng = np.random.default_rng(200 + 10 * w + N)
     nE = 4
@@ -229,7 +230,8 @@ def test_grad_block_ndiagonal_through_the_fused_chain(P, w, N, ck):
     sR = torch.tensor(prob.sigma_R, device="cuda")
     E = torch.tensor(prob.energies, device="cuda")
     plan = P.Plan(prob.sizes, 2 * w + 1, nE, outputs=P.NEGF_OUT_TRANSMISSION | P.NEGF_OUT_GRAD,
-                  checkpoint_every=ck)
+                  checkpoint_every=ck, n_domains=nd)
+    assert plan.n_domains == nd
     T, dH, dSL, dSR = plan.grad(Hp, sL, sR, E, torch.tensor(weights, device="cuda"))
     assert not plan.info.cpu().numpy().any()
     plan.close()
