@@ -322,7 +322,8 @@ def run_ours(a, rank, world, local_rank):
     tune = None
     if not a.no_autotune:
         best, tms = plan.autotune(H, sL, sR, E, out_band=Gb, out_g1n=G1)
-        tune = {"energy_groups": best, "ms_per_solve_by_groups": {str(k): v for k, v in tms.items()}}
+        tune = {"energy_groups": best, "ms_per_solve_by_groups": {str(k): v for k, v in tms.items()},
+                "tensor_core_tile_tmem_cols": P.negf_plan_tile_cols(plan.handle)}
     groups = P.negf_plan_groups(plan.handle)
 
     # per-kernel profile of one extra step (CUDA events around every launch on

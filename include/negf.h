@@ -367,6 +367,10 @@ negf_status negf_band_residual(negf_plan_t* p, const negf_c128* H, const negf_c1
  * repetitions each after one warm-up, and keeps the fastest count for the
  * plan's later calls.  ms (nullable): NEGF_AUTOTUNE_CANDIDATES doubles, the
  * time per solve for each candidate in that order, or -1 where skipped.  best_groups (nullable): the kept count.
+ * Mixed plans then time the tensor-core products' N tile at that count: the
+ * widest tile whose level accumulators fit an SM's 512 tensor-memory columns,
+ * or the widest within 256 (two CTAs hold tensor memory at once, the A
+ * operand is sliced once per tile), and keep the faster (negf_plan_tile_cols).
  * Synchronises the plan's stream.  NEGF_ERR_UNSUPPORTED for DDRGF and
  * checkpointed plans (fixed stream sets). */
 negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* sigma_L,
@@ -392,6 +396,13 @@ negf_status negf_tune_precision(negf_plan_t* p, const negf_c128* H, const negf_c
 
 /* The plan's product width in bits (0 for FP64 plans); -1 for NULL. */
 int32_t negf_plan_product_bits(const negf_plan_t* p);
+
+/* The tensor-memory columns one tensor-core product CTA of the plan may take
+ * (512 or 256, set by negf_autotune); -1 for NULL. */
+int32_t negf_plan_tile_cols(const negf_plan_t* p);
+
+/* Set it for later calls (512 or 256, else NEGF_ERR_ARG). */
+negf_status negf_plan_set_tile_cols(negf_plan_t* p, int32_t cols);
 
 /* The plan's current number of energy groups; -1 for NULL. */
 int32_t negf_plan_groups(const negf_plan_t* p);

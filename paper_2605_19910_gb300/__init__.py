@@ -58,6 +58,7 @@ EXPORTED = [
     "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
     "negf_fp64_peak", "negf_plan_set_wait_limit", "negf_grad_strided", "negf_tune_precision",
     "negf_plan_product_bits", "negf_plan_levels", "negf_ddrgf_model", "negf_measure_r_inv",
+    "negf_plan_tile_cols", "negf_plan_set_tile_cols",
 ]
 
 NEGF_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -140,6 +141,10 @@ def _load():
     lib.negf_autotune.restype = st
     lib.negf_plan_groups.argtypes = [vp]
     lib.negf_plan_groups.restype = i32
+    lib.negf_plan_tile_cols.argtypes = [vp]
+    lib.negf_plan_tile_cols.restype = i32
+    lib.negf_plan_set_tile_cols.argtypes = [vp, i32]
+    lib.negf_plan_set_tile_cols.restype = ctypes.c_int
     lib.negf_plan_set_groups.argtypes = [vp, i32]
     lib.negf_plan_set_groups.restype = st
     lib.negf_solve_host.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
@@ -351,6 +356,16 @@ def negf_measure_r_inv(b, batch, precision=NEGF_FP64, stream=None):
 def negf_plan_groups(plan):
     """``negf_plan_groups`` of include/negf.h (argument marshalling only)."""
     return int(_lib.negf_plan_groups(plan))
+
+
+def negf_plan_tile_cols(plan):
+    """``negf_plan_tile_cols`` of include/negf.h (argument marshalling only)."""
+    return int(_lib.negf_plan_tile_cols(plan))
+
+
+def negf_plan_set_tile_cols(plan, cols):
+    """``negf_plan_set_tile_cols`` of include/negf.h (argument marshalling only)."""
+    return int(_lib.negf_plan_set_tile_cols(plan, cols))
 
 
 def negf_plan_set_groups(plan, groups):

@@ -1458,12 +1458,49 @@ negf_status negf_autotune(negf_plan_t* p, const negf_c128* H, const negf_c128* s
     if (ms) ms[k] = per;
     if (per < best_ms) { best_ms = per; best = G; }
   }
+  p->groups = st == NEGF_OK ? best : g0;
+  // mixed plans: the tensor-core products' N tile at that group count, from
+  // the widest the tensor memory holds (one CTA may take all 512 columns of
+  // an SM) or half of it (two CTAs hold tensor memory at once; A is sliced
+  // once per tile): which is faster depends on the block sizes and widths
+  if (st == NEGF_OK && p->precision == NEGF_MIXED) {
+    const int c0 = p->tc_cols;
+    int best_c = c0;
+    double best_c_ms = best_ms;
+    for (int cols : {512, 256}) {
+      if (cols == c0) continue;
+      p->tc_cols = cols;
+      drop_graph(p);
+      st = negf_solve(p, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info);
+      if (st != NEGF_OK) break;
+      if (cudaEventRecord(a, p->stream) != cudaSuccess) { st = NEGF_ERR_CUDA; break; }
+      for (int r = 0; r < reps && st == NEGF_OK; ++r)
+        st = negf_solve(p, H, sigma_L, sigma_R, sigma_E_stride, E, G_band, G_1N, info);
+      if (st != NEGF_OK) break;
+      float t = 0.0f;
+      if (cudaEventRecord(b, p->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+          cudaEventElapsedTime(&t, a, b) != cudaSuccess) { st = NEGF_ERR_CUDA; break; }
+      const double per = (double)t / reps;
+      if (per < best_c_ms) { best_c_ms = per; best_c = cols; }
+    }
+    p->tc_cols = st == NEGF_OK ? best_c : c0;
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  p->groups = st == NEGF_OK ? best : g0;
   drop_graph(p);
   if (best_groups) *best_groups = p->groups;
   return st;
+}
+
+int32_t negf_plan_tile_cols(const negf_plan_t* p) { return p ? p->tc_cols : -1; }
+
+negf_status negf_plan_set_tile_cols(negf_plan_t* p, int32_t cols) {
+  if (!p || (cols != 512 && cols != 256)) return NEGF_ERR_ARG;
+  if (cols != p->tc_cols) {
+    p->tc_cols = cols;
+    drop_graph(p);
+  }
+  return NEGF_OK;
 }
 
 int32_t negf_plan_groups(const negf_plan_t* p) { return p ? p->groups : -1; }

@@ -36,6 +36,7 @@
 // complex columns.  Operands use the K-major, non-swizzled canonical layout
 // (8-row x 16-byte core matrices).  One thread issues the MMAs; completion is
 // tracked with an mbarrier whose wait is bounded.
+#include <algorithm>
 #include <type_traits>
 
 #include "negf_common.cuh"
@@ -710,7 +711,7 @@ int g_tc_smem_optin = 0;
 bool is_pm1(double2 z) { return z.y == 0.0 && (z.x == 1.0 || z.x == -1.0); }
 bool is_pm1_or_0(double2 z) { return z.y == 0.0 && (z.x == 1.0 || z.x == -1.0 || z.x == 0.0); }
 
-TcCfg tc_config(int n, int k, int bits) {
+TcCfg tc_config(int n, int k, int bits, int tmem_max = 512) {
   TcCfg c;
   if (bits <= 0) bits = 32;
   // Exact FP32 level sums: (products per level) * K_real * (2^s - 1)^2 < 2^24.
@@ -725,7 +726,10 @@ TcCfg tc_config(int n, int k, int bits) {
   }
   c.s = best_s;
   c.L = best_L;
-  const int cap = (512 / c.L) / 16 * 16;          // TMEM columns per level
+  // TMEM columns per level: the widest N tile whose L accumulators fit the
+  // allowed columns (narrower tiles let two CTAs hold tensor memory at once,
+  // at the cost of slicing A once per tile)
+  const int cap = std::max(16, (tmem_max / c.L) / 16 * 16);
   int nm = round_up(n < 16 ? 16 : n, 16);
   if (nm > cap) nm = cap;
   c.n_mma = nm;
@@ -768,7 +772,7 @@ cudaError_t zgemm_tc(const ZGemm& g, cudaStream_t st) {
       (g.C1 && !is_pm1_or_0(g.beta1)) || (g.C2 && !is_pm1_or_0(g.beta2)) ||
       (g.dshift && !is_pm1_or_0(g.gamma)))
     return cudaErrorNotSupported;
-  const TcCfg cfg = tc_config(g.n, g.k, g.bits);
+  const TcCfg cfg = tc_config(g.n, g.k, g.bits, g.tc_cols > 0 ? std::min(512, g.tc_cols) : 512);
   if (cfg.L > 8) return zgemm_f64(g, st);   // too long for exact slices: the FP64 product
   const int tiles_m = (g.m + MC - 1) / MC, tiles_n = (g.n + cfg.n_mma - 1) / cfg.n_mma;
   const size_t sm = tc_smem_bytes(cfg);

@@ -29,6 +29,7 @@ struct ZGemm {
   int* errword = nullptr;   // device error word for bounded-wait timeouts (tensor-core path)
   int bits = 0;             // tensor-core path: significant bits of the product (0 = 32; up to 56)
   long long wait_limit = -1;  // tensor-core path: polls of the MMA-completion wait (< 0: the default)
+  int tc_cols = 0;          // tensor-core path: most TMEM columns of one CTA (0 = 512; sets the N tile)
   int batch = 1;
   int reduce = 0;
 };

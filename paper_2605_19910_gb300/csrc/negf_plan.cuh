@@ -154,6 +154,7 @@ struct negf_plan_s {
 
   // independent energy groups run on forked streams (graph branches)
   int groups = 1;
+  int tc_cols = 512;   // tensor-core products: most TMEM columns per CTA (negf_autotune)
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;   // [0] fork, [1..] joins
   std::vector<cudaEvent_t> stagger;   // group g -> g + 1 start dependency

@@ -118,6 +118,7 @@ struct Sweep {
   cudaError_t gemm(ZGemm g) {
     g.errword = p->d_err;
     g.wait_limit = p->wait_limit;
+    g.tc_cols = p->tc_cols;
     if (g.bits == 0) g.bits = p->bits;
     if (p->precision == NEGF_MIXED)
       return launch(NEGF_PROF_GEMM_TC, gemm_flops(g), [&] { return negf::zgemm_tc(g, st); });

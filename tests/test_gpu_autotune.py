@@ -27,6 +27,7 @@ def test_autotune_keeps_a_timed_candidate_and_results_hold(P, precision, tol):
     assert set(ms) == set(P.AUTOTUNE_GROUPS) and all(t > 0 for t in ms.values())
     assert best in ms and ms[best] == min(ms.values())
     assert P.negf_plan_groups(plan.handle) == best
+    assert P.negf_plan_tile_cols(plan.handle) in ((512, 256) if precision == "mixed" else (512,))
     Gb, _ = plan.solve(Hp, sL, sR, E)
     plan.close()
     Gb = Gb.cpu().numpy()
@@ -54,3 +55,23 @@ def test_autotune_refuses_ddrgf_plans(P):
         plan.autotune(Hp, sL, sR, E)
     assert ei.value.status == P.NEGF_ERR_UNSUPPORTED
     plan.close()
+
+
+@pytest.mark.parametrize("cols", [256, 512])
+def test_tile_widths_give_the_oracle_results(P, cols):
+    """Both tensor-core N tiles negf_autotune chooses from (accumulators within
+    256 or 512 TMEM columns), on blocks of 96..160 (several tiles, ragged
+    last tiles) at the mixed defaults."""
+    import torch
+    prob = make_problem(10, b=None, size_range=(96, 160), w=1, n_energies=3, eta=1e-3, seed=95)
+    Hp, sL, sR, E = to_dev(prob, torch)
+    plan = P.Plan(prob.sizes, 3, 3, precision="mixed")
+    assert P.negf_plan_set_tile_cols(plan.handle, cols) == 0
+    assert P.negf_plan_tile_cols(plan.handle) == cols
+    assert P.negf_plan_set_tile_cols(plan.handle, 300) == P.NEGF_ERR_ARG
+    Gb, _ = plan.solve(Hp, sL, sR, E)
+    plan.close()
+    Gb = Gb.cpu().numpy()
+    for e in range(3):
+        ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, 1)
+        assert band_rel_err(Gb[e], ref["band"], prob.sizes, 1) < MIXED_TOL
