@@ -94,6 +94,8 @@ def _args():
                     help="refinement steps of the mixed plan's G_1N (the benchmark configuration has one)")
     ap.add_argument("--no-ddrgf-side", action="store_true",
                     help="skip the side measurement of DDRGF levels on a few-energy long chain")
+    ap.add_argument("--n-domains", type=int, default=1,
+                    help="DDRGF (D2, D1) pairs of the timed plan (1 = plain RGF, 0 = the cost model's choice)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -303,7 +305,10 @@ def run_ours(a, rank, world, local_rank):
     bits = a.product_bits if (a.product_bits is not None and a.precision == "mixed") else 0
     refine = a.refine_steps if a.precision == "mixed" else 0
     plan = P.Plan(prob.sizes, 2 * prob.w + 1, nE, precision=a.precision, outputs=outputs, product_bits=bits,
-                  refine_steps=refine)
+                  refine_steps=refine, n_domains=a.n_domains)
+    dd_plan = plan.n_domains > 1
+    if dd_plan:
+        refine = 0   # DDRGF plans take G_1N through the separators
     Gb = torch.empty(nE, plan.band_elems, dtype=torch.complex128, device=dev)
     G1 = torch.empty(nE, prob.sizes[0], prob.sizes[-1], dtype=torch.complex128, device=dev)
 
@@ -320,7 +325,7 @@ def run_ours(a, rank, world, local_rank):
         bits = tb
     # energy-group autotuner on these inputs (untimed, before the warm-up)
     tune = None
-    if not a.no_autotune:
+    if not a.no_autotune and not dd_plan:   # DDRGF plans keep fixed stream sets
         best, tms = plan.autotune(H, sL, sR, E, out_band=Gb, out_g1n=G1)
         tune = {"energy_groups": best, "ms_per_solve_by_groups": {str(k): v for k, v in tms.items()},
                 "tensor_core_tile_tmem_cols": P.negf_plan_tile_cols(plan.handle)}
@@ -330,14 +335,16 @@ def run_ours(a, rank, world, local_rank):
     # its stream) with the plan set to one energy group, so that concurrent
     # launches of the groups do not inflate each other's durations (same
     # chunking, hence the same launch shapes, as the timed plan)
-    P.negf_plan_set_groups(plan.handle, 1)
+    if not dd_plan:
+        P.negf_plan_set_groups(plan.handle, 1)
     P.negf_profile_enable(plan.handle, 1)
     for _ in range(2):                  # the second of two profiled steps
         plan.solve(H, sL, sR, E, out_band=Gb, out_g1n=G1, sync=False)
         prof = P.negf_profile_read(plan.handle)
     P.negf_profile_enable(plan.handle, 0)
     plan.sync()
-    P.negf_plan_set_groups(plan.handle, groups)
+    if not dd_plan:
+        P.negf_plan_set_groups(plan.handle, groups)
     P.negf_profile_enable(plan.handle, 1)
     step()
     launches_per_step = int(sum(v[2] for v in P.negf_profile_read(plan.handle).values()))
@@ -368,31 +375,8 @@ def run_ours(a, rank, world, local_rank):
     ms = max_over_ranks(t_start.elapsed_time(t_end) / a.steps, dist, dev)
     value = job_throughput(world, nE, N, ms)
 
-    fp64 = measure_fp64_peaks(P, local_rank, stream)
-
-    # sampled parity against the oracle (two energies) for the rel-err report:
-    # the band and G_1N (from the refined last column when refine_steps = 1)
-    rel = None
-    if rank == 0:
-        from oracle import rgf as O
-        errs, errs1 = [], []
-        for e in (0, nE // 2):
-            ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, prob.w, first_row=True)
-            got = P.unpack_band(Gb[e].cpu().numpy(), prob.sizes, prob.w)
-            num = sum(np.linalg.norm(got[k] - v) ** 2 for k, v in ref["band"].items())
-            den = sum(np.linalg.norm(v) ** 2 for v in ref["band"].values())
-            errs.append(float(np.sqrt(num / den)))
-            g1 = G1[e].cpu().numpy()
-            errs1.append(float(np.linalg.norm(g1 - ref["G1N"]) / np.linalg.norm(ref["G1N"])))
-        rel = {"band": max(errs), "G1N": max(errs1), "energies": [0, nE // 2],
-               "G1N_refined": bool(refine)}
-
-    # a-posteriori check of every energy's band from the band alone:
-    # sqrt(sum_i ||(M G)_ii - I||_F^2 / sum_i b_i) (negf_band_residual)
-    res = plan.band_residual(H, sL, sR, E, Gb).cpu().numpy()
-    band_residual = {"median": float(np.median(res)), "max": float(res.max()), "energies": int(nE)}
-
-    # end to end through the public API: pinned host inputs -> device, solve,
+    # end to end through the public API, right after the timed solves (before
+    # the host-side checks below): pinned host inputs -> device, solve,
     # selected blocks and G_1N back to pinned host memory, every step
     e2e = None
     if not a.no_e2e:
@@ -434,6 +418,30 @@ def run_ours(a, rank, world, local_rank):
                "timer": "host wall clock around the synchronous call",
                "plain_d2h_copy_gbps": d2h_gbps, "ms_per_call": [round(t, 2) for t in e2e_ms]}
         del Gb_h, G1_h
+
+    fp64 = measure_fp64_peaks(P, local_rank, stream)
+
+    # sampled parity against the oracle (two energies) for the rel-err report:
+    # the band and G_1N (from the refined last column when refine_steps = 1)
+    rel = None
+    if rank == 0:
+        from oracle import rgf as O
+        errs, errs1 = [], []
+        for e in (0, nE // 2):
+            ref = O.rgf_selected(O.system_blocks(prob, prob.energies[e]), prob.sizes, prob.w, first_row=True)
+            got = P.unpack_band(Gb[e].cpu().numpy(), prob.sizes, prob.w)
+            num = sum(np.linalg.norm(got[k] - v) ** 2 for k, v in ref["band"].items())
+            den = sum(np.linalg.norm(v) ** 2 for v in ref["band"].values())
+            errs.append(float(np.sqrt(num / den)))
+            g1 = G1[e].cpu().numpy()
+            errs1.append(float(np.linalg.norm(g1 - ref["G1N"]) / np.linalg.norm(ref["G1N"])))
+        rel = {"band": max(errs), "G1N": max(errs1), "energies": [0, nE // 2],
+               "G1N_refined": bool(refine)}
+
+    # a-posteriori check of every energy's band from the band alone:
+    # sqrt(sum_i ||(M G)_ii - I||_F^2 / sum_i b_i) (negf_band_residual)
+    res = plan.band_residual(H, sL, sR, E, Gb).cpu().numpy()
+    band_residual = {"median": float(np.median(res)), "max": float(res.max()), "energies": int(nE)}
 
     # roofline of the dominant kernel (from the profiled step)
     peaks = {}
@@ -512,6 +520,7 @@ def run_ours(a, rank, world, local_rank):
     from oracle.rgf import rgf_flops_paper
     flops_step = rgf_flops_paper(prob.sizes, prob.w) * nE
     ws_gb = P.negf_workspace_bytes(plan.handle) / 1e9
+    plan_domains = plan.n_domains
     plan_bits = P.negf_plan_product_bits(plan.handle)
     plan.close()
 
@@ -659,7 +668,10 @@ def run_ours(a, rank, world, local_rank):
                        "l2": "no flush: each step writes %.1f GB of selected blocks and %.1f GB of sweep "
                              "workspace, both far above the 129 MB L2" % (Gb.numel() * 16 / 1e9, ws_gb),
                        "parallelism": f"replicas x{world} (energies)",
-                       "energy_groups": groups},
+                       "energy_groups": groups,
+                       "n_domains": plan_domains,
+                       "hbm_footprint_gb": {"outputs": Gb.numel() * 16 / 1e9 + G1.numel() * 16 / 1e9,
+                                            "workspace": ws_gb}},
             "autotune": tune,
             "precision_tuning": prec_tune,
             "effective_tflops_paper_count": flops_step / (ms * 1e-3) / 1e12 * world,
