@@ -62,7 +62,7 @@ typedef enum {
   NEGF_ERR_NOMEM = 4,        /* workspace allocation failed                    */
   NEGF_ERR_CUDA = 5,         /* a CUDA runtime call failed                     */
   NEGF_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up             */
-  NEGF_ERR_UNSUPPORTED = 7   /* valid request this build does not implement    */
+  NEGF_ERR_UNSUPPORTED = 7   /* valid request this library does not implement  */
 } negf_status;
 
 /* Arithmetic of the sweep.

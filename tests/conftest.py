@@ -14,7 +14,7 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # GPU tests are never silently skipped on a GPU machine: they fail if CUDA or
+    # GPU tests are never silently skipped on a machine with a GPU: they fail if CUDA or
     # the library is missing.  On a CPU-only machine they are skipped unless
     # selected explicitly with -m gpu.
     try:
