@@ -418,8 +418,8 @@ def run_ours(a, rank, world, local_rank):
                "timer": "host wall clock around the synchronous call",
                "plain_d2h_copy_gbps": d2h_gbps, "ms_per_call": [round(t, 2) for t in e2e_ms],
                "ms_per_call_median": float(np.median(e2e_ms)),
-               "note": "the host link is shared with the machine's other GPUs: calls whose copies meet "
-                       "other traffic take longer (plain_d2h_copy_gbps is this run's plain copy rate)"}
+               "note": "calls whose copies meet other traffic on the host link take longer "
+                       "(plain_d2h_copy_gbps: this run's plain copy rate of the band)"}
         del Gb_h, G1_h
 
     fp64 = measure_fp64_peaks(P, local_rank, stream)
