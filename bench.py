@@ -276,10 +276,7 @@ def _overrides(a):
 
 def run_ours(a, rank, world, local_rank):
     import numpy as np
-    pool = None
     cores = os.cpu_count() or 1
-    if rank == 0 and world == 1 and not a.no_cpu:
-        pool = make_pool(cores)          # spawn, before the first GPU call
     import torch
     import __graft_entry__ as g
     g.build()
@@ -649,8 +646,11 @@ def run_ours(a, rank, world, local_rank):
             ddrgf_side[label] = {"ms": d0.elapsed_time(d1) / 5, "rel_dev_from_rgf": dev_}
         del dH, ref_band
 
+    # the CPU oracle baseline, after every GPU timing (spawned worker
+    # processes, so no CUDA state is forked; none exist while the GPU is timed)
     cpu = None
-    if pool is not None:
+    if rank == 0 and world == 1 and not a.no_cpu:
+        pool = make_pool(cores)
         cpu, _ = oracle_sample(a.workload, a.cpu_energies, pool, cores)
         pool.close()
 

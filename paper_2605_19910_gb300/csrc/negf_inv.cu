@@ -130,6 +130,7 @@ size_t inv_smem_bytes(int b) {
 }  // namespace
 
 static size_t g_inv_dyn_max = 0;   // dynamic shared memory opt-in of the kernel
+static int g_sms = 0;               // SMs of the device
 
 cudaError_t zinv_cluster_init();
 int zinv_cluster_max_block();
@@ -143,6 +144,8 @@ cudaError_t zinv_init() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa;
   e = cudaFuncGetAttributes(&fa, zinv_gj_kernel);
@@ -166,7 +169,12 @@ cudaError_t zinv_f64(const double2* S, int64_t sS, double2* T, int64_t sT, int b
                      int32_t* info, int layer1, int* errword, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   size_t sm = inv_smem_bytes(b);
-  if (sm > g_inv_dyn_max) return zinv_f64_cluster(S, sS, T, sT, b, batch, info, layer1, errword, st);
+  // blocks too large for one CTA, and launches too small to fill the GPU
+  // (few energies: a lone 64 x 64 inversion takes ~250 us of one SM's FP64
+  // unit) go to the 2-CTA cluster kernel, which splits each block's rows
+  // over two SMs
+  if (sm > g_inv_dyn_max || (b >= 48 && g_sms > 0 && 2 * batch <= g_sms))
+    return zinv_f64_cluster(S, sS, T, sT, b, batch, info, layer1, errword, st);
   zinv_gj_kernel<<<batch, dim3(INV_TX, INV_TY), sm, st>>>(S, sS, T, sT, b, info, layer1, errword);
   return cudaGetLastError();
 }
