@@ -444,6 +444,13 @@ enum { NEGF_PROF_INV = 0, NEGF_PROF_GEMM_F64 = 1, NEGF_PROF_GEMM_TC = 2, NEGF_PR
        NEGF_PROF_KINDS = 4 };
 negf_status negf_profile_enable(negf_plan_t* p, int32_t on);
 int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* launches);
+/* The same read (and reset), with the flops the hardware units execute per
+ * kind as well (issued_flops, may be NULL): the inverse's 8 b^3; the FP64
+ * product's three real products per complex one (3M form, 6 m n k); the
+ * tensor-core product's BF16 slice products, L (L + 1) / 2 per 16-deep real
+ * K step for L slices, over whole tiles of 128 real rows (padding included). */
+int32_t negf_profile_read_issued(negf_plan_t* p, double* ms, double* flops, double* issued_flops,
+                                 int64_t* launches);
 
 /* negf_solve for callers that cannot allocate device memory.
  *

@@ -55,7 +55,7 @@ EXPORTED = [
     "negf_plan_n_domains", "negf_auto_domains", "negf_band_residual", "negf_autotune", "negf_plan_groups",
     "negf_plan_set_groups", "negf_lesser", "negf_solve_host",
     "negf_transmission", "negf_grad", "negf_sync", "negf_destroy", "negf_status_string",
-    "negf_profile_enable", "negf_profile_read", "negf_last_cuda_error", "negf_solve_noalloc",
+    "negf_profile_enable", "negf_profile_read", "negf_profile_read_issued", "negf_last_cuda_error", "negf_solve_noalloc",
     "negf_fp64_peak", "negf_plan_set_wait_limit", "negf_grad_strided", "negf_tune_precision",
     "negf_plan_product_bits", "negf_plan_levels", "negf_ddrgf_model", "negf_measure_r_inv",
     "negf_plan_tile_cols", "negf_plan_set_tile_cols",
@@ -130,6 +130,8 @@ def _load():
     lp = ctypes.POINTER(ctypes.c_int64)
     lib.negf_profile_read.argtypes = [vp, dp, dp, lp]
     lib.negf_profile_read.restype = i32
+    lib.negf_profile_read_issued.argtypes = [vp, dp, dp, dp, lp]
+    lib.negf_profile_read_issued.restype = i32
     lib.negf_solve_noalloc.argtypes = [ctypes.POINTER(negf_desc), vp, vp, vp, i64, vp, vp, vp, vp, vp]
     lib.negf_solve_noalloc.restype = st
     lib.negf_last_cuda_error.argtypes = []
@@ -450,6 +452,19 @@ def negf_profile_read(plan):
     if n < 0:
         raise NegfError(NEGF_ERR_CUDA, "negf_profile_read")
     return {PROF_NAMES[k]: (ms[k], fl[k], ln[k]) for k in range(n)}
+
+
+def negf_profile_read_issued(plan):
+    """Returns ``{kind_name: (ms, flops, issued_flops, launches)}``: the read
+    of ``negf_profile_read`` with the flops the units execute per kind."""
+    ms = (ctypes.c_double * NEGF_PROF_KINDS)()
+    fl = (ctypes.c_double * NEGF_PROF_KINDS)()
+    iss = (ctypes.c_double * NEGF_PROF_KINDS)()
+    ln = (ctypes.c_int64 * NEGF_PROF_KINDS)()
+    n = _lib.negf_profile_read_issued(plan, ms, fl, iss, ln)
+    if n < 0:
+        raise NegfError(NEGF_ERR_CUDA, "negf_profile_read_issued")
+    return {PROF_NAMES[k]: (ms[k], fl[k], iss[k], ln[k]) for k in range(n)}
 
 
 # ---------------------------------------------------------------------------

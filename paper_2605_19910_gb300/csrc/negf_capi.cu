@@ -1592,7 +1592,8 @@ negf_status negf_profile_enable(negf_plan_t* p, int32_t on) {
   return NEGF_OK;
 }
 
-int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* launches) {
+int32_t negf_profile_read_issued(negf_plan_t* p, double* ms, double* flops, double* issued_flops,
+                                 int64_t* launches) {
   if (!p) return -1;
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return -1;
   for (auto& r : p->recs) {
@@ -1600,6 +1601,7 @@ int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* la
     if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
       p->prof_ms[r.kind] += t;
       p->prof_flops[r.kind] += r.flops;
+      p->prof_issued[r.kind] += r.issued;
       p->prof_launches[r.kind] += 1;
     }
     cudaEventDestroy(r.a);
@@ -1609,10 +1611,15 @@ int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* la
   for (int k = 0; k < NEGF_PROF_KINDS; ++k) {
     if (ms) ms[k] = p->prof_ms[k];
     if (flops) flops[k] = p->prof_flops[k];
+    if (issued_flops) issued_flops[k] = p->prof_issued[k];
     if (launches) launches[k] = p->prof_launches[k];
-    p->prof_ms[k] = 0; p->prof_flops[k] = 0; p->prof_launches[k] = 0;
+    p->prof_ms[k] = 0; p->prof_flops[k] = 0; p->prof_issued[k] = 0; p->prof_launches[k] = 0;
   }
   return NEGF_PROF_KINDS;
+}
+
+int32_t negf_profile_read(negf_plan_t* p, double* ms, double* flops, int64_t* launches) {
+  return negf_profile_read_issued(p, ms, flops, nullptr, launches);
 }
 
 }  // extern "C"

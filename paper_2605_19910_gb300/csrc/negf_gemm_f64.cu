@@ -173,4 +173,9 @@ cudaError_t zgemm_f64(const ZGemm& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+double zgemm_f64_issued_flops(const ZGemm& g) {
+  if (g.m <= 0 || g.n <= 0 || g.k <= 0 || g.batch <= 0) return 0.0;
+  return 6.0 * g.m * (double)g.n * g.k * g.batch;
+}
+
 }  // namespace negf

@@ -789,6 +789,16 @@ cudaError_t zgemm_tc(const ZGemm& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+double zgemm_tc_issued_flops(const ZGemm& g) {
+  if (g.m <= 0 || g.n <= 0 || g.k <= 0 || g.batch <= 0) return 0.0;
+  const TcCfg cfg = tc_config(g.n, g.k, g.bits, g.tc_cols > 0 ? std::min(512, g.tc_cols) : 512);
+  if (cfg.L > 8) return zgemm_f64_issued_flops(g);
+  const double tiles = (double)((g.m + MC - 1) / MC) * ((g.n + cfg.n_mma - 1) / cfg.n_mma);
+  const double ksteps = (double)((g.k + Chunk<16>::KC - 1) / Chunk<16>::KC) * (Chunk<16>::KR / 16);
+  const double pairs = cfg.L * (cfg.L + 1) / 2;
+  return tiles * g.batch * ksteps * pairs * 2.0 * 128.0 * cfg.n_mma * 16.0;
+}
+
 cudaError_t kernels_init() {
   cudaError_t e = zinv_init();
   if (e != cudaSuccess) return e;

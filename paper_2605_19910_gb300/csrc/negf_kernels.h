@@ -36,9 +36,18 @@ struct ZGemm {
 
 // FP64 product on the FP64 tensor path (mma.sync m8n8k4 f64).
 cudaError_t zgemm_f64(const ZGemm& g, cudaStream_t st);
-// FP32-accurate split product on the 5th-generation tensor cores.
+// Product from exact BF16 slices on the 5th-generation tensor cores
+// (g.bits significant bits, up to 56).
 cudaError_t zgemm_tc(const ZGemm& g, cudaStream_t st);
 bool zgemm_tc_available();
+// Flops the units execute for one call, for the profiler (the method counts
+// 8 m n k per complex product): zgemm_f64 issues three real products per
+// complex one (3M form), 6 m n k; zgemm_tc issues L (L + 1) / 2 BF16 slice
+// products per 16-deep real K step over whole tiles of 128 real rows and its
+// N tile (padding included), or the FP64 count where it hands over to
+// zgemm_f64.
+double zgemm_f64_issued_flops(const ZGemm& g);
+double zgemm_tc_issued_flops(const ZGemm& g);
 
 // One-time kernel attributes (shared-memory opt-in); call outside capture.
 cudaError_t kernels_init();

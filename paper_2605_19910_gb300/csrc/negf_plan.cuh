@@ -170,10 +170,11 @@ struct negf_plan_s {
 
   // optional per-launch timing (negf_profile_enable)
   bool profiling = false;
-  struct Rec { int kind; double flops; cudaEvent_t a, b; };
+  struct Rec { int kind; double flops, issued; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   double prof_ms[NEGF_PROF_KINDS] = {0};
   double prof_flops[NEGF_PROF_KINDS] = {0};
+  double prof_issued[NEGF_PROF_KINDS] = {0};
   int64_t prof_launches[NEGF_PROF_KINDS] = {0};
 
   // CUDA graph of the last call

@@ -101,9 +101,11 @@ struct Sweep {
   // Every kernel launch of the schedule goes through here so that the
   // optional profiler can bracket it with events on the launching stream.
   template <class F>
-  cudaError_t launch(int kind, double flops, F f) {
+  cudaError_t launch(int kind, double flops, F f) { return launch(kind, flops, flops, f); }
+  template <class F>
+  cudaError_t launch(int kind, double flops, double issued, F f) {
     if (!p->profiling) return f();
-    negf_plan_s::Rec r{kind, flops, nullptr, nullptr};
+    negf_plan_s::Rec r{kind, flops, issued, nullptr, nullptr};
     NEGF_TRY(cudaEventCreate(&r.a));
     NEGF_TRY(cudaEventCreate(&r.b));
     NEGF_TRY(cudaEventRecord(r.a, st));
@@ -121,11 +123,13 @@ struct Sweep {
     g.tc_cols = p->tc_cols;
     if (g.bits == 0) g.bits = p->bits;
     if (p->precision == NEGF_MIXED)
-      return launch(NEGF_PROF_GEMM_TC, gemm_flops(g), [&] { return negf::zgemm_tc(g, st); });
-    return launch(NEGF_PROF_GEMM_F64, gemm_flops(g), [&] { return negf::zgemm_f64(g, st); });
+      return launch(NEGF_PROF_GEMM_TC, gemm_flops(g), p->profiling ? negf::zgemm_tc_issued_flops(g) : 0.0,
+                    [&] { return negf::zgemm_tc(g, st); });
+    return gemm64(g);
   }
   cudaError_t gemm64(ZGemm g) {
-    return launch(NEGF_PROF_GEMM_F64, gemm_flops(g), [&] { return negf::zgemm_f64(g, st); });
+    return launch(NEGF_PROF_GEMM_F64, gemm_flops(g), p->profiling ? negf::zgemm_f64_issued_flops(g) : 0.0,
+                  [&] { return negf::zgemm_f64(g, st); });
   }
   cudaError_t inv(const double2* S, int64_t sS, double2* T, int64_t sT, int b, int batch, int layer1) {
     NEGF_TRY(launch(NEGF_PROF_INV, 8.0 * b * (double)b * b * batch, [&] {
