@@ -50,7 +50,7 @@ NCU_TRAFFIC = {
         "bytes_per_unit": ((269.672192e6 + 98.240256e6) + (408.351232e6 + 102.905088e6)) / 2 / 2048,
         "unit": "block product",
         "src": "paper_2605_19910_gb300/csrc/negf_gemm_tc.cu",
-        "sha256": "40857cfde27104ecf37a038d466d57a492525b74327609a446b67bf398ba73cc",
+        "sha256": "c97b4531aab19d8158d8640c74a7636a480541313ce7445c473f7c1193ed61cc",
     },
 }
 

@@ -713,9 +713,9 @@ bool is_pm1_or_0(double2 z) { return z.y == 0.0 && (z.x == 1.0 || z.x == -1.0 ||
 
 TcCfg tc_config(int n, int k, int bits, int tmem_max = 512) {
   TcCfg c;
-  if (bits <= 0) bits = 32;
+  if (bits <= 0) bits = 32;   // a plan always passes its width (48 unless set)
   // Exact FP32 level sums: (products per level) * K_real * (2^s - 1)^2 < 2^24.
-  // The default (32 bits) only needs level 0 exact (deeper levels carry
+  // Products of at most 32 bits only need level 0 exact (deeper levels carry
   // weights below 2^-32); longer products need every level exact.
   const double kr = 2.0 * k;
   int best_s = 1, best_L = 1;
