@@ -40,6 +40,8 @@ def test_status_strings_and_null_handling():
     assert P.lib().negf_band_offset(None, 0, 0) == -1
     assert P.lib().negf_workspace_bytes(None) == 0
     assert P.negf_sync(None) == P.NEGF_ERR_ARG
+    assert P.lib().negf_profile_read(None, None, None, None) == -1
+    assert P.lib().negf_profile_read_issued(None, None, None, None, None) == -1
     P.negf_destroy(None)
 
 
