@@ -364,8 +364,8 @@ negf_status negf_band_residual(negf_plan_t* p, const negf_c128* H, const negf_c1
  * replays the plan's negf_solve schedule on the caller's buffers (same
  * arguments as negf_solve) with 1, 2, 3, 4, 6 and 8 groups (at most
  * NEGF_MAX_GROUPS, at most one group per energy of a chunk), `reps` timed
- * repetitions each after one warm-up, and keeps the fastest count for the
- * plan's later calls.  ms (nullable): NEGF_AUTOTUNE_CANDIDATES doubles, the
+ * repetitions each after one warm-up, and keeps for the plan's later calls
+ * the fewest groups whose time is within 1 % of the fastest.  ms (nullable): NEGF_AUTOTUNE_CANDIDATES doubles, the
  * time per solve for each candidate in that order, or -1 where skipped.  best_groups (nullable): the kept count.
  * Mixed plans then time the tensor-core products' N tile at that count: the
  * widest tile whose level accumulators fit an SM's 512 tensor-memory columns,

@@ -25,7 +25,9 @@ def test_autotune_keeps_a_timed_candidate_and_results_hold(P, precision, tol):
     plan = P.Plan(prob.sizes, 3, len(prob.energies), precision=precision)
     best, ms = plan.autotune(Hp, sL, sR, E)
     assert set(ms) == set(P.AUTOTUNE_GROUPS) and all(t > 0 for t in ms.values())
-    assert best in ms and ms[best] == min(ms.values())
+    # the fewest groups within 1 % of the fastest
+    assert best in ms and ms[best] <= 1.01 * min(ms.values())
+    assert all(ms[g] > 1.01 * min(ms.values()) for g in ms if g < best)
     assert P.negf_plan_groups(plan.handle) == best
     assert P.negf_plan_tile_cols(plan.handle) in ((512, 256) if precision == "mixed" else (512,))
     Gb, _ = plan.solve(Hp, sL, sR, E)
