@@ -417,8 +417,9 @@ def run_ours(a, rank, world, local_rank):
                "timer": "host wall clock around the synchronous call",
                "plain_d2h_copy_gbps": d2h_gbps, "ms_per_call": [round(t, 2) for t in e2e_ms],
                "ms_per_call_median": float(np.median(e2e_ms)),
-               "note": "calls whose copies meet other traffic on the host link take longer "
-                       "(plain_d2h_copy_gbps: this run's plain copy rate of the band)"}
+               "note": "value from the mean call time; ms_per_call lists every call (on some runs an "
+                       "occasional call takes ~2x, cause not identified); plain_d2h_copy_gbps: this "
+                       "run's plain copy rate of the band, the copy the call overlaps with its solve"}
         del Gb_h, G1_h
 
     fp64 = measure_fp64_peaks(P, local_rank, stream)
